@@ -1,0 +1,869 @@
+/*
+ * oracle.c -- plain FP64 CPU reference of the codebook Gaussian rasterizer.
+ *
+ * TEST INFRASTRUCTURE.  Only the tests, the smoke check and the CPU-baseline
+ * leg of the benchmark load this file's library.  The CUDA library never
+ * links, includes or calls it, and it shares no code with the CUDA library.
+ *
+ * What it computes (ContraGS, arXiv 2509.03775):
+ *   - state S = {G, C}, g_i = {p_i, o_i, g2sr_i, g2sh_i}, C = {SH, SR}
+ *     (Sec. 3.1): every Gaussian reads its scale+rotation from SR[g2sr_i]
+ *     and its SH colour coefficients from SH[g2sh_i];
+ *   - Eq. 2: Sigma = R(q) S S^T R(q)^T;
+ *   - Eq. 1 projected onto the image plane (Sec. 2.1: "alpha_i is the 2D
+ *     Gaussian projected from the 3D density"), with the local affine (EWA)
+ *     Jacobian of the pinhole map;
+ *   - c_i: the SH colour seen along the viewing direction (Sec. 2.1);
+ *   - Eq. 3: front-to-back compositing C = sum_k alpha_k c_k prod_{i<k}(1-alpha_i);
+ *   - the exact chain rule of all of the above (the gradient that the
+ *     SGLD update of Appendix A.1 consumes), with the codebook gradient of a
+ *     row equal to the sum over the Gaussians that index it.
+ *
+ * Precision.  Every continuous quantity is FP64.  The integer outcomes of
+ * the renderer -- which Gaussians are culled, the 3-sigma tile rectangle,
+ * the FP32 depth key, which (pixel, Gaussian) evaluations are skipped,
+ * clamped or terminate the pixel, and the colour clamp -- are decided in
+ * FP32 by the written operation order ("decision arithmetic", the functions
+ * whose names end in 32), because the CUDA kernels decide them in FP32 and
+ * both sides must take such a decision in the same precision.  The FP64
+ * values are then evaluated under those decisions.
+ *
+ * Nothing here is blocked, fused or reordered for speed beyond an OpenMP
+ * loop over independent tiles / Gaussians.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAX_BASIS 16
+#define OR_SR_WIDTH 8
+
+/* ------------------------------------------------------------------------ */
+/* Inputs                                                                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int n, k_sr, k_sh, sh_degree;
+  const double *pos;          /* [n][3] */
+  const double *logit;        /* [n]    opacity o = sigmoid(logit) */
+  const uint16_t *g2sr;       /* [n] */
+  const uint16_t *g2sh;       /* [n] */
+  const double *sr;           /* [k_sr][8]: log-scale x3, quaternion w x y z, pad */
+  const double *sh;           /* [k_sh][(d+1)^2][3] */
+} or_scene;
+
+typedef struct {
+  int width, height;
+  double fx, fy, cx, cy;
+  double w2c[12];             /* row-major 3x4 [R | t], OpenCV axes */
+  double campos[3];
+  double near;
+} or_camera;
+
+/* Per (view, Gaussian) FP64 record. */
+typedef struct {
+  double t[3];       /* camera-space centre */
+  double mean[2];    /* projected centre, pixels */
+  double cov[3];     /* 2D covariance (a, b, c) incl. the 0.3 dilation */
+  double conic[3];   /* its inverse (c0, c1, c2): [[c0, c1], [c1, c2]] */
+  double opacity;    /* sigmoid(logit) */
+  double rgb[3];     /* SH colour after the clamp at zero */
+  double dir[3];     /* unit direction campos -> p */
+  double dist;       /* |p - campos| */
+  double sigma3[6];  /* Sigma (Eq. 2) of the Gaussian's SR row: 00 01 02 11 12 22 */
+} or_rec64;
+
+/* Per (view, Gaussian) FP32 decision record. */
+typedef struct {
+  float mx, my;            /* projected centre */
+  float h0, h1, h2;        /* -c0/2, -c1, -c2/2 of the FP32 conic */
+  float o;                 /* FP32 opacity */
+  int32_t x0, y0, x1, y1;  /* tile rectangle [x0,x1) x [y0,y1); empty when culled */
+  uint32_t depth_bits;     /* IEEE bits of the FP32 camera depth */
+  uint32_t rgb_clamped;    /* bit c: colour channel c clamped at zero */
+  int32_t visible;
+  int32_t pad;
+} or_rec32;
+
+/* ------------------------------------------------------------------------ */
+/* Real spherical harmonics, degree <= 3 (the colour c_i of Sec. 2.1 and the  */
+/* SH codebook rows of Sec. 3.1).  Constants from their closed forms.         */
+/* ------------------------------------------------------------------------ */
+
+static double sh_c0(void) { return 0.5 * sqrt(1.0 / M_PI); }
+static double sh_c1(void) { return sqrt(3.0 / (4.0 * M_PI)); }
+static double sh_c2a(void) { return sqrt(15.0 / (4.0 * M_PI)); }
+static double sh_c2b(void) { return sqrt(5.0 / (16.0 * M_PI)); }
+static double sh_c2c(void) { return sqrt(15.0 / (16.0 * M_PI)); }
+static double sh_c3a(void) { return sqrt(35.0 / (32.0 * M_PI)); }
+static double sh_c3b(void) { return sqrt(105.0 / (4.0 * M_PI)); }
+static double sh_c3c(void) { return sqrt(21.0 / (32.0 * M_PI)); }
+static double sh_c3d(void) { return sqrt(7.0 / (16.0 * M_PI)); }
+static double sh_c3e(void) { return sqrt(105.0 / (16.0 * M_PI)); }
+
+/* The 16 basis constants with their signs, in basis order. */
+static void sh_consts(double k[OR_MAX_BASIS]) {
+  k[0] = sh_c0();
+  k[1] = -sh_c1(); k[2] = sh_c1(); k[3] = -sh_c1();
+  k[4] = sh_c2a(); k[5] = -sh_c2a(); k[6] = sh_c2b(); k[7] = -sh_c2a(); k[8] = sh_c2c();
+  k[9] = -sh_c3a(); k[10] = sh_c3b(); k[11] = -sh_c3c(); k[12] = sh_c3d();
+  k[13] = -sh_c3c(); k[14] = sh_c3e(); k[15] = -sh_c3a();
+}
+
+/* Y_k(x, y, z) for a unit direction, and optionally dY_k/d(x, y, z) with
+ * x, y, z treated as independent variables. */
+void or_sh_basis(int degree, const double d[3], double *Y, double *dY /* [16][3] or NULL */) {
+  double k[OR_MAX_BASIS];
+  sh_consts(k);
+  const double x = d[0], y = d[1], z = d[2];
+  const int nb = (degree + 1) * (degree + 1);
+  double P[OR_MAX_BASIS], Px[OR_MAX_BASIS], Py[OR_MAX_BASIS], Pz[OR_MAX_BASIS];
+  /* polynomial part P_k and its partial derivatives */
+  P[0] = 1; Px[0] = 0; Py[0] = 0; Pz[0] = 0;
+  P[1] = y; Px[1] = 0; Py[1] = 1; Pz[1] = 0;
+  P[2] = z; Px[2] = 0; Py[2] = 0; Pz[2] = 1;
+  P[3] = x; Px[3] = 1; Py[3] = 0; Pz[3] = 0;
+  P[4] = x * y; Px[4] = y; Py[4] = x; Pz[4] = 0;
+  P[5] = y * z; Px[5] = 0; Py[5] = z; Pz[5] = y;
+  P[6] = 2 * z * z - x * x - y * y; Px[6] = -2 * x; Py[6] = -2 * y; Pz[6] = 4 * z;
+  P[7] = x * z; Px[7] = z; Py[7] = 0; Pz[7] = x;
+  P[8] = x * x - y * y; Px[8] = 2 * x; Py[8] = -2 * y; Pz[8] = 0;
+  P[9] = y * (3 * x * x - y * y); Px[9] = 6 * x * y; Py[9] = 3 * x * x - 3 * y * y; Pz[9] = 0;
+  P[10] = x * y * z; Px[10] = y * z; Py[10] = x * z; Pz[10] = x * y;
+  P[11] = y * (4 * z * z - x * x - y * y); Px[11] = -2 * x * y;
+  Py[11] = 4 * z * z - x * x - 3 * y * y; Pz[11] = 8 * y * z;
+  P[12] = z * (2 * z * z - 3 * x * x - 3 * y * y); Px[12] = -6 * x * z; Py[12] = -6 * y * z;
+  Pz[12] = 6 * z * z - 3 * x * x - 3 * y * y;
+  P[13] = x * (4 * z * z - x * x - y * y); Px[13] = 4 * z * z - 3 * x * x - y * y;
+  Py[13] = -2 * x * y; Pz[13] = 8 * x * z;
+  P[14] = z * (x * x - y * y); Px[14] = 2 * x * z; Py[14] = -2 * y * z; Pz[14] = x * x - y * y;
+  P[15] = x * (x * x - 3 * y * y); Px[15] = 3 * x * x - 3 * y * y; Py[15] = -6 * x * y; Pz[15] = 0;
+  for (int i = 0; i < nb; ++i) {
+    Y[i] = k[i] * P[i];
+    if (dY) { dY[3 * i] = k[i] * Px[i]; dY[3 * i + 1] = k[i] * Py[i]; dY[3 * i + 2] = k[i] * Pz[i]; }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 2 in FP64: Sigma = R(q) diag(s)^2 R(q)^T, s = exp(log-scale), q       */
+/* normalised, R from the unit-quaternion formula.                           */
+/* ------------------------------------------------------------------------ */
+
+static void quat_rot(const double q[4], double R[9]) {
+  const double w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+static void normalise_quat(const double *row, double qn[4], double *norm) {
+  double n2 = row[3] * row[3] + row[4] * row[4] + row[5] * row[5] + row[6] * row[6];
+  if (!(n2 > 0)) { qn[0] = 1; qn[1] = qn[2] = qn[3] = 0; *norm = 0; return; }
+  double n = sqrt(n2);
+  for (int i = 0; i < 4; ++i) qn[i] = row[3 + i] / n;
+  *norm = n;
+}
+
+void or_sr_sigma(const double *row, double sigma[6]) {
+  double qn[4], nrm, R[9], s[3];
+  normalise_quat(row, qn, &nrm);
+  quat_rot(qn, R);
+  for (int j = 0; j < 3; ++j) s[j] = exp(row[j]);
+  static const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+  for (int e = 0; e < 6; ++e) {
+    double acc = 0;
+    for (int j = 0; j < 3; ++j) acc += R[3 * ia[e] + j] * R[3 * ib[e] + j] * s[j] * s[j];
+    sigma[e] = acc;
+  }
+}
+
+/* Gradient of a scalar loss through Eq. 2: given dL/dSigma over the six
+ * unique entries, return dL/d(row[0..6]). */
+void or_sr_sigma_backward(const double *row, const double g[6], double drow[8]) {
+  double qn[4], nrm, R[9], s[3];
+  normalise_quat(row, qn, &nrm);
+  quat_rot(qn, R);
+  for (int j = 0; j < 3; ++j) s[j] = exp(row[j]);
+  /* full symmetric matrix gradient: off-diagonal halves */
+  double G[9] = {g[0], 0.5 * g[1], 0.5 * g[2],
+                 0.5 * g[1], g[3], 0.5 * g[4],
+                 0.5 * g[2], 0.5 * g[4], g[5]};
+  double M[9], dM[9];
+  for (int a = 0; a < 3; ++a)
+    for (int j = 0; j < 3; ++j) M[3 * a + j] = R[3 * a + j] * s[j];
+  for (int a = 0; a < 3; ++a)  /* Sigma = M M^T  =>  dM = (G + G^T) M = 2 G M */
+    for (int j = 0; j < 3; ++j) {
+      double acc = 0;
+      for (int b = 0; b < 3; ++b) acc += 2.0 * G[3 * a + b] * M[3 * b + j];
+      dM[3 * a + j] = acc;
+    }
+  double ds[3] = {0, 0, 0}, dR[9];
+  for (int a = 0; a < 3; ++a)
+    for (int j = 0; j < 3; ++j) {
+      ds[j] += dM[3 * a + j] * R[3 * a + j];
+      dR[3 * a + j] = dM[3 * a + j] * s[j];
+    }
+  for (int j = 0; j < 3; ++j) drow[j] = ds[j] * s[j];
+  const double w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+  double dq[4];
+  dq[0] = -2 * z * dR[1] + 2 * y * dR[2] + 2 * z * dR[3] - 2 * x * dR[5] - 2 * y * dR[6] + 2 * x * dR[7];
+  dq[1] = 2 * y * dR[1] + 2 * z * dR[2] + 2 * y * dR[3] - 4 * x * dR[4] - 2 * w * dR[5] + 2 * z * dR[6] +
+          2 * w * dR[7] - 4 * x * dR[8];
+  dq[2] = -4 * y * dR[0] + 2 * x * dR[1] + 2 * w * dR[2] + 2 * x * dR[3] + 2 * z * dR[5] - 2 * w * dR[6] +
+          2 * z * dR[7] - 4 * y * dR[8];
+  dq[3] = -4 * z * dR[0] - 2 * w * dR[1] + 2 * x * dR[2] + 2 * w * dR[3] - 4 * z * dR[4] + 2 * y * dR[5] +
+          2 * x * dR[6] + 2 * y * dR[7];
+  if (nrm > 0) {
+    double dot = dq[0] * w + dq[1] * x + dq[2] * y + dq[3] * z;
+    for (int i = 0; i < 4; ++i) drow[3 + i] = (dq[i] - qn[i] * dot) / nrm;
+  } else {
+    for (int i = 0; i < 4; ++i) drow[3 + i] = 0;
+  }
+  drow[7] = 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP32 decision arithmetic.  The operation order is fixed; fmaf is the IEEE */
+/* fused multiply-add and every other operation is one IEEE-754 binary32     */
+/* operation rounded to nearest (the library is built with contraction off). */
+/* ------------------------------------------------------------------------ */
+
+/* exp in binary32: Cody-Waite reduction x = n ln2 + r, with ln 2 split into
+ * a head of 15 significant bits (so n * head is exact for |n| < 512) and the
+ * remainder ln 2 - head, then the degree-6 Taylor polynomial of e^r
+ * (|r| <= ln2/2, truncation error < 1.3e-7 relative) by Horner's rule, then
+ * scaling by 2^n built from its exponent bits.  Inputs at or below -87 give
+ * 0 and inputs at or above 88 give +inf. */
+float or_e32(float x) {
+  if (!(x > -87.0f)) return 0.0f;
+  if (!(x < 88.0f)) return INFINITY;
+  const float log2e = 1.44269502162933349609375f;
+  const float ln2_hi = 0.693145751953125f;
+  const float ln2_lo = 1.42860682030941723212e-6f; /* ln 2 - ln2_hi */
+  float n = rintf(x * log2e);
+  float r = fmaf(-n, ln2_hi, x);
+  r = fmaf(-n, ln2_lo, r);
+  float p = 1.0f / 720.0f;
+  p = fmaf(p, r, 1.0f / 120.0f);
+  p = fmaf(p, r, 1.0f / 24.0f);
+  p = fmaf(p, r, 1.0f / 6.0f);
+  p = fmaf(p, r, 0.5f);
+  p = fmaf(p, r, 1.0f);
+  p = fmaf(p, r, 1.0f);
+  int ni = (int)n;
+  union { uint32_t u; float f; } sc;
+  sc.u = (uint32_t)(ni + 127) << 23;
+  return p * sc.f;
+}
+
+static float sigmoid32(float l) { return 1.0f / (1.0f + or_e32(-l)); }
+
+void or_sh_consts32(float out[OR_MAX_BASIS]) {
+  double k[OR_MAX_BASIS];
+  sh_consts(k);
+  for (int i = 0; i < OR_MAX_BASIS; ++i) out[i] = (float)k[i];
+}
+
+/* FP32 Sigma of an SR row (the decision arithmetic's input to the projection). */
+void or_sr_sigma32(const float *row, float sig[6]) {
+  float s0 = or_e32(row[0]), s1 = or_e32(row[1]), s2 = or_e32(row[2]);
+  float qw = row[3], qx = row[4], qy = row[5], qz = row[6];
+  float n2 = fmaf(qw, qw, fmaf(qx, qx, fmaf(qy, qy, qz * qz)));
+  float w, x, y, z;
+  if (n2 > 0.0f) {
+    float nrm = sqrtf(n2);
+    w = qw / nrm; x = qx / nrm; y = qy / nrm; z = qz / nrm;
+  } else {
+    w = 1.0f; x = y = z = 0.0f;
+  }
+  float R[9];
+  R[0] = 1.0f - 2.0f * fmaf(y, y, z * z);
+  R[1] = 2.0f * fmaf(x, y, -(w * z));
+  R[2] = 2.0f * fmaf(x, z, w * y);
+  R[3] = 2.0f * fmaf(x, y, w * z);
+  R[4] = 1.0f - 2.0f * fmaf(x, x, z * z);
+  R[5] = 2.0f * fmaf(y, z, -(w * x));
+  R[6] = 2.0f * fmaf(x, z, -(w * y));
+  R[7] = 2.0f * fmaf(y, z, w * x);
+  R[8] = 1.0f - 2.0f * fmaf(x, x, y * y);
+  float M[9];
+  const float s[3] = {s0, s1, s2};
+  for (int a = 0; a < 3; ++a)
+    for (int j = 0; j < 3; ++j) M[3 * a + j] = R[3 * a + j] * s[j];
+  static const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+  for (int e = 0; e < 6; ++e) {
+    const float *ma = M + 3 * ia[e], *mb = M + 3 * ib[e];
+    sig[e] = fmaf(ma[0], mb[0], fmaf(ma[1], mb[1], ma[2] * mb[2]));
+  }
+}
+
+/* FP32 projection and decision record of one Gaussian in one view. */
+static void shadow_one(const float p[3], float logit, const float sig[6], const float *shrow, int nb,
+                       const float *camf /* 20 floats, see below */, int tile, int tiles_x,
+                       int tiles_y, const float shk[OR_MAX_BASIS], or_rec32 *r) {
+  /* camf: w2c[12], fx, fy, cx, cy, near, campos[3] */
+  const float *W = camf;
+  const float fx = camf[12], fy = camf[13], cx = camf[14], cy = camf[15], nearz = camf[16];
+  memset(r, 0, sizeof(*r));
+  float t[3];
+  for (int a = 0; a < 3; ++a)
+    t[a] = fmaf(W[4 * a], p[0], fmaf(W[4 * a + 1], p[1], fmaf(W[4 * a + 2], p[2], W[4 * a + 3])));
+  if (!(t[2] > nearz)) return;
+  const float tz = t[2];
+  const float u = t[0] / tz, v = t[1] / tz;
+  const float J00 = fx / tz, J02 = -(fx * u) / tz, J11 = fy / tz, J12 = -(fy * v) / tz;
+  float T[6];
+  for (int j = 0; j < 3; ++j) {
+    T[j] = fmaf(J00, W[j], J02 * W[8 + j]);
+    T[3 + j] = fmaf(J11, W[4 + j], J12 * W[8 + j]);
+  }
+  const float S[9] = {sig[0], sig[1], sig[2], sig[1], sig[3], sig[4], sig[2], sig[4], sig[5]};
+  float U[6];
+  for (int a = 0; a < 2; ++a)
+    for (int j = 0; j < 3; ++j)
+      U[3 * a + j] = fmaf(T[3 * a], S[j], fmaf(T[3 * a + 1], S[3 + j], T[3 * a + 2] * S[6 + j]));
+  const float A = fmaf(U[0], T[0], fmaf(U[1], T[1], U[2] * T[2])) + 0.3f;
+  const float B = fmaf(U[0], T[3], fmaf(U[1], T[4], U[2] * T[5]));
+  const float C = fmaf(U[3], T[3], fmaf(U[4], T[4], U[5] * T[5])) + 0.3f;
+  const float det = fmaf(A, C, -(B * B));
+  if (!(det > 0.0f)) return;
+  const float mid = 0.5f * (A + C);
+  const float disc = fmaf(mid, mid, -det);
+  const float lam = mid + sqrtf(disc > 0.1f ? disc : 0.1f);
+  const float rad = ceilf(3.0f * sqrtf(lam));
+  const float mx = fmaf(fx, u, cx), my = fmaf(fy, v, cy);
+  const float ts = (float)tile, tm1 = (float)(tile - 1);
+  float fx0 = floorf((mx - rad) / ts), fx1 = floorf(((mx + rad) + tm1) / ts);
+  float fy0 = floorf((my - rad) / ts), fy1 = floorf(((my + rad) + tm1) / ts);
+  const float TX = (float)tiles_x, TY = (float)tiles_y;
+  fx0 = fx0 < 0.0f ? 0.0f : (fx0 > TX ? TX : fx0);
+  fx1 = fx1 < 0.0f ? 0.0f : (fx1 > TX ? TX : fx1);
+  fy0 = fy0 < 0.0f ? 0.0f : (fy0 > TY ? TY : fy0);
+  fy1 = fy1 < 0.0f ? 0.0f : (fy1 > TY ? TY : fy1);
+  const int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1;
+  if (x1 <= x0 || y1 <= y0) return;
+  /* conic and opacity */
+  const float c0 = C / det, c1 = -B / det, c2 = A / det;
+  r->mx = mx; r->my = my;
+  r->h0 = -0.5f * c0; r->h1 = -c1; r->h2 = -0.5f * c2;
+  r->o = sigmoid32(logit);
+  r->x0 = x0; r->y0 = y0; r->x1 = x1; r->y1 = y1;
+  union { float f; uint32_t u; } db;
+  db.f = tz;
+  r->depth_bits = db.u;
+  r->visible = 1;
+  /* SH colour clamp decision */
+  const float dx = p[0] - camf[17], dy = p[1] - camf[18], dz = p[2] - camf[19];
+  const float l2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float nrm = sqrtf(l2);
+  const float x = dx / nrm, y = dy / nrm, z = dz / nrm;
+  float Y[OR_MAX_BASIS];
+  Y[0] = shk[0];
+  if (nb > 1) {
+    Y[1] = shk[1] * y; Y[2] = shk[2] * z; Y[3] = shk[3] * x;
+  }
+  if (nb > 4) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = shk[4] * (x * y);
+    Y[5] = shk[5] * (y * z);
+    Y[6] = shk[6] * ((2.0f * zz - xx) - yy);
+    Y[7] = shk[7] * (x * z);
+    Y[8] = shk[8] * (xx - yy);
+    if (nb > 9) {
+      Y[9] = (shk[9] * y) * (3.0f * xx - yy);
+      Y[10] = (shk[10] * (x * y)) * z;
+      Y[11] = (shk[11] * y) * ((4.0f * zz - xx) - yy);
+      Y[12] = (shk[12] * z) * ((2.0f * zz - 3.0f * xx) - 3.0f * yy);
+      Y[13] = (shk[13] * x) * ((4.0f * zz - xx) - yy);
+      Y[14] = (shk[14] * z) * (xx - yy);
+      Y[15] = (shk[15] * x) * (xx - 3.0f * yy);
+    }
+  }
+  for (int c = 0; c < 3; ++c) {
+    float acc = shrow[c] * Y[0];
+    for (int k = 1; k < nb; ++k) acc = fmaf(shrow[3 * k + c], Y[k], acc);
+    const float pre = acc + 0.5f;
+    if (pre < 0.0f) r->rgb_clamped |= 1u << c;
+  }
+}
+
+static void camera_floats(const or_camera *c, float out[20]) {
+  for (int i = 0; i < 12; ++i) out[i] = (float)c->w2c[i];
+  out[12] = (float)c->fx; out[13] = (float)c->fy; out[14] = (float)c->cx; out[15] = (float)c->cy;
+  out[16] = (float)c->near;
+  for (int i = 0; i < 3; ++i) out[17 + i] = (float)c->campos[i];
+}
+
+static int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+/* FP32 decision records for all views: rec32[v * n + g]. */
+void or_shadow32(const or_scene *s, const or_camera *cams, int n_views, int tile, or_rec32 *rec32) {
+  const int nb = (s->sh_degree + 1) * (s->sh_degree + 1);
+  float shk[OR_MAX_BASIS];
+  or_sh_consts32(shk);
+  float *sig32 = (float *)malloc(sizeof(float) * 6 * (size_t)(s->k_sr > 0 ? s->k_sr : 1));
+  for (int k = 0; k < s->k_sr; ++k) {
+    float row[8];
+    for (int i = 0; i < 8; ++i) row[i] = (float)s->sr[8 * (size_t)k + i];
+    or_sr_sigma32(row, sig32 + 6 * (size_t)k);
+  }
+  for (int v = 0; v < n_views; ++v) {
+    float camf[20];
+    camera_floats(&cams[v], camf);
+    const int tx = ceil_div(cams[v].width, tile), ty = ceil_div(cams[v].height, tile);
+#pragma omp parallel for schedule(static)
+    for (int g = 0; g < s->n; ++g) {
+      float p[3] = {(float)s->pos[3 * (size_t)g], (float)s->pos[3 * (size_t)g + 1],
+                    (float)s->pos[3 * (size_t)g + 2]};
+      float shrow[3 * OR_MAX_BASIS];
+      const double *src = s->sh + (size_t)s->g2sh[g] * 3 * nb;
+      for (int i = 0; i < 3 * nb; ++i) shrow[i] = (float)src[i];
+      shadow_one(p, (float)s->logit[g], sig32 + 6 * (size_t)s->g2sr[g], shrow, nb, camf, tile, tx, ty,
+                 shk, &rec32[(size_t)v * s->n + g]);
+    }
+  }
+  free(sig32);
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP64 projection (EWA) and colour under the FP32 decisions.                */
+/* ------------------------------------------------------------------------ */
+
+void or_preprocess64(const or_scene *s, const or_camera *cams, int n_views, const or_rec32 *rec32,
+                     or_rec64 *rec64) {
+  const int nb = (s->sh_degree + 1) * (s->sh_degree + 1);
+  for (int v = 0; v < n_views; ++v) {
+    const or_camera *c = &cams[v];
+    const double *W = c->w2c;
+#pragma omp parallel for schedule(static)
+    for (int g = 0; g < s->n; ++g) {
+      or_rec64 *r = &rec64[(size_t)v * s->n + g];
+      memset(r, 0, sizeof(*r));
+      const double *p = s->pos + 3 * (size_t)g;
+      or_sr_sigma(s->sr + 8 * (size_t)s->g2sr[g], r->sigma3);
+      for (int a = 0; a < 3; ++a) r->t[a] = W[4 * a] * p[0] + W[4 * a + 1] * p[1] + W[4 * a + 2] * p[2] + W[4 * a + 3];
+      const double tx = r->t[0], ty = r->t[1], tz = r->t[2];
+      r->opacity = 1.0 / (1.0 + exp(-s->logit[g]));
+      double dv[3] = {p[0] - c->campos[0], p[1] - c->campos[1], p[2] - c->campos[2]};
+      r->dist = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+      for (int a = 0; a < 3; ++a) r->dir[a] = dv[a] / r->dist;
+      const or_rec32 *q = &rec32[(size_t)v * s->n + g];
+      if (!q->visible) continue;
+      /* pinhole mean and its Jacobian J at t */
+      r->mean[0] = c->fx * tx / tz + c->cx;
+      r->mean[1] = c->fy * ty / tz + c->cy;
+      const double J[6] = {c->fx / tz, 0, -c->fx * tx / (tz * tz), 0, c->fy / tz, -c->fy * ty / (tz * tz)};
+      double T[6];
+      for (int a = 0; a < 2; ++a)
+        for (int j = 0; j < 3; ++j) T[3 * a + j] = J[3 * a] * W[j] + J[3 * a + 1] * W[4 + j] + J[3 * a + 2] * W[8 + j];
+      const double *sg = r->sigma3;
+      const double S[9] = {sg[0], sg[1], sg[2], sg[1], sg[3], sg[4], sg[2], sg[4], sg[5]};
+      double cov[3] = {0.3, 0.0, 0.3};
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          cov[0] += T[i] * S[3 * i + j] * T[j];
+          cov[1] += T[i] * S[3 * i + j] * T[3 + j];
+          cov[2] += T[3 + i] * S[3 * i + j] * T[3 + j];
+        }
+      for (int i = 0; i < 3; ++i) r->cov[i] = cov[i];
+      const double det = cov[0] * cov[2] - cov[1] * cov[1];
+      r->conic[0] = cov[2] / det; r->conic[1] = -cov[1] / det; r->conic[2] = cov[0] / det;
+      double Y[OR_MAX_BASIS];
+      or_sh_basis(s->sh_degree, r->dir, Y, NULL);
+      const double *row = s->sh + (size_t)s->g2sh[g] * 3 * nb;
+      for (int ch = 0; ch < 3; ++ch) {
+        double acc = 0.5;
+        for (int k = 0; k < nb; ++k) acc += row[3 * k + ch] * Y[k];
+        r->rgb[ch] = (q->rgb_clamped >> ch & 1u) ? 0.0 : acc;
+      }
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tile lists: every visible (view, Gaussian) record is listed in each tile  */
+/* of its rectangle; a tile's list is ordered by FP32 depth, ties by record. */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { uint64_t key; uint32_t rec; } or_pair;
+
+static int pair_cmp(const void *a, const void *b) {
+  const or_pair *p = (const or_pair *)a, *q = (const or_pair *)b;
+  if (p->key != q->key) return p->key < q->key ? -1 : 1;
+  return p->rec < q->rec ? -1 : (p->rec > q->rec);
+}
+
+/* Count of (tile, record) pairs. */
+int64_t or_count_pairs(const or_rec32 *rec32, int64_t n_rec) {
+  int64_t k = 0;
+  for (int64_t i = 0; i < n_rec; ++i)
+    if (rec32[i].visible) k += (int64_t)(rec32[i].x1 - rec32[i].x0) * (rec32[i].y1 - rec32[i].y0);
+  return k;
+}
+
+/* tile_base[v] = index of view v's first tile; tiles are row-major per view.
+ * Writes list[k_pairs] (record indices v*n+g), keys[k_pairs] and
+ * ranges[n_tiles][2]. */
+void or_build_lists(const or_rec32 *rec32, int n, int n_views, const int *tiles_x, const int64_t *tile_base,
+                    int64_t n_tiles, int64_t k_pairs, uint32_t *list, uint64_t *keys, uint32_t *ranges) {
+  or_pair *pairs = (or_pair *)malloc(sizeof(or_pair) * (size_t)(k_pairs > 0 ? k_pairs : 1));
+  int64_t k = 0;
+  for (int v = 0; v < n_views; ++v)
+    for (int g = 0; g < n; ++g) {
+      const or_rec32 *r = &rec32[(size_t)v * n + g];
+      if (!r->visible) continue;
+      for (int y = r->y0; y < r->y1; ++y)
+        for (int x = r->x0; x < r->x1; ++x) {
+          const uint64_t gt = (uint64_t)(tile_base[v] + (int64_t)y * tiles_x[v] + x);
+          pairs[k].key = (gt << 32) | r->depth_bits;
+          pairs[k].rec = (uint32_t)((size_t)v * n + g);
+          ++k;
+        }
+    }
+  qsort(pairs, (size_t)k, sizeof(or_pair), pair_cmp);
+  memset(ranges, 0, sizeof(uint32_t) * 2 * (size_t)n_tiles);
+  for (int64_t i = 0; i < k; ++i) {
+    list[i] = pairs[i].rec;
+    keys[i] = pairs[i].key;
+    const uint64_t t = pairs[i].key >> 32;
+    if (i == 0 || (pairs[i - 1].key >> 32) != t) ranges[2 * t] = (uint32_t)i;
+    if (i == k - 1 || (pairs[i + 1].key >> 32) != t) ranges[2 * t + 1] = (uint32_t)(i + 1);
+  }
+  free(pairs);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-pixel compositing, Eq. 3.                                             */
+/* mode 0: the rasterizer rules -- an evaluation whose FP32 alpha is below   */
+/*   1/255 is skipped, alpha is clamped at 0.99, and the pixel stops before  */
+/*   the Gaussian that would bring the FP32 transmittance below 1e-4.        */
+/* mode 1: Eq. 3 as printed: every listed Gaussian contributes o*G, no       */
+/*   threshold, no clamp, no termination.                                    */
+/* ------------------------------------------------------------------------ */
+
+#define CODE_SKIP 0
+#define CODE_ADD 1
+#define CODE_ADD_CLAMPED 2
+
+/* FP32 decision for one evaluation; *T32 is the running FP32 transmittance.
+ * Returns CODE_SKIP / CODE_ADD / CODE_ADD_CLAMPED, or -1 when the pixel stops. */
+static int decide32(const or_rec32 *q, float pxc, float pyc, float *T32) {
+  const float dx = q->mx - pxc, dy = q->my - pyc;
+  const float power = fmaf(q->h0 * dx, dx, fmaf(q->h2 * dy, dy, (q->h1 * dx) * dy));
+  if (power > 0.0f) return CODE_SKIP;
+  const float v = q->o * or_e32(power);
+  const int clamped = v > 0.99f;
+  const float alpha = clamped ? 0.99f : v;
+  if (alpha < 1.0f / 255.0f) return CODE_SKIP;
+  const float test_T = *T32 * (1.0f - alpha);
+  if (test_T < 0.0001f) return -1;
+  *T32 = test_T;
+  return clamped ? CODE_ADD_CLAMPED : CODE_ADD;
+}
+
+static double gauss64(const or_rec64 *r, double pxc, double pyc, double *dx, double *dy) {
+  *dx = r->mean[0] - pxc;
+  *dy = r->mean[1] - pyc;
+  const double power = -0.5 * (r->conic[0] * *dx * *dx + r->conic[2] * *dy * *dy) - r->conic[1] * *dx * *dy;
+  return exp(power);
+}
+
+typedef struct {
+  int width, height, tiles_x, tiles_y;
+  int64_t tile_base, pix_base;
+} view_geom;
+
+static void make_geoms(const or_camera *cams, int n_views, int tile, view_geom *vg) {
+  int64_t tb = 0, pb = 0;
+  for (int v = 0; v < n_views; ++v) {
+    vg[v].width = cams[v].width; vg[v].height = cams[v].height;
+    vg[v].tiles_x = ceil_div(cams[v].width, tile); vg[v].tiles_y = ceil_div(cams[v].height, tile);
+    vg[v].tile_base = tb; vg[v].pix_base = pb;
+    tb += (int64_t)vg[v].tiles_x * vg[v].tiles_y;
+    pb += (int64_t)cams[v].width * cams[v].height;
+  }
+}
+
+static int find_view(const view_geom *vg, int n_views, int64_t gt) {
+  int v = 0;
+  while (v + 1 < n_views && vg[v + 1].tile_base <= gt) ++v;
+  return v;
+}
+
+/* image[3 * pix_base + c * H * W + y * W + x]; t_final / n_contrib indexed
+ * by pix_base + y * W + x.  tile_mask (may be NULL) restricts the work to
+ * tiles with a non-zero byte; other pixels are left untouched. */
+void or_blend_forward(const or_camera *cams, int n_views, int tile, const double bg[3], int mode,
+                      const or_rec32 *rec32, const or_rec64 *rec64, const uint32_t *list,
+                      const uint32_t *ranges, const uint8_t *tile_mask, double *image, double *t_final,
+                      int32_t *n_contrib) {
+  view_geom vg[64];
+  make_geoms(cams, n_views, tile, vg);
+  const int64_t n_tiles = vg[n_views - 1].tile_base + (int64_t)vg[n_views - 1].tiles_x * vg[n_views - 1].tiles_y;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t gt = 0; gt < n_tiles; ++gt) {
+    if (tile_mask && !tile_mask[gt]) continue;
+    const int v = find_view(vg, n_views, gt);
+    const view_geom *G = &vg[v];
+    const int64_t lt = gt - G->tile_base;
+    const int tx = (int)(lt % G->tiles_x), ty = (int)(lt / G->tiles_x);
+    const uint32_t beg = ranges[2 * gt], end = ranges[2 * gt + 1];
+    for (int y = ty * tile; y < (ty + 1) * tile && y < G->height; ++y)
+      for (int x = tx * tile; x < (tx + 1) * tile && x < G->width; ++x) {
+        const float pxc32 = (float)x + 0.5f, pyc32 = (float)y + 0.5f;
+        const double pxc = x + 0.5, pyc = y + 0.5;
+        float T32 = 1.0f;
+        double T = 1.0, C[3] = {0, 0, 0};
+        int32_t last = 0;
+        for (uint32_t i = beg; i < end; ++i) {
+          const uint32_t rid = list[i];
+          const or_rec64 *r = &rec64[rid];
+          double dx, dy;
+          const double Gv = gauss64(r, pxc, pyc, &dx, &dy);
+          double alpha;
+          if (mode == 1) {
+            alpha = r->opacity * Gv;
+          } else {
+            const int code = decide32(&rec32[rid], pxc32, pyc32, &T32);
+            if (code < 0) break;
+            if (code == CODE_SKIP) continue;
+            alpha = code == CODE_ADD_CLAMPED ? 0.99 : r->opacity * Gv;
+          }
+          for (int c = 0; c < 3; ++c) C[c] += alpha * T * r->rgb[c];
+          T *= 1.0 - alpha;
+          last = (int32_t)(i - beg + 1);
+        }
+        const int64_t pix = G->pix_base + (int64_t)y * G->width + x;
+        const int64_t hw = (int64_t)G->width * G->height;
+        for (int c = 0; c < 3; ++c)
+          image[3 * G->pix_base + c * hw + (int64_t)y * G->width + x] = C[c] + T * bg[c];
+        t_final[pix] = T;
+        n_contrib[pix] = last;
+      }
+  }
+}
+
+/* Backward of Eq. 3 per pixel, accumulated per (view, Gaussian) record:
+ * grad9[rec][9] = dL/d(mean_x, mean_y, conic0, conic1, conic2, opacity, r, g, b).
+ * The pixel's contributions are gathered front to back under the same
+ * decisions as the forward, then differentiated exactly. */
+void or_blend_backward(const or_camera *cams, int n_views, int tile, const double bg[3], int mode,
+                       const or_rec32 *rec32, const or_rec64 *rec64, const uint32_t *list,
+                       const uint32_t *ranges, const uint8_t *tile_mask, const double *d_image,
+                       int64_t n_rec, double *grad9) {
+  view_geom vg[64];
+  make_geoms(cams, n_views, tile, vg);
+  const int64_t n_tiles = vg[n_views - 1].tile_base + (int64_t)vg[n_views - 1].tiles_x * vg[n_views - 1].tiles_y;
+  memset(grad9, 0, sizeof(double) * 9 * (size_t)n_rec);
+  /* one accumulator row per (tile, list position), summed per record after */
+  int64_t total = 0;
+  for (int64_t gt = 0; gt < n_tiles; ++gt)
+    if (ranges[2 * gt + 1] > (uint32_t)total) total = ranges[2 * gt + 1];
+  double *pair = (double *)calloc((size_t)(total > 0 ? total : 1) * 9, sizeof(double));
+#pragma omp parallel
+  {
+    int cap = 0;
+    int *idx = NULL;
+    double *alph = NULL, *Gs = NULL, *Ts = NULL;
+    int *clampf = NULL;
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t gt = 0; gt < n_tiles; ++gt) {
+      if (tile_mask && !tile_mask[gt]) continue;
+      const int v = find_view(vg, n_views, gt);
+      const view_geom *G = &vg[v];
+      const int64_t lt = gt - G->tile_base;
+      const int tx = (int)(lt % G->tiles_x), ty = (int)(lt / G->tiles_x);
+      const uint32_t beg = ranges[2 * gt], end = ranges[2 * gt + 1];
+      const int len = (int)(end - beg);
+      if (len > cap) {
+        cap = len;
+        idx = (int *)realloc(idx, sizeof(int) * cap);
+        alph = (double *)realloc(alph, sizeof(double) * cap);
+        Gs = (double *)realloc(Gs, sizeof(double) * cap);
+        Ts = (double *)realloc(Ts, sizeof(double) * cap);
+        clampf = (int *)realloc(clampf, sizeof(int) * cap);
+      }
+      const int64_t hw = (int64_t)G->width * G->height;
+      for (int y = ty * tile; y < (ty + 1) * tile && y < G->height; ++y)
+        for (int x = tx * tile; x < (tx + 1) * tile && x < G->width; ++x) {
+          const float pxc32 = (float)x + 0.5f, pyc32 = (float)y + 0.5f;
+          const double pxc = x + 0.5, pyc = y + 0.5;
+          float T32 = 1.0f;
+          double T = 1.0;
+          int m = 0;
+          for (uint32_t i = beg; i < end; ++i) {
+            const uint32_t rid = list[i];
+            const or_rec64 *r = &rec64[rid];
+            double dx, dy;
+            const double Gv = gauss64(r, pxc, pyc, &dx, &dy);
+            double alpha;
+            int clamped = 0;
+            if (mode == 1) {
+              alpha = r->opacity * Gv;
+            } else {
+              const int code = decide32(&rec32[rid], pxc32, pyc32, &T32);
+              if (code < 0) break;
+              if (code == CODE_SKIP) continue;
+              clamped = code == CODE_ADD_CLAMPED;
+              alpha = clamped ? 0.99 : r->opacity * Gv;
+            }
+            idx[m] = (int)(i - beg); alph[m] = alpha; Gs[m] = Gv; Ts[m] = T; clampf[m] = clamped;
+            ++m;
+            T *= 1.0 - alpha;
+          }
+          double dC[3];
+          for (int c = 0; c < 3; ++c) dC[c] = d_image[3 * G->pix_base + c * hw + (int64_t)y * G->width + x];
+          /* behind[c] = sum_{j>k} alpha_j T_j c_j + T_final bg, built back to front */
+          double behind[3] = {T * bg[0], T * bg[1], T * bg[2]};
+          for (int k = m - 1; k >= 0; --k) {
+            const uint32_t rid = list[beg + idx[k]];
+            const or_rec64 *r = &rec64[rid];
+            const double a = alph[k], Tk = Ts[k];
+            double *acc = pair + 9 * (size_t)(beg + idx[k]);
+            double dalpha = 0;
+            for (int c = 0; c < 3; ++c) {
+              acc[6 + c] += a * Tk * dC[c];
+              dalpha += (Tk * r->rgb[c] - behind[c] / (1.0 - a)) * dC[c];
+            }
+            for (int c = 0; c < 3; ++c) behind[c] += a * Tk * r->rgb[c];
+            if (!clampf[k]) {
+              /* alpha = o * exp(power) */
+              const double dx = r->mean[0] - pxc, dy = r->mean[1] - pyc;
+              acc[5] += Gs[k] * dalpha;
+              const double dpow = a * dalpha;
+              acc[0] += dpow * (-r->conic[0] * dx - r->conic[1] * dy);
+              acc[1] += dpow * (-r->conic[2] * dy - r->conic[1] * dx);
+              acc[2] += dpow * (-0.5 * dx * dx);
+              acc[3] += dpow * (-dx * dy);
+              acc[4] += dpow * (-0.5 * dy * dy);
+            }
+          }
+        }
+    }
+    free(idx); free(alph); free(Gs); free(Ts); free(clampf);
+  }
+  for (int64_t i = 0; i < total; ++i) {
+    const uint32_t rid = list[i];
+    for (int e = 0; e < 9; ++e) grad9[9 * (size_t)rid + e] += pair[9 * (size_t)i + e];
+  }
+  free(pair);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Backward of the projection, the colour and the opacity per Gaussian.      */
+/* Outputs: dpos[n][3], dlogit[n], dsigma[n][6] (summed over views, w.r.t.   */
+/* the six unique entries of Sigma), drgb[n_views*n][3] (after the clamp     */
+/* mask, per view: the SH codebook reduction needs it with the direction).   */
+/* ------------------------------------------------------------------------ */
+
+void or_preprocess_backward(const or_scene *s, const or_camera *cams, int n_views, const or_rec32 *rec32,
+                            const or_rec64 *rec64, const double *grad9, double *dpos, double *dlogit,
+                            double *dsigma, double *drgb) {
+  const int nb = (s->sh_degree + 1) * (s->sh_degree + 1);
+#pragma omp parallel for schedule(static)
+  for (int g = 0; g < s->n; ++g) {
+    double dp[3] = {0, 0, 0}, dl = 0, dsg[6] = {0, 0, 0, 0, 0, 0};
+    for (int v = 0; v < n_views; ++v) {
+      const size_t rid = (size_t)v * s->n + g;
+      const or_rec32 *q = &rec32[rid];
+      const or_rec64 *r = &rec64[rid];
+      double *drgb_out = drgb + 3 * rid;
+      drgb_out[0] = drgb_out[1] = drgb_out[2] = 0;
+      if (!q->visible) continue;
+      const double *gr = grad9 + 9 * rid;
+      const or_camera *c = &cams[v];
+      const double *W = c->w2c;
+      /* opacity */
+      dl += gr[5] * r->opacity * (1.0 - r->opacity);
+      /* colour: clamp mask, then the view direction */
+      double dY[OR_MAX_BASIS * 3], Y[OR_MAX_BASIS];
+      or_sh_basis(s->sh_degree, r->dir, Y, dY);
+      const double *row = s->sh + (size_t)s->g2sh[g] * 3 * nb;
+      double ddir[3] = {0, 0, 0};
+      for (int ch = 0; ch < 3; ++ch) {
+        const double d = (q->rgb_clamped >> ch & 1u) ? 0.0 : gr[6 + ch];
+        drgb_out[ch] = d;
+        for (int k = 0; k < nb; ++k)
+          for (int a = 0; a < 3; ++a) ddir[a] += d * row[3 * k + ch] * dY[3 * k + a];
+      }
+      const double dd = ddir[0] * r->dir[0] + ddir[1] * r->dir[1] + ddir[2] * r->dir[2];
+      for (int a = 0; a < 3; ++a) dp[a] += (ddir[a] - r->dir[a] * dd) / r->dist;
+      /* conic -> 2D covariance */
+      const double a = r->cov[0], b = r->cov[1], cc = r->cov[2];
+      const double det = a * cc - b * b, det2 = det * det;
+      const double g0 = gr[2], g1 = gr[3], g2 = gr[4];
+      const double da = (-g0 * cc * cc + g1 * b * cc - g2 * b * b) / det2;
+      const double db = (2 * g0 * b * cc - g1 * (a * cc + b * b) + 2 * g2 * a * b) / det2;
+      const double dc = (-g0 * b * b + g1 * a * b - g2 * a * a) / det2;
+      /* 2D covariance = T Sigma T^T with T = J R_w */
+      const double tx = r->t[0], ty = r->t[1], tz = r->t[2];
+      const double J[6] = {c->fx / tz, 0, -c->fx * tx / (tz * tz), 0, c->fy / tz, -c->fy * ty / (tz * tz)};
+      double T[6];
+      for (int aa = 0; aa < 2; ++aa)
+        for (int j = 0; j < 3; ++j)
+          T[3 * aa + j] = J[3 * aa] * W[j] + J[3 * aa + 1] * W[4 + j] + J[3 * aa + 2] * W[8 + j];
+      const double *sg = r->sigma3;
+      const double S[9] = {sg[0], sg[1], sg[2], sg[1], sg[3], sg[4], sg[2], sg[4], sg[5]};
+      double ST0[3], ST1[3];
+      for (int i = 0; i < 3; ++i) {
+        ST0[i] = S[3 * i] * T[0] + S[3 * i + 1] * T[1] + S[3 * i + 2] * T[2];
+        ST1[i] = S[3 * i] * T[3] + S[3 * i + 1] * T[4] + S[3 * i + 2] * T[5];
+      }
+      double dT[6];
+      for (int j = 0; j < 3; ++j) {
+        dT[j] = 2 * da * ST0[j] + db * ST1[j];
+        dT[3 + j] = db * ST0[j] + 2 * dc * ST1[j];
+      }
+      static const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+      for (int e = 0; e < 6; ++e) {
+        const int i = ia[e], j = ib[e];
+        double f = da * T[i] * T[j] + db * T[i] * T[3 + j] + dc * T[3 + i] * T[3 + j];
+        if (i != j) f += da * T[j] * T[i] + db * T[j] * T[3 + i] + dc * T[3 + j] * T[3 + i];
+        dsg[e] += f;
+      }
+      /* T = J R_w  =>  dJ = dT R_w^T */
+      double dJ[6];
+      for (int aa = 0; aa < 2; ++aa)
+        for (int k = 0; k < 3; ++k)
+          dJ[3 * aa + k] = dT[3 * aa] * W[4 * k] + dT[3 * aa + 1] * W[4 * k + 1] + dT[3 * aa + 2] * W[4 * k + 2];
+      const double fx = c->fx, fy = c->fy;
+      double dt[3];
+      dt[0] = -fx / (tz * tz) * dJ[2] + fx / tz * gr[0];
+      dt[1] = -fy / (tz * tz) * dJ[5] + fy / tz * gr[1];
+      dt[2] = -fx / (tz * tz) * dJ[0] + 2 * fx * tx / (tz * tz * tz) * dJ[2] - fy / (tz * tz) * dJ[4] +
+              2 * fy * ty / (tz * tz * tz) * dJ[5] - fx * tx / (tz * tz) * gr[0] - fy * ty / (tz * tz) * gr[1];
+      /* t = R_w p + t_w */
+      for (int k = 0; k < 3; ++k) dp[k] += W[k] * dt[0] + W[4 + k] * dt[1] + W[8 + k] * dt[2];
+    }
+    for (int a = 0; a < 3; ++a) dpos[3 * (size_t)g + a] = dp[a];
+    dlogit[g] = dl;
+    for (int e = 0; e < 6; ++e) dsigma[6 * (size_t)g + e] = dsg[e];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Codebook gradients: a row's gradient is the sum over the Gaussians that   */
+/* index it (g2sr / g2sh, Sec. 3.1), pushed through Eq. 2 for SR rows and    */
+/* through the SH basis for SH rows.                                         */
+/* ------------------------------------------------------------------------ */
+
+void or_codebook_reduce(const or_scene *s, int n_views, const or_rec64 *rec64, const double *dsigma,
+                        const double *drgb, double *d_sr, double *d_sh) {
+  const int nb = (s->sh_degree + 1) * (s->sh_degree + 1);
+  double *sum_sigma = (double *)calloc((size_t)(s->k_sr > 0 ? s->k_sr : 1) * 6, sizeof(double));
+  memset(d_sh, 0, sizeof(double) * (size_t)s->k_sh * nb * 3);
+  for (int g = 0; g < s->n; ++g) {
+    for (int e = 0; e < 6; ++e) sum_sigma[6 * (size_t)s->g2sr[g] + e] += dsigma[6 * (size_t)g + e];
+    for (int v = 0; v < n_views; ++v) {
+      const size_t rid = (size_t)v * s->n + g;
+      double Y[OR_MAX_BASIS];
+      or_sh_basis(s->sh_degree, rec64[rid].dir, Y, NULL);
+      double *dst = d_sh + (size_t)s->g2sh[g] * nb * 3;
+      for (int k = 0; k < nb; ++k)
+        for (int c = 0; c < 3; ++c) dst[3 * k + c] += Y[k] * drgb[3 * rid + c];
+    }
+  }
+  for (int k = 0; k < s->k_sr; ++k) or_sr_sigma_backward(s->sr + 8 * (size_t)k, sum_sigma + 6 * (size_t)k, d_sr + 8 * (size_t)k);
+  free(sum_sigma);
+}
