@@ -1,0 +1,191 @@
+/*
+ * cg.h -- C ABI of the codebook Gaussian-splatting rasterizer for GB300
+ * (sm_103a).  libcg.so implements it; every stage runs in hand-written
+ * CUDA kernels of that library.
+ *
+ * The method (ContraGS, arXiv 2509.03775):
+ *   State S = {G, C} (Sec. 3.1).  A Gaussian g_i = {p_i, o_i, g2sr_i, g2sh_i}
+ *   holds a position, an opacity and two integer indices; its scale and
+ *   rotation come from row g2sr_i of the SR codebook ("scaling + quaternion
+ *   concatenated", Fig. 4) and its SH colour coefficients from row g2sh_i of
+ *   the SH codebook.  The image I_P(G, C) of camera P (the posterior of
+ *   Sec. 3.2 is a function of it) is Eq. 3 over Gaussians whose density is
+ *   Eq. 1 with the covariance of Eq. 2, projected onto the image plane.
+ *   Training updates p, o, SH and SR with the gradient of the loss
+ *   (Sec. 3.4, "S_diff", and the SGLD steps of Appendix A.1); a codebook
+ *   row's gradient is the sum over the Gaussians that index it.
+ *
+ * Conventions shared by every call:
+ *   - All array arguments are DEVICE pointers unless marked "host".  The
+ *     caller allocates and owns every buffer, including the workspace; the
+ *     library allocates no memory and keeps no state between calls outside
+ *     the workspace.
+ *   - Every call is asynchronous on `stream` and launches kernels only, so
+ *     a sequence of calls can be captured in a CUDA graph.
+ *   - Gradient outputs are overwritten, never accumulated.  Inputs are never
+ *     modified.
+ *   - Host-detectable argument problems return an error before anything is
+ *     launched.  Problems found on the device (an index >= K, more
+ *     (tile, Gaussian) pairs than the workspace holds) set a status word in
+ *     the workspace, read back by cg_last_device_status; the kernels never
+ *     read or write out of bounds because of them.
+ */
+#ifndef CG_H_
+#define CG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (binary compatible); 0 is the legacy default stream. */
+typedef struct CUstream_st *cg_stream_t;
+
+typedef enum {
+  CG_OK = 0,
+  CG_ERR_ARG = 1,      /* null / misaligned pointer, bad size or option */
+  CG_ERR_INDEX = 2,    /* device: g2sr >= k_sr or g2sh >= k_sh (Gaussian culled) */
+  CG_ERR_CAPACITY = 3, /* device: more pairs than pair_capacity (nothing rendered) */
+  CG_ERR_TIMEOUT = 4,  /* device: a bounded loop gave up */
+  CG_ERR_CUDA = 5      /* a CUDA runtime call failed */
+} cg_status;
+
+typedef enum { CG_F32 = 0, CG_BF16 = 1 } cg_dtype;
+
+#define CG_MAX_VIEWS 64
+#define CG_SR_WIDTH 8
+
+/* Pinhole camera, OpenCV axes (x right, y down, z forward).  A point p maps
+ * to t = R p + t_w with world_to_cam = [R | t_w] (row-major 3x4) and to the
+ * pixel (fx t_x / t_z + cx, fy t_y / t_z + cy); pixel (x, y) has its centre
+ * at (x + 0.5, y + 0.5).  campos is the eye point (used for the viewing
+ * direction of the SH colour).  Points with t_z <= near_z are culled. */
+typedef struct {
+  int width, height;
+  float fx, fy, cx, cy;
+  float world_to_cam[12];
+  float campos[3];
+  float near_z;
+} cg_camera;
+
+/* The state S = {G, C} of Sec. 3.1.  Device pointers:
+ *   pos            [n][3] float
+ *   opacity_logit  [n] float          o_i = sigmoid(logit_i)
+ *   g2sr, g2sh     [n] uint16
+ *   sr_rows        [k_sr][8] of cb_dtype: log-scale x3, quaternion (w,x,y,z),
+ *                  one pad entry (ignored)
+ *   sh_rows        [k_sh][(sh_degree+1)^2][3] of cb_dtype
+ * n >= 1, 1 <= k_sr, k_sh <= 65536, 0 <= sh_degree <= 3.  BF16 rows are
+ * widened to FP32 exactly; all arithmetic is FP32. */
+typedef struct {
+  int n, k_sr, k_sh, sh_degree;
+  cg_dtype cb_dtype;
+  const float *pos;
+  const float *opacity_logit;
+  const uint16_t *g2sr;
+  const uint16_t *g2sh;
+  const void *sr_rows;
+  const void *sh_rows;
+} cg_scene;
+
+/* tile: 8, 16 or 32 pixels (square tiles; the tile size changes which
+ * Gaussians a tile lists, so it is part of the image definition).
+ * batch: Gaussians staged in shared memory per step of the blend kernels,
+ * 0 = default; one of 32, 64, 128, 256.  bg: background colour added with
+ * the final transmittance.  pair_capacity: (tile, Gaussian) pairs the
+ * workspace has room for (1 <= pair_capacity < 2^32); every call on a
+ * workspace must pass the value it was sized with. */
+typedef struct {
+  int tile;
+  int batch;
+  float bg[3];
+  uint32_t pair_capacity;
+} cg_opts;
+
+/* Workspace bytes for rendering `n_views` cameras (host array) of `scene`
+ * with these options.  Returns 0 for invalid arguments. */
+size_t cg_workspace_bytes(const cg_scene *scene, const cg_camera *cams, int n_views, const cg_opts *opts);
+
+/* Forward render I_P(G, C) of every view (Eqs. 1-3, Sec. 3.1 indirection):
+ * codebook gather, Eq. 2, EWA projection, SH colour, tile/depth keys, radix
+ * sort, per-tile front-to-back compositing.
+ *   cams      host array of n_views cameras (1 <= n_views <= CG_MAX_VIEWS)
+ *   images    device float, views packed one after the other, each [3][H][W]
+ * The workspace keeps what the backward needs (per-Gaussian records, sorted
+ * pairs, final transmittance and contributor counts per pixel). */
+cg_status cg_render_fwd(const cg_scene *scene, const cg_camera *cams, int n_views, const cg_opts *opts,
+                        void *workspace, size_t ws_bytes, float *images, cg_stream_t stream);
+
+/* Backward of the last cg_render_fwd on this workspace (same scene, cameras,
+ * options): reverse-order compositing recomputing the blend state, then the
+ * projection / colour / opacity backward per Gaussian.
+ *   d_images          dL/dimages, same layout as images
+ *   d_pos             [n][3] dL/dp (summed over views)
+ *   d_opacity_logit   [n]    dL/dlogit
+ * Per-Gaussian covariance and colour gradients stay in the workspace for
+ * cg_codebook_reduce.  Deterministic: no floating-point atomics. */
+cg_status cg_render_bwd(const cg_scene *scene, const cg_camera *cams, int n_views, const cg_opts *opts,
+                        void *workspace, size_t ws_bytes, const float *d_images, float *d_pos,
+                        float *d_opacity_logit, cg_stream_t stream);
+
+/* Codebook gradients after cg_render_bwd: each row's gradient is the sum,
+ * over the Gaussians that index it (and over views for SH), of their
+ * per-Gaussian terms, pushed through Eq. 2 (SR) or the SH basis (SH).  The
+ * sums run in a fixed order (members in Gaussian-index order, fixed chunks,
+ * fixed tree), so results are bitwise reproducible.
+ *   d_sr_rows   [k_sr][8] float (entry 7 is written as 0)
+ *   d_sh_rows   [k_sh][(sh_degree+1)^2][3] float */
+cg_status cg_codebook_reduce(const cg_scene *scene, const cg_camera *cams, int n_views, const cg_opts *opts,
+                             void *workspace, size_t ws_bytes, float *d_sr_rows, float *d_sh_rows,
+                             cg_stream_t stream);
+
+/* Synchronises `stream` and returns the device status of the workspace
+ * (CG_OK, CG_ERR_INDEX or CG_ERR_CAPACITY).  *pairs_out (host, may be NULL)
+ * receives the pair count of the last forward, which is also the capacity
+ * needed when the status is CG_ERR_CAPACITY. */
+cg_status cg_last_device_status(void *workspace, size_t ws_bytes, cg_stream_t stream, uint64_t *pairs_out);
+
+/* L1 loss of Eq. 4's first term as a test harness: *loss_out (device, one
+ * double) = mean |image - target| over `count` values, d_image = sign(image -
+ * target) / count.  Fixed-order reduction.  Uses the workspace's scratch. */
+cg_status cg_l1_loss(const float *image, const float *target, int64_t count, float *d_image, double *loss_out,
+                     void *workspace, size_t ws_bytes, cg_stream_t stream);
+
+/* Internal arrays of the workspace, for inspection by tests (device pointer
+ * and element count written to the host outputs).  Layouts:
+ *   CG_WS_RECT        [V*n] uint16x4  tile rectangle x0, y0, x1, y1 (x1 == x0 when culled)
+ *   CG_WS_DEPTH       [V*n] uint32    IEEE bits of the FP32 camera depth
+ *   CG_WS_PAIRS       [K]   uint64    sorted (global tile << 32) | (v*n + g)
+ *   CG_WS_RANGES      [T]   uint32x2  [start, end) of each global tile in the pairs
+ *   CG_WS_NCONTRIB    [P]   uint32    position after the last contributor, per pixel
+ *   CG_WS_TFINAL      [P]   float     final transmittance per pixel
+ *   CG_WS_DSIGMA      [n]   float x6  dL/dSigma per Gaussian (unique entries 00 01 02 11 12 22)
+ *   CG_WS_DRGB        [V*n] float x3  dL/dcolour per view and Gaussian, after the clamp mask
+ *   CG_WS_GEO         [V*n] float x8  mean x, y, -c0/2, -c1, -c2/2, opacity, skip bound, 0
+ *   CG_WS_RGB         [V*n] float x4  colour r, g, b, clamp mask bits
+ *   CG_WS_SIGMA3      [k_sr] float x6 Sigma of each SR row (Eq. 2, FP32) */
+typedef enum {
+  CG_WS_RECT = 0, CG_WS_DEPTH, CG_WS_PAIRS, CG_WS_RANGES, CG_WS_NCONTRIB, CG_WS_TFINAL,
+  CG_WS_DSIGMA, CG_WS_DRGB, CG_WS_GEO, CG_WS_RGB, CG_WS_SIGMA3
+} cg_ws_array;
+cg_status cg_workspace_array(void *workspace, size_t ws_bytes, cg_ws_array which, void **ptr_out,
+                             uint64_t *count_out);
+
+/* Host-side twins of the FP32 decision arithmetic compiled from the same
+ * source as the kernels, so it can be checked without a GPU:
+ *   cg_host_exp32       the binary32 exp of the decision arithmetic
+ *   cg_host_sh_consts   the 16 SH basis constants (with signs) in FP32
+ *   cg_host_sigma3      Eq. 2 of one SR row (8 floats) -> 6 floats */
+float cg_host_exp32(float x);
+void cg_host_sh_consts(float out[16]);
+void cg_host_sigma3(const float row[8], float out[6]);
+
+/* Library version string. */
+const char *cg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CG_H_ */

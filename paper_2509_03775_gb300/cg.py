@@ -1,0 +1,340 @@
+"""ctypes binding of libcg (include/cg.h): argument marshalling only.
+
+Every step of the render runs in the library's CUDA kernels; this module
+turns torch tensors into device pointers, owns the workspace tensor and the
+stream handle, and raises if the library is missing or a call fails.  There
+is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcg.so")
+
+CG_OK, CG_ERR_ARG, CG_ERR_INDEX, CG_ERR_CAPACITY, CG_ERR_TIMEOUT, CG_ERR_CUDA = range(6)
+STATUS_NAMES = {0: "CG_OK", 1: "CG_ERR_ARG", 2: "CG_ERR_INDEX", 3: "CG_ERR_CAPACITY", 4: "CG_ERR_TIMEOUT",
+                5: "CG_ERR_CUDA"}
+CG_F32, CG_BF16 = 0, 1
+MAX_VIEWS = 64
+
+WS_RECT, WS_DEPTH, WS_PAIRS, WS_RANGES, WS_NCONTRIB, WS_TFINAL, WS_DSIGMA, WS_DRGB, WS_GEO, WS_RGB, WS_SIGMA3 = \
+    range(11)
+
+# every symbol include/cg.h declares
+EXPORTS = ["cg_workspace_bytes", "cg_render_fwd", "cg_render_bwd", "cg_codebook_reduce", "cg_last_device_status",
+           "cg_l1_loss", "cg_workspace_array", "cg_host_exp32", "cg_host_sh_consts", "cg_host_sigma3", "cg_version"]
+
+
+class CgError(RuntimeError):
+    def __init__(self, call: str, status: int):
+        super().__init__(f"{call} returned {STATUS_NAMES.get(status, status)}")
+        self.status = status
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("world_to_cam", ctypes.c_float * 12),
+                ("campos", ctypes.c_float * 3), ("near_z", ctypes.c_float)]
+
+
+class Scene(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("k_sr", ctypes.c_int), ("k_sh", ctypes.c_int), ("sh_degree", ctypes.c_int),
+                ("cb_dtype", ctypes.c_int), ("pos", ctypes.c_void_p), ("opacity_logit", ctypes.c_void_p),
+                ("g2sr", ctypes.c_void_p), ("g2sh", ctypes.c_void_p), ("sr_rows", ctypes.c_void_p),
+                ("sh_rows", ctypes.c_void_p)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int), ("batch", ctypes.c_int), ("bg", ctypes.c_float * 3),
+                ("pair_capacity", ctypes.c_uint32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libcg.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libcg.so not found at {p}: build it with paper_2509_03775_gb300._build.build()")
+        L = ctypes.CDLL(p)
+        P = ctypes.c_void_p
+        L.cg_workspace_bytes.argtypes = [P, P, ctypes.c_int, P]
+        L.cg_workspace_bytes.restype = ctypes.c_size_t
+        L.cg_render_fwd.argtypes = [P, P, ctypes.c_int, P, P, ctypes.c_size_t, P, P]
+        L.cg_render_bwd.argtypes = [P, P, ctypes.c_int, P, P, ctypes.c_size_t, P, P, P, P]
+        L.cg_codebook_reduce.argtypes = [P, P, ctypes.c_int, P, P, ctypes.c_size_t, P, P, P]
+        L.cg_last_device_status.argtypes = [P, ctypes.c_size_t, P, ctypes.POINTER(ctypes.c_uint64)]
+        L.cg_l1_loss.argtypes = [P, P, ctypes.c_int64, P, P, P, ctypes.c_size_t, P]
+        L.cg_workspace_array.argtypes = [P, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                         ctypes.POINTER(ctypes.c_uint64)]
+        L.cg_host_exp32.argtypes = [ctypes.c_float]
+        L.cg_host_exp32.restype = ctypes.c_float
+        L.cg_host_sh_consts.argtypes = [P]
+        L.cg_host_sigma3.argtypes = [P, P]
+        L.cg_version.restype = ctypes.c_char_p
+        for name in ("cg_render_fwd", "cg_render_bwd", "cg_codebook_reduce", "cg_last_device_status", "cg_l1_loss",
+                     "cg_workspace_array"):
+            getattr(L, name).restype = ctypes.c_int
+        if path is None:
+            _lib = L
+        return L
+
+
+def _check(call: str, status: int):
+    if status != CG_OK:
+        raise CgError(call, status)
+
+
+def make_camera(cam) -> Camera:
+    c = Camera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    w = np.asarray(cam.world_to_cam, dtype=np.float32).ravel()
+    for i in range(12):
+        c.world_to_cam[i] = float(w[i])
+    for i in range(3):
+        c.campos[i] = float(np.float32(cam.campos[i]))
+    c.near_z = float(cam.near)
+    return c
+
+
+def camera_array(cams: Sequence) -> ctypes.Array:
+    if not 1 <= len(cams) <= MAX_VIEWS:
+        raise ValueError(f"1..{MAX_VIEWS} views")
+    arr = (Camera * len(cams))()
+    for i, cam in enumerate(cams):
+        arr[i] = make_camera(cam)
+    return arr
+
+
+def _stream_ptr(stream: torch.cuda.Stream | None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class SceneTensors:
+    """Device tensors of the state S = {G, C}.  Indices are stored in int16
+    tensors holding the uint16 bit patterns."""
+
+    def __init__(self, pos, opacity_logit, g2sr, g2sh, sr_rows, sh_rows, sh_degree: int):
+        self.pos = pos
+        self.opacity_logit = opacity_logit
+        self.g2sr = g2sr
+        self.g2sh = g2sh
+        self.sr_rows = sr_rows
+        self.sh_rows = sh_rows
+        self.sh_degree = int(sh_degree)
+
+    @classmethod
+    def from_scene(cls, scene, device="cuda", codebook_dtype: torch.dtype = torch.float32):
+        """Copy a numpy scene (scenes.Scene) to the device."""
+        def t(a, dt=torch.float32):
+            return torch.from_numpy(np.ascontiguousarray(a)).to(device=device, dtype=dt)
+
+        if codebook_dtype == torch.bfloat16:
+            from .scenes import bf16_bits
+            sr = torch.from_numpy(bf16_bits(scene.sr_rows).view(np.int16)).to(device).view(torch.bfloat16)
+            sh = torch.from_numpy(bf16_bits(scene.sh_rows).view(np.int16)).to(device).view(torch.bfloat16)
+        else:
+            sr, sh = t(scene.sr_rows), t(scene.sh_rows)
+        return cls(t(scene.pos), t(scene.opacity_logit),
+                   torch.from_numpy(np.ascontiguousarray(scene.g2sr).view(np.int16)).to(device),
+                   torch.from_numpy(np.ascontiguousarray(scene.g2sh).view(np.int16)).to(device),
+                   sr.contiguous(), sh.contiguous(), scene.sh_degree)
+
+    @property
+    def n(self) -> int:
+        return int(self.pos.shape[0])
+
+    def struct(self) -> Scene:
+        for name in ("pos", "opacity_logit", "g2sr", "g2sh", "sr_rows", "sh_rows"):
+            tt = getattr(self, name)
+            if not tt.is_cuda or not tt.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous CUDA tensor")
+        if self.sr_rows.dtype != self.sh_rows.dtype or self.sr_rows.dtype not in (torch.float32, torch.bfloat16):
+            raise ValueError("codebooks must both be float32 or both bfloat16")
+        return Scene(self.n, int(self.sr_rows.shape[0]), int(self.sh_rows.shape[0]), self.sh_degree,
+                     CG_BF16 if self.sr_rows.dtype == torch.bfloat16 else CG_F32,
+                     self.pos.data_ptr(), self.opacity_logit.data_ptr(), self.g2sr.data_ptr(),
+                     self.g2sh.data_ptr(), self.sr_rows.data_ptr(), self.sh_rows.data_ptr())
+
+
+class Renderer:
+    """Workspace owner for one scene size and one camera set.
+
+    forward() -> packed images [sum_v 3*H_v*W_v]; backward(d_images) ->
+    (d_pos, d_logit); codebook_reduce() -> (d_sr_rows, d_sh_rows).  The
+    workspace holds the state of the last forward: call backward before the
+    next forward.  The pair capacity grows (and the forward is re-run) when
+    a forward reports CG_ERR_CAPACITY, unless check=False.
+    """
+
+    def __init__(self, cams: Sequence, tile: int = 16, batch: int = 0, bg=(0.0, 0.0, 0.0),
+                 pair_capacity: int = 1 << 20, device: str | torch.device = "cuda"):
+        self.lib = load()
+        self.cams = list(cams)
+        self._cams = camera_array(self.cams)
+        self.tile, self.batch = int(tile), int(batch)
+        self.bg = tuple(float(b) for b in bg)
+        self.pair_capacity = int(pair_capacity)
+        self.device = torch.device(device)
+        self.ws = None
+        self.ws_bytes = 0
+        self._key = None
+        self.pixels = sum(c.width * c.height for c in self.cams)
+
+    def opts(self) -> Opts:
+        o = Opts()
+        o.tile, o.batch = self.tile, self.batch
+        for i in range(3):
+            o.bg[i] = self.bg[i]
+        o.pair_capacity = self.pair_capacity
+        return o
+
+    def _ensure(self, sc: Scene):
+        key = (sc.n, sc.k_sr, sc.k_sh, sc.sh_degree, self.pair_capacity)
+        if self._key == key and self.ws is not None:
+            return
+        o = self.opts()
+        nbytes = self.lib.cg_workspace_bytes(ctypes.byref(sc), self._cams, len(self.cams), ctypes.byref(o))
+        if nbytes == 0:
+            raise CgError("cg_workspace_bytes", CG_ERR_ARG)
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.ws.data_ptr()) % 256
+        self._ws_ptr = ctypes.c_void_p(self.ws.data_ptr() + off)
+        self.ws_bytes = nbytes
+        self._key = key
+
+    def workspace_bytes(self, scene: SceneTensors) -> int:
+        sc = scene.struct()
+        o = self.opts()
+        return int(self.lib.cg_workspace_bytes(ctypes.byref(sc), self._cams, len(self.cams), ctypes.byref(o)))
+
+    def status(self, stream=None) -> tuple[int, int]:
+        pairs = ctypes.c_uint64(0)
+        st = self.lib.cg_last_device_status(self._ws_ptr, self.ws_bytes, _stream_ptr(stream), ctypes.byref(pairs))
+        return int(st), int(pairs.value)
+
+    def forward(self, scene: SceneTensors, images: torch.Tensor | None = None, check: bool = True,
+                stream=None) -> torch.Tensor:
+        sc = scene.struct()
+        self._scene = scene
+        for _ in range(3):
+            self._ensure(sc)
+            if images is None:
+                images = torch.empty(3 * self.pixels, dtype=torch.float32, device=self.device)
+            o = self.opts()
+            _check("cg_render_fwd", self.lib.cg_render_fwd(ctypes.byref(sc), self._cams, len(self.cams),
+                                                           ctypes.byref(o), self._ws_ptr, self.ws_bytes,
+                                                           _ptr(images), _stream_ptr(stream)))
+            if not check:
+                return images
+            st, pairs = self.status(stream)
+            if st == CG_ERR_CAPACITY:
+                self.pair_capacity = min((1 << 32) - 1, int(pairs * 1.25) + 1024)
+                continue
+            _check("device status", st)
+            self.last_pairs = pairs
+            return images
+        raise CgError("cg_render_fwd", CG_ERR_CAPACITY)
+
+    def backward(self, d_images: torch.Tensor, d_pos: torch.Tensor | None = None,
+                 d_logit: torch.Tensor | None = None, stream=None):
+        sc = self._scene.struct()
+        n = sc.n
+        d_images = d_images.contiguous().float()
+        if d_pos is None:
+            d_pos = torch.empty((n, 3), dtype=torch.float32, device=self.device)
+        if d_logit is None:
+            d_logit = torch.empty((n,), dtype=torch.float32, device=self.device)
+        o = self.opts()
+        _check("cg_render_bwd", self.lib.cg_render_bwd(ctypes.byref(sc), self._cams, len(self.cams), ctypes.byref(o),
+                                                       self._ws_ptr, self.ws_bytes, _ptr(d_images), _ptr(d_pos),
+                                                       _ptr(d_logit), _stream_ptr(stream)))
+        return d_pos, d_logit
+
+    def codebook_reduce(self, d_sr: torch.Tensor | None = None, d_sh: torch.Tensor | None = None, stream=None):
+        sc = self._scene.struct()
+        nb = (sc.sh_degree + 1) ** 2
+        if d_sr is None:
+            d_sr = torch.empty((sc.k_sr, 8), dtype=torch.float32, device=self.device)
+        if d_sh is None:
+            d_sh = torch.empty((sc.k_sh, nb, 3), dtype=torch.float32, device=self.device)
+        o = self.opts()
+        _check("cg_codebook_reduce", self.lib.cg_codebook_reduce(ctypes.byref(sc), self._cams, len(self.cams),
+                                                                 ctypes.byref(o), self._ws_ptr, self.ws_bytes,
+                                                                 _ptr(d_sr), _ptr(d_sh), _stream_ptr(stream)))
+        return d_sr, d_sh
+
+    def l1_loss(self, images: torch.Tensor, target: torch.Tensor, d_images: torch.Tensor | None = None,
+                loss: torch.Tensor | None = None, stream=None):
+        if d_images is None:
+            d_images = torch.empty_like(images)
+        if loss is None:
+            loss = torch.empty((1,), dtype=torch.float64, device=self.device)
+        _check("cg_l1_loss", self.lib.cg_l1_loss(_ptr(images), _ptr(target), images.numel(), _ptr(d_images),
+                                                 _ptr(loss), self._ws_ptr, self.ws_bytes, _stream_ptr(stream)))
+        return loss, d_images
+
+    def array(self, which: int, dtype: torch.dtype, width: int = 1) -> torch.Tensor:
+        """A copy of one internal workspace array (see cg_workspace_array)."""
+        p = ctypes.c_void_p()
+        cnt = ctypes.c_uint64()
+        _check("cg_workspace_array", self.lib.cg_workspace_array(self._ws_ptr, self.ws_bytes, which, ctypes.byref(p),
+                                                                 ctypes.byref(cnt)))
+        count = int(cnt.value) * width
+        elem = torch.empty((), dtype=dtype).element_size()
+        base = self.ws.data_ptr()
+        off = (p.value or 0) - base
+        raw = self.ws[off:off + count * elem]
+        return raw.view(dtype).clone()
+
+    def view_images(self, images: torch.Tensor) -> list[torch.Tensor]:
+        out, b = [], 0
+        for c in self.cams:
+            m = 3 * c.width * c.height
+            out.append(images[b:b + m].view(3, c.height, c.width))
+            b += m
+        return out
+
+
+class CodebookRender(torch.autograd.Function):
+    """images = I_P(G, C) with gradients for positions, opacity logits and
+    both codebooks (the differentiable set S_diff of Sec. 3.4)."""
+
+    @staticmethod
+    def forward(ctx, renderer: Renderer, pos, opacity_logit, sr_rows, sh_rows, g2sr, g2sh, sh_degree: int):
+        scene = SceneTensors(pos.detach().contiguous(), opacity_logit.detach().contiguous(), g2sr, g2sh,
+                             sr_rows.detach().contiguous(), sh_rows.detach().contiguous(), sh_degree)
+        images = renderer.forward(scene)
+        ctx.renderer = renderer
+        ctx.dtypes = (sr_rows.dtype, sh_rows.dtype)
+        return images
+
+    @staticmethod
+    def backward(ctx, d_images):
+        r = ctx.renderer
+        d_pos, d_logit = r.backward(d_images)
+        d_sr, d_sh = r.codebook_reduce()
+        return (None, d_pos, d_logit, d_sr.to(ctx.dtypes[0]), d_sh.to(ctx.dtypes[1]), None, None, None)
+
+
+def render(renderer: Renderer, pos, opacity_logit, sr_rows, sh_rows, g2sr, g2sh, sh_degree: int) -> torch.Tensor:
+    return CodebookRender.apply(renderer, pos, opacity_logit, sr_rows, sh_rows, g2sr, g2sh, sh_degree)

@@ -1,0 +1,265 @@
+// cg_api.cu -- the C ABI of include/cg.h: argument checks, workspace layout
+// and the launch sequence of each call.
+#include <algorithm>
+#include <cstddef>
+#include <cstdio>
+
+#include "cg_common.cuh"
+
+using namespace cg;
+
+namespace {
+
+constexpr uint64_t kAlign = 256;
+
+uint64_t align_up(uint64_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+int ceil_log2(int64_t x) {
+  int b = 0;
+  while ((int64_t(1) << b) < x) ++b;
+  return b;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Checks arguments and computes the view table and the workspace layout.
+cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_opts* o, ViewTable* table,
+               Layout* L) {
+  if (!s || !cams || !o || !table || !L) return CG_ERR_ARG;
+  if (s->n < 1 || s->k_sr < 1 || s->k_sh < 1 || s->k_sr > 65536 || s->k_sh > 65536) return CG_ERR_ARG;
+  if (s->sh_degree < 0 || s->sh_degree > 3) return CG_ERR_ARG;
+  if (s->cb_dtype != CG_F32 && s->cb_dtype != CG_BF16) return CG_ERR_ARG;
+  if (n_views < 1 || n_views > CG_MAX_VIEWS) return CG_ERR_ARG;
+  if (o->tile != 8 && o->tile != 16 && o->tile != 32) return CG_ERR_ARG;
+  if (o->batch != 0 && o->batch != 32 && o->batch != 64 && o->batch != 128 && o->batch != 256) return CG_ERR_ARG;
+  if (o->pair_capacity < 1) return CG_ERR_ARG;
+  const int64_t n = s->n;
+  const int64_t R = n * n_views;
+  if (R >= (int64_t(1) << 32)) return CG_ERR_ARG;
+  memset(table, 0, sizeof(*table));
+  table->n_views = n_views;
+  table->tile = o->tile;
+  int64_t T = 0, P = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const cg_camera& c = cams[v];
+    if (c.width < 1 || c.height < 1 || c.width > 65535 || c.height > 65535) return CG_ERR_ARG;
+    ViewInfo& vi = table->v[v];
+    for (int i = 0; i < 12; ++i) vi.w2c[i] = c.world_to_cam[i];
+    vi.fx = c.fx; vi.fy = c.fy; vi.cx = c.cx; vi.cy = c.cy;
+    for (int i = 0; i < 3; ++i) vi.campos[i] = c.campos[i];
+    vi.near_z = c.near_z;
+    vi.width = c.width; vi.height = c.height;
+    vi.tiles_x = (c.width + o->tile - 1) / o->tile;
+    vi.tiles_y = (c.height + o->tile - 1) / o->tile;
+    vi.tile_base = T;
+    vi.pix_base = P;
+    T += (int64_t)vi.tiles_x * vi.tiles_y;
+    P += (int64_t)c.width * c.height;
+  }
+  if (T >= (int64_t(1) << 31)) return CG_ERR_ARG;
+  memset(L, 0, sizeof(*L));
+  const int nb = (s->sh_degree + 1) * (s->sh_degree + 1);
+  const int64_t Kc = (int64_t)o->pair_capacity;
+  L->n = n; L->R = R; L->T = T; L->P = P; L->Kc = Kc;
+  L->k_sr = s->k_sr; L->k_sh = s->k_sh; L->nb = nb; L->n_views = n_views; L->tile = o->tile;
+  L->tile_bits = std::max(1, ceil_log2(T));
+  L->sort_blocks_cap = (std::max(Kc, R) + 4095) / 4096 + 1;
+  const int64_t kmax = std::max(s->k_sr, s->k_sh) + 1;
+  L->scan_blocks_cap = (std::max(R, kmax) + 4095) / 4096 + 1;
+  L->chunks_cap = (n + 255) / 256 + kmax;
+  uint64_t off = 0;
+  auto take = [&](uint64_t bytes) {
+    const uint64_t at = off;
+    off = align_up(off + std::max<uint64_t>(bytes, 1));
+    return at;
+  };
+  L->hdr = take(sizeof(WsHeader));
+  L->views = take(sizeof(ViewInfo) * CG_MAX_VIEWS);
+  L->sigma3 = take(sizeof(float) * 6 * s->k_sr);
+  L->geo = take(sizeof(float4) * 2 * R);
+  L->rgbm = take(sizeof(float4) * R);
+  L->rect = take(sizeof(ushort4) * R);
+  L->ntiles = take(sizeof(uint32_t) * R);
+  L->depth = take(sizeof(uint32_t) * R);
+  L->offrec = take(sizeof(uint32_t) * R);
+  L->scan = take(sizeof(uint32_t) * std::max(R, kmax));
+  L->dkeys0 = take(sizeof(uint64_t) * R);
+  L->dkeys1 = take(sizeof(uint64_t) * R);
+  L->pairs0 = take(sizeof(uint64_t) * Kc);
+  L->pairs1 = take(sizeof(uint64_t) * Kc);
+  L->ranges = take(sizeof(uint32_t) * 2 * T);
+  L->tfinal = take(sizeof(float) * P);
+  L->ncontrib = take(sizeof(uint32_t) * P);
+  L->pairgrad = take(sizeof(float) * 9 * Kc);
+  L->dsigma = take(sizeof(float) * 6 * n);
+  L->drgb = take(sizeof(float) * 3 * R);
+  L->csr_off_sr = take(sizeof(uint32_t) * (3 * (int64_t)s->k_sr + 1));
+  L->csr_off_sh = take(sizeof(uint32_t) * (3 * (int64_t)s->k_sh + 1));
+  L->csr_ids_sr = take(sizeof(uint32_t) * n);
+  L->csr_ids_sh = take(sizeof(uint32_t) * n);
+  L->chunks = take(sizeof(uint4) * L->chunks_cap);
+  L->partials = take(sizeof(float) * std::max(6, 3 * nb) * L->chunks_cap);
+  L->hist = take(sizeof(uint32_t) * (256 * L->sort_blocks_cap + 256));
+  L->blocksums = take(sizeof(uint64_t) * L->scan_blocks_cap);
+  L->l1 = take(sizeof(double) * 1024);
+  L->total = off;
+  return CG_OK;
+}
+
+cg_status check_scene_ptrs(const cg_scene* s) {
+  if (!s->pos || !s->opacity_logit || !s->g2sr || !s->g2sh || !s->sr_rows || !s->sh_rows) return CG_ERR_ARG;
+  const size_t el = s->cb_dtype == CG_BF16 ? 2 : 4;
+  if (!aligned(s->pos, 4) || !aligned(s->opacity_logit, 4) || !aligned(s->g2sr, 2) || !aligned(s->g2sh, 2) ||
+      !aligned(s->sr_rows, el) || !aligned(s->sh_rows, el))
+    return CG_ERR_ARG;
+  return CG_OK;
+}
+
+cg_status check_ws(void* ws, size_t ws_bytes, const Layout& L) {
+  if (!ws || !aligned(ws, kAlign) || ws_bytes < L.total) return CG_ERR_ARG;
+  return CG_OK;
+}
+
+SceneArgs scene_args(const cg_scene* s) {
+  SceneArgs a;
+  a.n = s->n; a.k_sr = s->k_sr; a.k_sh = s->k_sh;
+  a.nb = (s->sh_degree + 1) * (s->sh_degree + 1);
+  a.dtype = (int)s->cb_dtype;
+  a.pos = s->pos; a.logit = s->opacity_logit; a.g2sr = s->g2sr; a.g2sh = s->g2sh;
+  a.sr_rows = s->sr_rows; a.sh_rows = s->sh_rows;
+  return a;
+}
+
+cg_status cuda_status(cudaError_t e) { return e == cudaSuccess ? CG_OK : CG_ERR_CUDA; }
+
+thread_local ViewTable tl_table;  // large: kept off the stack
+
+cg_status plan_call(const cg_scene* s, const cg_camera* cams, int n_views, const cg_opts* o, void* ws,
+                    size_t ws_bytes, Layout* L) {
+  cg_status st = plan(s, cams, n_views, o, &tl_table, L);
+  if (st == CG_OK) st = check_scene_ptrs(s);
+  if (st == CG_OK) st = check_ws(ws, ws_bytes, *L);
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t cg_workspace_bytes(const cg_scene* scene, const cg_camera* cams, int n_views, const cg_opts* opts) {
+  Layout L;
+  if (plan(scene, cams, n_views, opts, &tl_table, &L) != CG_OK) return 0;
+  return (size_t)L.total;
+}
+
+cg_status cg_render_fwd(const cg_scene* scene, const cg_camera* cams, int n_views, const cg_opts* opts,
+                        void* workspace, size_t ws_bytes, float* images, cg_stream_t stream) {
+  Layout L;
+  cg_status st = plan_call(scene, cams, n_views, opts, workspace, ws_bytes, &L);
+  if (st == CG_OK && (!images || !aligned(images, 4))) st = CG_ERR_ARG;
+  if (st != CG_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const SceneArgs sc = scene_args(scene);
+  const int batch = opts->batch ? opts->batch : 256;
+  cudaError_t e = launch_setup(tl_table, L, workspace, s);
+  if (e == cudaSuccess) e = launch_sigma3(sc, L, workspace, s);
+  if (e == cudaSuccess) e = launch_preprocess(sc, L, workspace, s);
+  if (e == cudaSuccess) e = launch_build_pairs(L, workspace, L.tile_bits, s);
+  if (e == cudaSuccess) e = launch_blend_fwd(L, workspace, opts->tile, batch, opts->bg, images, s);
+  return cuda_status(e);
+}
+
+cg_status cg_render_bwd(const cg_scene* scene, const cg_camera* cams, int n_views, const cg_opts* opts,
+                        void* workspace, size_t ws_bytes, const float* d_images, float* d_pos,
+                        float* d_opacity_logit, cg_stream_t stream) {
+  Layout L;
+  cg_status st = plan_call(scene, cams, n_views, opts, workspace, ws_bytes, &L);
+  if (st == CG_OK && (!d_images || !d_pos || !d_opacity_logit || !aligned(d_images, 4) || !aligned(d_pos, 4) ||
+                      !aligned(d_opacity_logit, 4)))
+    st = CG_ERR_ARG;
+  if (st != CG_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const SceneArgs sc = scene_args(scene);
+  const int batch = opts->batch ? std::min(opts->batch, 128) : 64;
+  cudaError_t e = launch_blend_bwd(L, workspace, opts->tile, batch, opts->bg, d_images, s);
+  if (e == cudaSuccess) e = launch_gaussian_bwd(sc, L, workspace, d_pos, d_opacity_logit, s);
+  return cuda_status(e);
+}
+
+cg_status cg_codebook_reduce(const cg_scene* scene, const cg_camera* cams, int n_views, const cg_opts* opts,
+                             void* workspace, size_t ws_bytes, float* d_sr_rows, float* d_sh_rows,
+                             cg_stream_t stream) {
+  Layout L;
+  cg_status st = plan_call(scene, cams, n_views, opts, workspace, ws_bytes, &L);
+  if (st == CG_OK && (!d_sr_rows || !d_sh_rows || !aligned(d_sr_rows, 4) || !aligned(d_sh_rows, 4))) st = CG_ERR_ARG;
+  if (st != CG_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  return cuda_status(launch_codebook_reduce(scene_args(scene), L, workspace, d_sr_rows, d_sh_rows, s));
+}
+
+cg_status cg_last_device_status(void* workspace, size_t ws_bytes, cg_stream_t stream, uint64_t* pairs_out) {
+  if (!workspace || ws_bytes < sizeof(WsHeader) || !aligned(workspace, kAlign)) return CG_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  WsHeader h;
+  cudaError_t e = cudaMemcpyAsync(&h, workspace, sizeof(WsHeader), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return CG_ERR_CUDA;
+  if (h.magic != kMagic) return CG_ERR_ARG;
+  if (pairs_out) *pairs_out = h.st.pairs;
+  return (cg_status)h.st.status;
+}
+
+cg_status cg_l1_loss(const float* image, const float* target, int64_t count, float* d_image, double* loss_out,
+                     void* workspace, size_t ws_bytes, cg_stream_t stream) {
+  if (!image || !target || !d_image || !loss_out || count < 1 || !workspace || !aligned(workspace, kAlign) ||
+      ws_bytes < sizeof(WsHeader))
+    return CG_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  WsHeader h;
+  cudaError_t e = cudaMemcpyAsync(&h, workspace, sizeof(WsHeader), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return CG_ERR_CUDA;
+  if (h.magic != kMagic || h.layout.l1 + 1024 * sizeof(double) > ws_bytes) return CG_ERR_ARG;
+  return cuda_status(launch_l1(image, target, count, d_image, loss_out, h.layout, workspace, s));
+}
+
+cg_status cg_workspace_array(void* workspace, size_t ws_bytes, cg_ws_array which, void** ptr_out,
+                             uint64_t* count_out) {
+  if (!workspace || !ptr_out || !count_out || ws_bytes < sizeof(WsHeader)) return CG_ERR_ARG;
+  WsHeader h;
+  if (cudaMemcpy(&h, workspace, sizeof(WsHeader), cudaMemcpyDeviceToHost) != cudaSuccess) return CG_ERR_CUDA;
+  if (h.magic != kMagic) return CG_ERR_ARG;
+  const Layout& L = h.layout;
+  char* b = reinterpret_cast<char*>(workspace);
+  uint64_t off = 0, cnt = 0;
+  const int passes = (L.tile_bits + 7) / 8;
+  switch (which) {
+    case CG_WS_RECT: off = L.rect; cnt = L.R; break;
+    case CG_WS_DEPTH: off = L.depth; cnt = L.R; break;
+    case CG_WS_PAIRS: off = (passes & 1) ? L.pairs1 : L.pairs0; cnt = h.st.pairs_ok ? h.st.pairs : 0; break;
+    case CG_WS_RANGES: off = L.ranges; cnt = L.T; break;
+    case CG_WS_NCONTRIB: off = L.ncontrib; cnt = L.P; break;
+    case CG_WS_TFINAL: off = L.tfinal; cnt = L.P; break;
+    case CG_WS_DSIGMA: off = L.dsigma; cnt = L.n; break;
+    case CG_WS_DRGB: off = L.drgb; cnt = L.R; break;
+    case CG_WS_GEO: off = L.geo; cnt = L.R; break;
+    case CG_WS_RGB: off = L.rgbm; cnt = L.R; break;
+    case CG_WS_SIGMA3: off = L.sigma3; cnt = L.k_sr; break;
+    default: return CG_ERR_ARG;
+  }
+  *ptr_out = b + off;
+  *count_out = cnt;
+  return CG_OK;
+}
+
+float cg_host_exp32(float x) { return exp32(x); }
+
+void cg_host_sh_consts(float out[16]) {
+  for (int k = 0; k < 16; ++k) out[k] = sh_const(k);
+}
+
+void cg_host_sigma3(const float row[8], float out[6]) { sigma3_from_row(row, out); }
+
+const char* cg_version(void) { return "cg 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,299 @@
+// cg_common.cuh -- types, workspace layout and the FP32 decision arithmetic
+// shared by the kernels of libcg.
+//
+// The whole library is compiled with -fmad=false (device) and
+// -ffp-contract=off (host): every multiply-add that should fuse is written as
+// fmaf(), every other operation is one IEEE binary32 operation, rounded to
+// nearest.  The operation order of the functions marked "decision
+// arithmetic" is part of the render's definition: culling, the 3-sigma tile
+// rectangle, the depth key, and the skip / clamp / termination of every
+// (pixel, Gaussian) evaluation are decided by it.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/cg.h"
+
+#define CG_HD __host__ __device__ __forceinline__
+
+namespace cg {
+
+// ----------------------------------------------------------------------------
+// constants
+// ----------------------------------------------------------------------------
+constexpr float kAlphaMin = 0x1.010102p-8f;  // 1/255 rounded to binary32
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 0.0001f;
+constexpr float kDilation = 0.3f;
+constexpr float kLambdaFloor = 0.1f;
+constexpr int kMaxBasis = 16;
+
+CG_HD float bits_to_float(uint32_t u) {
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+}
+CG_HD uint32_t float_to_bits(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  return u;
+}
+
+// ----------------------------------------------------------------------------
+// decision arithmetic
+// ----------------------------------------------------------------------------
+
+// exp in binary32.  Cody-Waite range reduction x = n ln2 + r (ln 2 split into
+// a 15-significant-bit head, exact when multiplied by |n| < 512, and the
+// remainder), the degree-6 Taylor polynomial of e^r on |r| <= ln2/2 by
+// Horner's rule (truncation < 1.3e-7 relative), then the factor 2^n from its
+// exponent bits.  x <= -87 gives 0, x >= 88 gives +inf, NaN gives 0.
+CG_HD float exp32(float x) {
+  if (!(x > -87.0f)) return 0.0f;
+  if (!(x < 88.0f)) return bits_to_float(0x7f800000u);
+  const float log2e = 1.44269502162933349609375f;
+  const float ln2_hi = 0.693145751953125f;
+  const float ln2_lo = 1.42860682030941723212e-6f;
+  const float n = rintf(x * log2e);
+  float r = fmaf(-n, ln2_hi, x);
+  r = fmaf(-n, ln2_lo, r);
+  float p = 1.0f / 720.0f;
+  p = fmaf(p, r, 1.0f / 120.0f);
+  p = fmaf(p, r, 1.0f / 24.0f);
+  p = fmaf(p, r, 1.0f / 6.0f);
+  p = fmaf(p, r, 0.5f);
+  p = fmaf(p, r, 1.0f);
+  p = fmaf(p, r, 1.0f);
+  const int ni = (int)n;
+  return p * bits_to_float((uint32_t)(ni + 127) << 23);
+}
+
+CG_HD float sigmoid32(float l) { return 1.0f / (1.0f + exp32(-l)); }
+
+// The real SH basis constants with their signs (graphics convention with the
+// Condon-Shortley phase), as the closed forms rounded to binary32:
+//   1/(2 sqrt(pi)); sqrt(3/(4pi)); sqrt(15/(4pi)), sqrt(5/(16pi)),
+//   sqrt(15/(16pi)); sqrt(35/(32pi)), sqrt(105/(4pi)), sqrt(21/(32pi)),
+//   sqrt(7/(16pi)), sqrt(105/(16pi)).
+// The decimal literals carry 17 significant digits of the FP64 closed forms,
+// so their binary32 rounding is the rounding of the closed form.
+#define CG_SH_C0 0.28209479177387814
+#define CG_SH_C1 0.48860251190291992
+#define CG_SH_C2A 1.0925484305920792
+#define CG_SH_C2B 0.31539156525252005
+#define CG_SH_C2C 0.54627421529603959
+#define CG_SH_C3A 0.59004358992664352
+#define CG_SH_C3B 2.8906114426405538
+#define CG_SH_C3C 0.4570457994644658
+#define CG_SH_C3D 0.3731763325901154
+#define CG_SH_C3E 1.4453057213202769
+
+CG_HD float sh_const(int k) {
+  switch (k) {
+    case 0: return (float)CG_SH_C0;
+    case 1: return (float)-CG_SH_C1;
+    case 2: return (float)CG_SH_C1;
+    case 3: return (float)-CG_SH_C1;
+    case 4: return (float)CG_SH_C2A;
+    case 5: return (float)-CG_SH_C2A;
+    case 6: return (float)CG_SH_C2B;
+    case 7: return (float)-CG_SH_C2A;
+    case 8: return (float)CG_SH_C2C;
+    case 9: return (float)-CG_SH_C3A;
+    case 10: return (float)CG_SH_C3B;
+    case 11: return (float)-CG_SH_C3C;
+    case 12: return (float)CG_SH_C3D;
+    case 13: return (float)-CG_SH_C3C;
+    case 14: return (float)CG_SH_C3E;
+    default: return (float)-CG_SH_C3A;
+  }
+}
+
+// Y_k of a unit direction (x, y, z), decision arithmetic (the colour clamp
+// depends on it).
+CG_HD void sh_basis32(int nb, float x, float y, float z, float* Y) {
+  Y[0] = sh_const(0);
+  if (nb > 1) {
+    Y[1] = sh_const(1) * y;
+    Y[2] = sh_const(2) * z;
+    Y[3] = sh_const(3) * x;
+  }
+  if (nb > 4) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = sh_const(4) * (x * y);
+    Y[5] = sh_const(5) * (y * z);
+    Y[6] = sh_const(6) * ((2.0f * zz - xx) - yy);
+    Y[7] = sh_const(7) * (x * z);
+    Y[8] = sh_const(8) * (xx - yy);
+    if (nb > 9) {
+      Y[9] = (sh_const(9) * y) * (3.0f * xx - yy);
+      Y[10] = (sh_const(10) * (x * y)) * z;
+      Y[11] = (sh_const(11) * y) * ((4.0f * zz - xx) - yy);
+      Y[12] = (sh_const(12) * z) * ((2.0f * zz - 3.0f * xx) - 3.0f * yy);
+      Y[13] = (sh_const(13) * x) * ((4.0f * zz - xx) - yy);
+      Y[14] = (sh_const(14) * z) * (xx - yy);
+      Y[15] = (sh_const(15) * x) * (xx - 3.0f * yy);
+    }
+  }
+}
+
+// Eq. 2 for one SR row: Sigma = R(q) diag(exp(ls))^2 R(q)^T, q normalised;
+// unique entries 00 01 02 11 12 22.  Decision arithmetic (the tile
+// rectangle depends on it).
+CG_HD void sigma3_from_row(const float* row, float* sig) {
+  const float s0 = exp32(row[0]), s1 = exp32(row[1]), s2 = exp32(row[2]);
+  const float qw = row[3], qx = row[4], qy = row[5], qz = row[6];
+  const float n2 = fmaf(qw, qw, fmaf(qx, qx, fmaf(qy, qy, qz * qz)));
+  float w, x, y, z;
+  if (n2 > 0.0f) {
+    const float nrm = sqrtf(n2);
+    w = qw / nrm;
+    x = qx / nrm;
+    y = qy / nrm;
+    z = qz / nrm;
+  } else {
+    w = 1.0f;
+    x = y = z = 0.0f;
+  }
+  float R[9];
+  R[0] = 1.0f - 2.0f * fmaf(y, y, z * z);
+  R[1] = 2.0f * fmaf(x, y, -(w * z));
+  R[2] = 2.0f * fmaf(x, z, w * y);
+  R[3] = 2.0f * fmaf(x, y, w * z);
+  R[4] = 1.0f - 2.0f * fmaf(x, x, z * z);
+  R[5] = 2.0f * fmaf(y, z, -(w * x));
+  R[6] = 2.0f * fmaf(x, z, -(w * y));
+  R[7] = 2.0f * fmaf(y, z, w * x);
+  R[8] = 1.0f - 2.0f * fmaf(x, x, y * y);
+  const float s[3] = {s0, s1, s2};
+  float M[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) M[3 * a + j] = R[3 * a + j] * s[j];
+  const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    const float* ma = M + 3 * ia[e];
+    const float* mb = M + 3 * ib[e];
+    sig[e] = fmaf(ma[0], mb[0], fmaf(ma[1], mb[1], ma[2] * mb[2]));
+  }
+}
+
+// ----------------------------------------------------------------------------
+// views and workspace
+// ----------------------------------------------------------------------------
+
+struct ViewInfo {
+  float w2c[12];
+  float fx, fy, cx, cy;
+  float campos[3];
+  float near_z;
+  int width, height;
+  int tiles_x, tiles_y;
+  int64_t tile_base;  // first global tile of the view
+  int64_t pix_base;   // first pixel of the view (images hold 3 * pix_base floats before it)
+};
+
+struct ViewTable {
+  int n_views;
+  int tile;
+  ViewInfo v[CG_MAX_VIEWS];
+};
+
+// Offsets (bytes from the workspace base) of every region; written by the
+// host into the setup kernel's parameters and by that kernel into the header.
+struct Layout {
+  uint64_t total;
+  uint64_t hdr, views, sigma3, geo, rgbm, rect, ntiles, depth, offrec, scan, dkeys0, dkeys1, pairs0, pairs1,
+      ranges, tfinal, ncontrib, pairgrad, dsigma, drgb, csr_off_sr, csr_off_sh, csr_ids_sr, csr_ids_sh, chunks,
+      partials, hist, blocksums, l1;
+  // sizes
+  int64_t n, R, T, P, Kc;
+  int k_sr, k_sh, nb, n_views, tile, tile_bits;
+  int64_t sort_blocks_cap;   // capacity of the per-block digit histograms
+  int64_t scan_blocks_cap;   // capacity of the per-block scan sums
+  int64_t chunks_cap;        // capacity of the codebook-reduction chunk table
+};
+
+// Device-written status and counters (in the header).
+struct DeviceState {
+  uint32_t status;      // cg_status of device-detected problems (first wins)
+  uint32_t detail;
+  uint64_t pairs;       // K of the last forward
+  uint64_t visible;     // visible (view, Gaussian) records of the last forward
+  uint64_t scan_total;  // scratch total written by the scan kernels
+  uint32_t pairs_ok;    // 1 if pairs <= capacity
+  uint32_t pad;
+};
+
+struct WsHeader {
+  uint64_t magic;
+  Layout layout;
+  DeviceState st;
+};
+
+constexpr uint64_t kMagic = 0x43475753'00000001ull;  // "CGWS" v1
+
+template <typename T>
+CG_HD T* ws_ptr(void* base, uint64_t off) {
+  return reinterpret_cast<T*>(reinterpret_cast<char*>(base) + off);
+}
+
+__device__ __forceinline__ void set_status(DeviceState* st, uint32_t code, uint32_t detail) {
+  if (atomicCAS(&st->status, 0u, code) == 0u) st->detail = detail;
+}
+
+__device__ __forceinline__ float load_row(const void* rows, int dtype, size_t i) {
+  if (dtype == CG_BF16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(rows)[i]);
+  return reinterpret_cast<const float*>(rows)[i];
+}
+
+__device__ __forceinline__ int find_view(const ViewInfo* views, int n_views, int64_t gtile) {
+  int v = 0;
+  while (v + 1 < n_views && views[v + 1].tile_base <= gtile) ++v;
+  return v;
+}
+
+// ----------------------------------------------------------------------------
+// kernel launchers (one translation unit each)
+// ----------------------------------------------------------------------------
+struct SceneArgs {
+  int n, k_sr, k_sh, nb, dtype;
+  const float* pos;
+  const float* logit;
+  const uint16_t* g2sr;
+  const uint16_t* g2sh;
+  const void* sr_rows;
+  const void* sh_rows;
+};
+
+cudaError_t launch_setup(const ViewTable& table, const Layout& L, void* ws, cudaStream_t s);
+cudaError_t launch_sigma3(const SceneArgs& sc, const Layout& L, void* ws, cudaStream_t s);
+cudaError_t launch_preprocess(const SceneArgs& sc, const Layout& L, void* ws, cudaStream_t s);
+cudaError_t launch_build_pairs(const Layout& L, void* ws, int tile_bits, cudaStream_t s);
+cudaError_t launch_blend_fwd(const Layout& L, void* ws, int tile, int batch, const float bg[3], float* images,
+                             cudaStream_t s);
+cudaError_t launch_blend_bwd(const Layout& L, void* ws, int tile, int batch, const float bg[3],
+                             const float* d_images, cudaStream_t s);
+cudaError_t launch_gaussian_bwd(const SceneArgs& sc, const Layout& L, void* ws, float* d_pos, float* d_logit,
+                                cudaStream_t s);
+cudaError_t launch_codebook_reduce(const SceneArgs& sc, const Layout& L, void* ws, float* d_sr, float* d_sh,
+                                   cudaStream_t s);
+cudaError_t launch_l1(const float* img, const float* tgt, int64_t count, float* d_img, double* loss,
+                      const Layout& L, void* ws, cudaStream_t s);
+
+// Radix sort of `count` (device value) uint64 keys on bits [lo, lo + 8 * passes),
+// stable, ping-pong between a and b; returns in *result_in_b whether the
+// sorted keys end in b.  Used for depth keys, tile keys and codebook rows.
+cudaError_t sort_u64(void* ws, const Layout& L, uint64_t* a, uint64_t* b, const uint64_t* count_dev,
+                     int64_t count_cap, int lo_bit, int passes, bool* result_in_b, cudaStream_t s);
+// Exclusive scan of `count` (device value) uint32 values into out (may alias in),
+// total written to *total_dev.
+cudaError_t scan_u32(void* ws, const Layout& L, const uint32_t* in, uint32_t* out, const uint64_t* count_dev,
+                     int64_t count_cap, uint64_t* total_dev, cudaStream_t s);
+
+}  // namespace cg

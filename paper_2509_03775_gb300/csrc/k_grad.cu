@@ -1,0 +1,540 @@
+// k_grad.cu -- per-Gaussian backward (pair slots -> projection, colour and
+// opacity chain rule) and the deterministic codebook reduction: a row's
+// gradient is the sum over the Gaussians that index it (g2sr / g2sh of
+// Sec. 3.1), pushed through Eq. 2 for SR rows and through the SH basis for
+// SH rows.  Every sum runs in a fixed order; no floating-point atomics.
+#include <algorithm>
+
+#include "cg_common.cuh"
+
+namespace cg {
+
+constexpr int kChunk = 256;  // members per chunk of the codebook reduction
+
+// Y_k and dY_k/d(x, y, z) (x, y, z treated as independent), FP32.
+template <int NB>
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float* Y, float* Dx, float* Dy, float* Dz) {
+  const float k0 = sh_const(0);
+  Y[0] = k0;
+  Dx[0] = Dy[0] = Dz[0] = 0.0f;
+  if (NB > 1) {
+    const float k1 = sh_const(1), k2 = sh_const(2), k3 = sh_const(3);
+    Y[1] = k1 * y; Dx[1] = 0.0f; Dy[1] = k1; Dz[1] = 0.0f;
+    Y[2] = k2 * z; Dx[2] = 0.0f; Dy[2] = 0.0f; Dz[2] = k2;
+    Y[3] = k3 * x; Dx[3] = k3; Dy[3] = 0.0f; Dz[3] = 0.0f;
+  }
+  if (NB > 4) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    float k;
+    k = sh_const(4); Y[4] = k * x * y; Dx[4] = k * y; Dy[4] = k * x; Dz[4] = 0.0f;
+    k = sh_const(5); Y[5] = k * y * z; Dx[5] = 0.0f; Dy[5] = k * z; Dz[5] = k * y;
+    k = sh_const(6); Y[6] = k * (2.0f * zz - xx - yy); Dx[6] = -2.0f * k * x; Dy[6] = -2.0f * k * y; Dz[6] = 4.0f * k * z;
+    k = sh_const(7); Y[7] = k * x * z; Dx[7] = k * z; Dy[7] = 0.0f; Dz[7] = k * x;
+    k = sh_const(8); Y[8] = k * (xx - yy); Dx[8] = 2.0f * k * x; Dy[8] = -2.0f * k * y; Dz[8] = 0.0f;
+    if (NB > 9) {
+      k = sh_const(9); Y[9] = k * y * (3.0f * xx - yy); Dx[9] = k * 6.0f * x * y; Dy[9] = k * 3.0f * (xx - yy); Dz[9] = 0.0f;
+      k = sh_const(10); Y[10] = k * x * y * z; Dx[10] = k * y * z; Dy[10] = k * x * z; Dz[10] = k * x * y;
+      k = sh_const(11); Y[11] = k * y * (4.0f * zz - xx - yy); Dx[11] = -2.0f * k * x * y;
+      Dy[11] = k * (4.0f * zz - xx - 3.0f * yy); Dz[11] = 8.0f * k * y * z;
+      k = sh_const(12); Y[12] = k * z * (2.0f * zz - 3.0f * xx - 3.0f * yy); Dx[12] = -6.0f * k * x * z;
+      Dy[12] = -6.0f * k * y * z; Dz[12] = k * (6.0f * zz - 3.0f * xx - 3.0f * yy);
+      k = sh_const(13); Y[13] = k * x * (4.0f * zz - xx - yy); Dx[13] = k * (4.0f * zz - 3.0f * xx - yy);
+      Dy[13] = -2.0f * k * x * y; Dz[13] = 8.0f * k * x * z;
+      k = sh_const(14); Y[14] = k * z * (xx - yy); Dx[14] = 2.0f * k * x * z; Dy[14] = -2.0f * k * y * z; Dz[14] = k * (xx - yy);
+      k = sh_const(15); Y[15] = k * x * (xx - 3.0f * yy); Dx[15] = 3.0f * k * (xx - yy); Dy[15] = -6.0f * k * x * y; Dz[15] = 0.0f;
+    }
+  }
+}
+
+template <int NB>
+__device__ __forceinline__ void sh_basis_only(float x, float y, float z, float* Y) {
+  float Dx[kMaxBasis], Dy[kMaxBasis], Dz[kMaxBasis];
+  sh_basis_grad<NB>(x, y, z, Y, Dx, Dy, Dz);
+}
+
+// ---------------------------------------------------------------------------
+// per-Gaussian backward
+// ---------------------------------------------------------------------------
+
+template <int NB>
+__global__ void __launch_bounds__(256) k_gaussian_bwd(const SceneArgs sc, const ViewInfo* __restrict__ views,
+                                                      int n_views, const float* __restrict__ sig3,
+                                                      const float4* __restrict__ geo, const float4* __restrict__ rgbm,
+                                                      const uint32_t* __restrict__ ntiles,
+                                                      const uint32_t* __restrict__ offrec,
+                                                      const float* __restrict__ pairgrad, const DeviceState* st,
+                                                      float* __restrict__ d_pos, float* __restrict__ d_logit,
+                                                      float* __restrict__ dsigma, float* __restrict__ drgb) {
+  const bool ok = st->pairs_ok != 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < sc.n; g += stride) {
+    float dp[3] = {0.0f, 0.0f, 0.0f}, dl = 0.0f, dsg[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    const float p[3] = {sc.pos[3 * g], sc.pos[3 * g + 1], sc.pos[3 * g + 2]};
+    const uint32_t isr = sc.g2sr[g], ish = sc.g2sh[g];
+    for (int v = 0; v < n_views; ++v) {
+      const int64_t rec = (int64_t)v * sc.n + g;
+      const uint32_t nt = ok ? ntiles[rec] : 0u;
+      if (nt == 0) {
+        drgb[3 * rec] = drgb[3 * rec + 1] = drgb[3 * rec + 2] = 0.0f;
+        continue;
+      }
+      // sum of the pair slots of this record, in tile order
+      float gs[9] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+      const float* src = pairgrad + 9 * (size_t)offrec[rec];
+      for (uint32_t i = 0; i < nt; ++i) {
+#pragma unroll
+        for (int e = 0; e < 9; ++e) gs[e] += src[9 * (size_t)i + e];
+      }
+      const ViewInfo& cam = views[v];
+      const float* W = cam.w2c;
+      const float4 gb = geo[2 * rec + 1];
+      const float o = gb.y;
+      dl = fmaf(gs[5], o * (1.0f - o), dl);
+      // colour -> clamp mask -> SH direction
+      const uint32_t mask = (uint32_t)rgbm[rec].w;
+      float dc[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dc[c] = (mask >> c & 1u) ? 0.0f : gs[6 + c];
+      drgb[3 * rec] = dc[0];
+      drgb[3 * rec + 1] = dc[1];
+      drgb[3 * rec + 2] = dc[2];
+      const float dv[3] = {p[0] - cam.campos[0], p[1] - cam.campos[1], p[2] - cam.campos[2]};
+      const float dist = sqrtf(fmaf(dv[0], dv[0], fmaf(dv[1], dv[1], dv[2] * dv[2])));
+      const float inv = 1.0f / dist;
+      const float dir[3] = {dv[0] * inv, dv[1] * inv, dv[2] * inv};
+      float Y[kMaxBasis], Dx[kMaxBasis], Dy[kMaxBasis], Dz[kMaxBasis];
+      sh_basis_grad<NB>(dir[0], dir[1], dir[2], Y, Dx, Dy, Dz);
+      float dd[3] = {0.0f, 0.0f, 0.0f};
+      const size_t rb = (size_t)ish * NB * 3;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        const float dyk = fmaf(dc[0], load_row(sc.sh_rows, sc.dtype, rb + 3 * k),
+                               fmaf(dc[1], load_row(sc.sh_rows, sc.dtype, rb + 3 * k + 1),
+                                    dc[2] * load_row(sc.sh_rows, sc.dtype, rb + 3 * k + 2)));
+        dd[0] = fmaf(dyk, Dx[k], dd[0]);
+        dd[1] = fmaf(dyk, Dy[k], dd[1]);
+        dd[2] = fmaf(dyk, Dz[k], dd[2]);
+      }
+      const float ddot = fmaf(dd[0], dir[0], fmaf(dd[1], dir[1], dd[2] * dir[2]));
+#pragma unroll
+      for (int a = 0; a < 3; ++a) dp[a] = fmaf(dd[a] - dir[a] * ddot, inv, dp[a]);
+      // projection
+      float t[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) t[a] = fmaf(W[4 * a], p[0], fmaf(W[4 * a + 1], p[1], fmaf(W[4 * a + 2], p[2], W[4 * a + 3])));
+      const float iz = 1.0f / t[2];
+      const float fx = cam.fx, fy = cam.fy;
+      const float J00 = fx * iz, J02 = -fx * t[0] * iz * iz, J11 = fy * iz, J12 = -fy * t[1] * iz * iz;
+      float T[6];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T[j] = fmaf(J00, W[j], J02 * W[8 + j]);
+        T[3 + j] = fmaf(J11, W[4 + j], J12 * W[8 + j]);
+      }
+      const float* sg = sig3 + (size_t)isr * 6;
+      const float S[9] = {sg[0], sg[1], sg[2], sg[1], sg[3], sg[4], sg[2], sg[4], sg[5]};
+      float ST0[3], ST1[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        ST0[i] = fmaf(S[3 * i], T[0], fmaf(S[3 * i + 1], T[1], S[3 * i + 2] * T[2]));
+        ST1[i] = fmaf(S[3 * i], T[3], fmaf(S[3 * i + 1], T[4], S[3 * i + 2] * T[5]));
+      }
+      const float A = fmaf(T[0], ST0[0], fmaf(T[1], ST0[1], T[2] * ST0[2])) + kDilation;
+      const float B = fmaf(T[3], ST0[0], fmaf(T[4], ST0[1], T[5] * ST0[2]));
+      const float C = fmaf(T[3], ST1[0], fmaf(T[4], ST1[1], T[5] * ST1[2])) + kDilation;
+      const float det = fmaf(A, C, -(B * B));
+      const float id2 = 1.0f / (det * det);
+      const float g0 = gs[2], g1 = gs[3], g2 = gs[4];
+      const float da = (-g0 * C * C + g1 * B * C - g2 * B * B) * id2;
+      const float db = (2.0f * g0 * B * C - g1 * (A * C + B * B) + 2.0f * g2 * A * B) * id2;
+      const float dcc = (-g0 * B * B + g1 * A * B - g2 * A * A) * id2;
+      float dT[6];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        dT[j] = fmaf(2.0f * da, ST0[j], db * ST1[j]);
+        dT[3 + j] = fmaf(db, ST0[j], 2.0f * dcc * ST1[j]);
+      }
+      const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        const int i = ia[e], j = ib[e];
+        float f = fmaf(da * T[i], T[j], fmaf(db * T[i], T[3 + j], dcc * T[3 + i] * T[3 + j]));
+        if (i != j) f += fmaf(da * T[j], T[i], fmaf(db * T[j], T[3 + i], dcc * T[3 + j] * T[3 + i]));
+        dsg[e] += f;
+      }
+      float dJ[6];
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          dJ[3 * a + k] = fmaf(dT[3 * a], W[4 * k], fmaf(dT[3 * a + 1], W[4 * k + 1], dT[3 * a + 2] * W[4 * k + 2]));
+      const float gmx = gs[0], gmy = gs[1];
+      const float iz2 = iz * iz;
+      float dt[3];
+      dt[0] = fmaf(-fx * iz2, dJ[2], fx * iz * gmx);
+      dt[1] = fmaf(-fy * iz2, dJ[5], fy * iz * gmy);
+      dt[2] = -fx * iz2 * dJ[0] + 2.0f * fx * t[0] * iz2 * iz * dJ[2] - fy * iz2 * dJ[4] +
+              2.0f * fy * t[1] * iz2 * iz * dJ[5] - fx * t[0] * iz2 * gmx - fy * t[1] * iz2 * gmy;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) dp[k] += fmaf(W[k], dt[0], fmaf(W[4 + k], dt[1], W[8 + k] * dt[2]));
+    }
+    d_pos[3 * g] = dp[0];
+    d_pos[3 * g + 1] = dp[1];
+    d_pos[3 * g + 2] = dp[2];
+    d_logit[g] = dl;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) dsigma[6 * g + e] = dsg[e];
+  }
+}
+
+cudaError_t launch_gaussian_bwd(const SceneArgs& sc, const Layout& L, void* ws, float* d_pos, float* d_logit,
+                                cudaStream_t s) {
+  WsHeader* hdr = ws_ptr<WsHeader>(ws, L.hdr);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((L.n + 255) / 256, 152 * 16));
+  const ViewInfo* views = ws_ptr<ViewInfo>(ws, L.views);
+  const float* sig = ws_ptr<float>(ws, L.sigma3);
+  const float4* geo = ws_ptr<float4>(ws, L.geo);
+  const float4* rgbm = ws_ptr<float4>(ws, L.rgbm);
+  const uint32_t* nt = ws_ptr<uint32_t>(ws, L.ntiles);
+  const uint32_t* off = ws_ptr<uint32_t>(ws, L.offrec);
+  const float* pg = ws_ptr<float>(ws, L.pairgrad);
+  float* dsig = ws_ptr<float>(ws, L.dsigma);
+  float* drgb = ws_ptr<float>(ws, L.drgb);
+#define CG_GB(NBV) k_gaussian_bwd<NBV><<<grid, 256, 0, s>>>(sc, views, L.n_views, sig, geo, rgbm, nt, off, pg, &hdr->st, d_pos, d_logit, dsig, drgb)
+  switch (sc.nb) {
+    case 1: CG_GB(1); break;
+    case 4: CG_GB(4); break;
+    case 9: CG_GB(9); break;
+    case 16: CG_GB(16); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef CG_GB
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// codebook membership (CSR) and chunked, fixed-order row sums
+// ---------------------------------------------------------------------------
+
+// Keys (row << 32 | g); an index >= k (already reported by the forward) is
+// keyed past the last row and counted nowhere.
+__global__ void k_row_keys(const uint16_t* __restrict__ idx, int64_t n, int k, uint64_t* __restrict__ keys,
+                           uint32_t* __restrict__ counts, uint64_t* count_slot) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += stride) {
+    const uint32_t r = idx[g];
+    const bool ok = r < (uint32_t)k;
+    keys[g] = ((uint64_t)(ok ? r : (uint32_t)k) << 32) | (uint64_t)g;
+    if (ok) atomicAdd(&counts[r], 1u);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *count_slot = (uint64_t)n;
+}
+
+__global__ void k_zero_counts(uint32_t* c, int64_t m) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) c[i] = 0u;
+}
+
+// chunks per row: ceil(count / kChunk)
+__global__ void k_chunk_counts(const uint32_t* __restrict__ counts, int k, uint32_t* __restrict__ nch,
+                               uint64_t* count_slot) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < k; r += stride)
+    nch[r] = (counts[r] + kChunk - 1) / kChunk;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *count_slot = (uint64_t)k;
+}
+
+// chunk c of row r covers member positions [off_r + c*kChunk, min(.., off_{r+1}))
+__global__ void k_fill_chunks(const uint32_t* __restrict__ row_off, const uint32_t* __restrict__ counts,
+                              const uint32_t* __restrict__ chunk_base, int k, uint4* __restrict__ chunks) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < k; r += stride) {
+    const uint32_t cnt = counts[r], base = row_off[r], cb = chunk_base[r];
+    for (uint32_t c = 0; c * kChunk < cnt; ++c)
+      chunks[cb + c] = make_uint4((uint32_t)r, base + c * kChunk, base + min(cnt, (c + 1) * kChunk), 0u);
+  }
+}
+
+__global__ void k_ids_from_keys(const uint64_t* __restrict__ keys, int64_t n, uint32_t* __restrict__ ids) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) ids[i] = (uint32_t)keys[i];
+}
+
+// warp per chunk: SR terms are the 6 entries of dL/dSigma of each member
+__global__ void __launch_bounds__(256) k_sr_partials(const uint4* __restrict__ chunks, const uint64_t* n_chunks_dev,
+                                                     const uint32_t* __restrict__ ids,
+                                                     const float* __restrict__ dsigma, float* __restrict__ part) {
+  const int64_t nch = (int64_t)*n_chunks_dev;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); c < nch; c += warps) {
+    const uint4 ch = chunks[c];
+    float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    for (uint32_t i = ch.y + lane; i < ch.z; i += 32) {
+      const float* d = dsigma + 6 * (size_t)ids[i];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) acc[e] += d[e];
+    }
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int e = 0; e < 6; ++e) part[6 * c + e] = acc[e];
+    }
+  }
+}
+
+// warp per chunk: SH terms Y_k(dir_{v,g}) * dL/dcolour_{v,g}, summed over views
+template <int NB>
+__global__ void __launch_bounds__(256) k_sh_partials(const uint4* __restrict__ chunks, const uint64_t* n_chunks_dev,
+                                                     const uint32_t* __restrict__ ids, const float* __restrict__ pos,
+                                                     const ViewInfo* __restrict__ views, int n_views, int64_t n,
+                                                     const float* __restrict__ drgb, float* __restrict__ part) {
+  const int64_t nch = (int64_t)*n_chunks_dev;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); c < nch; c += warps) {
+    const uint4 ch = chunks[c];
+    float acc[NB * 3];
+#pragma unroll
+    for (int e = 0; e < NB * 3; ++e) acc[e] = 0.0f;
+    for (uint32_t i = ch.y + lane; i < ch.z; i += 32) {
+      const uint32_t g = ids[i];
+      const float p0 = pos[3 * (size_t)g], p1 = pos[3 * (size_t)g + 1], p2 = pos[3 * (size_t)g + 2];
+      for (int v = 0; v < n_views; ++v) {
+        const float* d = drgb + 3 * ((size_t)v * n + g);
+        const float d0 = d[0], d1 = d[1], d2 = d[2];
+        if (d0 == 0.0f && d1 == 0.0f && d2 == 0.0f) continue;
+        const ViewInfo& cam = views[v];
+        const float dx = p0 - cam.campos[0], dy = p1 - cam.campos[1], dz = p2 - cam.campos[2];
+        const float inv = 1.0f / sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        float Y[kMaxBasis];
+        sh_basis_only<NB>(dx * inv, dy * inv, dz * inv, Y);
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+          acc[3 * k] = fmaf(Y[k], d0, acc[3 * k]);
+          acc[3 * k + 1] = fmaf(Y[k], d1, acc[3 * k + 1]);
+          acc[3 * k + 2] = fmaf(Y[k], d2, acc[3 * k + 2]);
+        }
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < NB * 3; ++e) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int e = 0; e < NB * 3; ++e) part[(size_t)NB * 3 * c + e] = acc[e];
+    }
+  }
+}
+
+// Gradient through Eq. 2 of one SR row given dL/dSigma (unique entries), FP32.
+__device__ void sigma3_backward(const float* row, const float* g, float* drow) {
+  const float s[3] = {exp32(row[0]), exp32(row[1]), exp32(row[2])};
+  const float qn2 = row[3] * row[3] + row[4] * row[4] + row[5] * row[5] + row[6] * row[6];
+  const float nrm = sqrtf(qn2);
+  float w = 1.0f, x = 0.0f, y = 0.0f, z = 0.0f;
+  if (qn2 > 0.0f) {
+    w = row[3] / nrm;
+    x = row[4] / nrm;
+    y = row[5] / nrm;
+    z = row[6] / nrm;
+  }
+  const float R[9] = {1.0f - 2.0f * (y * y + z * z), 2.0f * (x * y - w * z), 2.0f * (x * z + w * y),
+                      2.0f * (x * y + w * z), 1.0f - 2.0f * (x * x + z * z), 2.0f * (y * z - w * x),
+                      2.0f * (x * z - w * y), 2.0f * (y * z + w * x), 1.0f - 2.0f * (x * x + y * y)};
+  const float G[9] = {g[0], 0.5f * g[1], 0.5f * g[2], 0.5f * g[1], g[3], 0.5f * g[4], 0.5f * g[2], 0.5f * g[4], g[5]};
+  float M[9], dM[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) M[3 * a + j] = R[3 * a + j] * s[j];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      dM[3 * a + j] = 2.0f * fmaf(G[3 * a], M[j], fmaf(G[3 * a + 1], M[3 + j], G[3 * a + 2] * M[6 + j]));
+  float ds[3] = {0.0f, 0.0f, 0.0f}, dR[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      ds[j] = fmaf(dM[3 * a + j], R[3 * a + j], ds[j]);
+      dR[3 * a + j] = dM[3 * a + j] * s[j];
+    }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) drow[j] = ds[j] * s[j];
+  float dq[4];
+  dq[0] = 2.0f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+  dq[1] = 2.0f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.0f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] -
+                  2.0f * x * dR[8]);
+  dq[2] = 2.0f * (-2.0f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] -
+                  2.0f * y * dR[8]);
+  dq[3] = 2.0f * (-2.0f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.0f * z * dR[4] + y * dR[5] +
+                  x * dR[6] + y * dR[7]);
+  if (qn2 > 0.0f) {
+    const float dot = dq[0] * w + dq[1] * x + dq[2] * y + dq[3] * z;
+    drow[3] = (dq[0] - w * dot) / nrm;
+    drow[4] = (dq[1] - x * dot) / nrm;
+    drow[5] = (dq[2] - y * dot) / nrm;
+    drow[6] = (dq[3] - z * dot) / nrm;
+  } else {
+    drow[3] = drow[4] = drow[5] = drow[6] = 0.0f;
+  }
+  drow[7] = 0.0f;
+}
+
+__global__ void k_sr_rows(const uint32_t* __restrict__ counts, const uint32_t* __restrict__ chunk_base, int k_sr,
+                          const float* __restrict__ part, const void* __restrict__ rows, int dtype,
+                          float* __restrict__ d_sr) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= k_sr) return;
+  const uint32_t nch = (counts[r] + kChunk - 1) / kChunk, cb = chunk_base[r];
+  float g[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  for (uint32_t c = 0; c < nch; ++c)
+#pragma unroll
+    for (int e = 0; e < 6; ++e) g[e] += part[6 * (size_t)(cb + c) + e];
+  float row[8];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) row[i] = load_row(rows, dtype, (size_t)r * CG_SR_WIDTH + i);
+  row[7] = 0.0f;
+  float drow[8];
+  sigma3_backward(row, g, drow);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) d_sr[(size_t)r * 8 + i] = drow[i];
+}
+
+__global__ void k_sh_rows(const uint32_t* __restrict__ counts, const uint32_t* __restrict__ chunk_base, int k_sh,
+                          int width, const float* __restrict__ part, float* __restrict__ d_sh) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)k_sh * width) return;
+  const int r = (int)(i / width), e = (int)(i - (int64_t)r * width);
+  const uint32_t nch = (counts[r] + kChunk - 1) / kChunk, cb = chunk_base[r];
+  float s = 0.0f;
+  for (uint32_t c = 0; c < nch; ++c) s += part[(size_t)width * (cb + c) + e];
+  d_sh[i] = s;
+}
+
+// CSR of one index array; returns member ids (sorted by row, then Gaussian),
+// counts, row offsets, chunk bases and chunk table (chunk count in *nch_dev).
+static cudaError_t build_csr(void* ws, const Layout& L, const uint16_t* idx, int k, uint32_t* row_off,
+                             uint32_t* ids, uint32_t* counts, uint32_t* chunk_base, uint4* chunks, uint64_t* slot_a,
+                             uint64_t* slot_b, cudaStream_t s) {
+  const int64_t n = L.n;
+  uint64_t* k0 = ws_ptr<uint64_t>(ws, L.dkeys0);
+  uint64_t* k1 = ws_ptr<uint64_t>(ws, L.dkeys1);
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
+  const int gk = std::max(1, std::min((k + 255) / 256, 152 * 8));
+  k_zero_counts<<<gk, 256, 0, s>>>(counts, k);
+  k_row_keys<<<g, 256, 0, s>>>(idx, n, k, k0, counts, slot_a);
+  bool in_b = false;
+  cudaError_t e = sort_u64(ws, L, k0, k1, slot_a, n, 32, k >= 65536 ? 3 : 2, &in_b, s);
+  if (e != cudaSuccess) return e;
+  k_ids_from_keys<<<g, 256, 0, s>>>(in_b ? k1 : k0, n, ids);
+  k_chunk_counts<<<gk, 256, 0, s>>>(counts, k, chunk_base, slot_b);
+  e = scan_u32(ws, L, counts, row_off, slot_b, k, slot_a, s);  // slot_a <- n (total)
+  if (e != cudaSuccess) return e;
+  e = scan_u32(ws, L, chunk_base, chunk_base, slot_b, k, slot_a, s);  // slot_a <- chunk count
+  if (e != cudaSuccess) return e;
+  k_fill_chunks<<<gk, 256, 0, s>>>(row_off, counts, chunk_base, k, chunks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_codebook_reduce(const SceneArgs& sc, const Layout& L, void* ws, float* d_sr, float* d_sh,
+                                   cudaStream_t s) {
+  WsHeader* hdr = ws_ptr<WsHeader>(ws, L.hdr);
+  uint64_t* slot_a = &hdr->st.scan_total;
+  uint64_t* slot_b = &hdr->st.visible;  // scratch here; rewritten by the next forward
+  uint4* chunks = ws_ptr<uint4>(ws, L.chunks);
+  float* part = ws_ptr<float>(ws, L.partials);
+  uint32_t* cnt = ws_ptr<uint32_t>(ws, L.csr_off_sr) + (L.k_sr + 1);  // counts after offsets
+  uint32_t* cbase = cnt + L.k_sr;
+  // SR rows
+  cudaError_t e = build_csr(ws, L, sc.g2sr, sc.k_sr, ws_ptr<uint32_t>(ws, L.csr_off_sr),
+                            ws_ptr<uint32_t>(ws, L.csr_ids_sr), cnt, cbase, chunks, slot_a, slot_b, s);
+  if (e != cudaSuccess) return e;
+  const int gw = 152 * 8;
+  k_sr_partials<<<gw, 256, 0, s>>>(chunks, slot_a, ws_ptr<uint32_t>(ws, L.csr_ids_sr), ws_ptr<float>(ws, L.dsigma),
+                                  part);
+  k_sr_rows<<<(sc.k_sr + 127) / 128, 128, 0, s>>>(cnt, cbase, sc.k_sr, part, sc.sr_rows, sc.dtype, d_sr);
+  // SH rows
+  uint32_t* cnt2 = ws_ptr<uint32_t>(ws, L.csr_off_sh) + (L.k_sh + 1);
+  uint32_t* cbase2 = cnt2 + L.k_sh;
+  e = build_csr(ws, L, sc.g2sh, sc.k_sh, ws_ptr<uint32_t>(ws, L.csr_off_sh), ws_ptr<uint32_t>(ws, L.csr_ids_sh), cnt2,
+                cbase2, chunks, slot_a, slot_b, s);
+  if (e != cudaSuccess) return e;
+  const ViewInfo* views = ws_ptr<ViewInfo>(ws, L.views);
+  const uint32_t* ids = ws_ptr<uint32_t>(ws, L.csr_ids_sh);
+  const float* drgb = ws_ptr<float>(ws, L.drgb);
+#define CG_SHP(NBV) k_sh_partials<NBV><<<gw, 256, 0, s>>>(chunks, slot_a, ids, sc.pos, views, L.n_views, L.n, drgb, part)
+  switch (sc.nb) {
+    case 1: CG_SHP(1); break;
+    case 4: CG_SHP(4); break;
+    case 9: CG_SHP(9); break;
+    case 16: CG_SHP(16); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef CG_SHP
+  const int width = sc.nb * 3;
+  const int64_t tot = (int64_t)sc.k_sh * width;
+  k_sh_rows<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(cnt2, cbase2, sc.k_sh, width, part, d_sh);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// L1 loss harness
+// ---------------------------------------------------------------------------
+
+constexpr int kL1Blocks = 1024;
+
+__global__ void __launch_bounds__(256) k_l1(const float* __restrict__ img, const float* __restrict__ tgt,
+                                            int64_t count, float* __restrict__ d_img, double* __restrict__ part) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  const float inv = 1.0f / (float)count;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    const float d = img[i] - tgt[i];
+    acc += (double)fabsf(d);
+    d_img[i] = d > 0.0f ? inv : (d < 0.0f ? -inv : 0.0f);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_l1_final(const double* __restrict__ part, int64_t count, double* loss) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < kL1Blocks; i += blockDim.x) acc += part[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+    *loss = t / (double)count;
+  }
+}
+
+cudaError_t launch_l1(const float* img, const float* tgt, int64_t count, float* d_img, double* loss,
+                      const Layout& L, void* ws, cudaStream_t s) {
+  double* part = ws_ptr<double>(ws, L.l1);
+  k_l1<<<kL1Blocks, 256, 0, s>>>(img, tgt, count, d_img, part);
+  k_l1_final<<<1, 256, 0, s>>>(part, count, loss);
+  return cudaGetLastError();
+}
+
+}  // namespace cg

@@ -1,0 +1,164 @@
+// k_preprocess.cu -- workspace setup, Eq. 2 per SR row, and the per (view,
+// Gaussian) projection record: gather of the Gaussian's codebook rows
+// (Sec. 3.1), EWA projection of Eq. 1 onto the image plane, SH colour,
+// 3-sigma tile rectangle and FP32 depth key.
+#include <algorithm>
+
+#include "cg_common.cuh"
+
+namespace cg {
+
+__global__ void k_setup(const __grid_constant__ ViewTable table, const __grid_constant__ Layout L, void* ws) {
+  WsHeader* hdr = ws_ptr<WsHeader>(ws, L.hdr);
+  ViewInfo* views = ws_ptr<ViewInfo>(ws, L.views);
+  for (int i = threadIdx.x; i < table.n_views; i += blockDim.x) views[i] = table.v[i];
+  if (threadIdx.x == 0) {
+    hdr->magic = kMagic;
+    hdr->layout = L;
+    DeviceState st = {};
+    hdr->st = st;
+  }
+}
+
+cudaError_t launch_setup(const ViewTable& table, const Layout& L, void* ws, cudaStream_t s) {
+  k_setup<<<1, 64, 0, s>>>(table, L, ws);
+  return cudaGetLastError();
+}
+
+// Eq. 2 per SR row (FP32 decision arithmetic), 6 unique entries per row.
+__global__ void k_sigma3(const void* __restrict__ rows, int dtype, int k_sr, float* __restrict__ sig) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= k_sr) return;
+  float row[8];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) row[i] = load_row(rows, dtype, (size_t)k * CG_SR_WIDTH + i);
+  row[7] = 0.0f;
+  float out[6];
+  sigma3_from_row(row, out);
+#pragma unroll
+  for (int e = 0; e < 6; ++e) sig[(size_t)k * 6 + e] = out[e];
+}
+
+cudaError_t launch_sigma3(const SceneArgs& sc, const Layout& L, void* ws, cudaStream_t s) {
+  k_sigma3<<<(sc.k_sr + 127) / 128, 128, 0, s>>>(sc.sr_rows, sc.dtype, sc.k_sr, ws_ptr<float>(ws, L.sigma3));
+  return cudaGetLastError();
+}
+
+// One thread per (view, Gaussian) record, record = v * n + g.
+template <int NB>
+__global__ void __launch_bounds__(256) k_preprocess(const SceneArgs sc, const ViewInfo* __restrict__ views,
+                                                    int n_views, int tile, const float* __restrict__ sig3,
+                                                    float4* __restrict__ geo, float4* __restrict__ rgbm,
+                                                    ushort4* __restrict__ rect, uint32_t* __restrict__ ntiles,
+                                                    uint32_t* __restrict__ depth, DeviceState* st) {
+  const int64_t R = (int64_t)sc.n * n_views;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t rec = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; rec < R; rec += stride) {
+    const int v = (int)(rec / sc.n);
+    const int64_t g = rec - (int64_t)v * sc.n;
+    const ViewInfo& cam = views[v];
+    ntiles[rec] = 0u;
+    rect[rec] = make_ushort4(0, 0, 0, 0);
+    depth[rec] = 0xffffffffu;
+    const uint32_t isr = sc.g2sr[g], ish = sc.g2sh[g];
+    if (isr >= (uint32_t)sc.k_sr || ish >= (uint32_t)sc.k_sh) {
+      set_status(st, CG_ERR_INDEX, (uint32_t)g);
+      continue;
+    }
+    const float p0 = sc.pos[3 * g], p1 = sc.pos[3 * g + 1], p2 = sc.pos[3 * g + 2];
+    const float* W = cam.w2c;
+    float t[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) t[a] = fmaf(W[4 * a], p0, fmaf(W[4 * a + 1], p1, fmaf(W[4 * a + 2], p2, W[4 * a + 3])));
+    if (!(t[2] > cam.near_z)) continue;
+    const float tz = t[2];
+    const float u = t[0] / tz, w = t[1] / tz;
+    const float fx = cam.fx, fy = cam.fy;
+    const float J00 = fx / tz, J02 = -(fx * u) / tz, J11 = fy / tz, J12 = -(fy * w) / tz;
+    float T[6];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      T[j] = fmaf(J00, W[j], J02 * W[8 + j]);
+      T[3 + j] = fmaf(J11, W[4 + j], J12 * W[8 + j]);
+    }
+    const float* sg = sig3 + (size_t)isr * 6;
+    const float S[9] = {sg[0], sg[1], sg[2], sg[1], sg[3], sg[4], sg[2], sg[4], sg[5]};
+    float U[6];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        U[3 * a + j] = fmaf(T[3 * a], S[j], fmaf(T[3 * a + 1], S[3 + j], T[3 * a + 2] * S[6 + j]));
+    const float A = fmaf(U[0], T[0], fmaf(U[1], T[1], U[2] * T[2])) + kDilation;
+    const float B = fmaf(U[0], T[3], fmaf(U[1], T[4], U[2] * T[5]));
+    const float C = fmaf(U[3], T[3], fmaf(U[4], T[4], U[5] * T[5])) + kDilation;
+    const float det = fmaf(A, C, -(B * B));
+    if (!(det > 0.0f)) continue;
+    const float mid = 0.5f * (A + C);
+    const float disc = fmaf(mid, mid, -det);
+    const float lam = mid + sqrtf(disc > kLambdaFloor ? disc : kLambdaFloor);
+    const float rad = ceilf(3.0f * sqrtf(lam));
+    const float mx = fmaf(fx, u, cam.cx), my = fmaf(fy, w, cam.cy);
+    const float ts = (float)tile, tm1 = (float)(tile - 1);
+    float fx0 = floorf((mx - rad) / ts), fx1 = floorf(((mx + rad) + tm1) / ts);
+    float fy0 = floorf((my - rad) / ts), fy1 = floorf(((my + rad) + tm1) / ts);
+    const float TX = (float)cam.tiles_x, TY = (float)cam.tiles_y;
+    fx0 = fx0 < 0.0f ? 0.0f : (fx0 > TX ? TX : fx0);
+    fx1 = fx1 < 0.0f ? 0.0f : (fx1 > TX ? TX : fx1);
+    fy0 = fy0 < 0.0f ? 0.0f : (fy0 > TY ? TY : fy0);
+    fy1 = fy1 < 0.0f ? 0.0f : (fy1 > TY ? TY : fy1);
+    const int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1;
+    if (x1 <= x0 || y1 <= y0) continue;
+    const float c0 = C / det, c1 = -B / det, c2 = A / det;
+    const float o = sigmoid32(sc.logit[g]);
+    // conservative skip bound: power below it means o * exp32(power) < 1/255
+    const float pthr = -logf(255.0f * o) - 1e-3f;
+    // SH colour with its clamp at zero (decision arithmetic)
+    const float dx = p0 - cam.campos[0], dy = p1 - cam.campos[1], dz = p2 - cam.campos[2];
+    const float nrm = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    float Y[kMaxBasis];
+    sh_basis32(NB, dx / nrm, dy / nrm, dz / nrm, Y);
+    const size_t rb = (size_t)ish * NB * 3;
+    float col[3];
+    uint32_t mask = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float acc = load_row(sc.sh_rows, sc.dtype, rb + c) * Y[0];
+#pragma unroll
+      for (int k = 1; k < NB; ++k) acc = fmaf(load_row(sc.sh_rows, sc.dtype, rb + 3 * k + c), Y[k], acc);
+      const float pre = acc + 0.5f;
+      if (pre < 0.0f) mask |= 1u << c;
+      col[c] = pre < 0.0f ? 0.0f : pre;
+    }
+    geo[2 * rec] = make_float4(mx, my, -0.5f * c0, -c1);
+    geo[2 * rec + 1] = make_float4(-0.5f * c2, o, pthr, 0.0f);
+    rgbm[rec] = make_float4(col[0], col[1], col[2], (float)mask);
+    rect[rec] = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1);
+    ntiles[rec] = (uint32_t)((x1 - x0) * (y1 - y0));
+    depth[rec] = float_to_bits(tz);
+  }
+}
+
+cudaError_t launch_preprocess(const SceneArgs& sc, const Layout& L, void* ws, cudaStream_t s) {
+  WsHeader* hdr = ws_ptr<WsHeader>(ws, L.hdr);
+  const int64_t R = L.R;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((R + 255) / 256, 152 * 16));
+  const ViewInfo* views = ws_ptr<ViewInfo>(ws, L.views);
+  const float* sig = ws_ptr<float>(ws, L.sigma3);
+  float4* geo = ws_ptr<float4>(ws, L.geo);
+  float4* rgbm = ws_ptr<float4>(ws, L.rgbm);
+  ushort4* rect = ws_ptr<ushort4>(ws, L.rect);
+  uint32_t* nt = ws_ptr<uint32_t>(ws, L.ntiles);
+  uint32_t* dp = ws_ptr<uint32_t>(ws, L.depth);
+  DeviceState* st = &hdr->st;
+  switch (sc.nb) {
+    case 1: k_preprocess<1><<<grid, 256, 0, s>>>(sc, views, L.n_views, L.tile, sig, geo, rgbm, rect, nt, dp, st); break;
+    case 4: k_preprocess<4><<<grid, 256, 0, s>>>(sc, views, L.n_views, L.tile, sig, geo, rgbm, rect, nt, dp, st); break;
+    case 9: k_preprocess<9><<<grid, 256, 0, s>>>(sc, views, L.n_views, L.tile, sig, geo, rgbm, rect, nt, dp, st); break;
+    case 16: k_preprocess<16><<<grid, 256, 0, s>>>(sc, views, L.n_views, L.tile, sig, geo, rgbm, rect, nt, dp, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace cg

@@ -1,0 +1,202 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Discrete outputs -- tile rectangles, depth keys, the sorted pair list, per-
+tile ranges, contributor counts and the FP32 decision records -- must be
+bit-exact.  Images must agree within 1e-4 absolute.  Gradients must agree
+within 1e-3 relative or an absolute floor of 1e-6 times the largest
+magnitude of that gradient array (FP32 accumulation over thousands of pixel
+terms cannot do better in absolute terms on entries that cancel).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_03775_gb300 import cg, scenes
+
+pytestmark = pytest.mark.gpu
+
+IMG_ATOL = 1e-4
+GRAD_RTOL = 1e-3
+GRAD_AFLOOR = 1e-6
+
+
+def _run_gpu(scene, cams, d_image, tile=16, batch=0, bg=(0.0, 0.0, 0.0), bf16=False, pair_capacity=1 << 16):
+    r = cg.Renderer(cams, tile=tile, batch=batch, bg=bg, pair_capacity=pair_capacity)
+    st = cg.SceneTensors.from_scene(scene, codebook_dtype=torch.bfloat16 if bf16 else torch.float32)
+    img = r.forward(st)
+    d_pos, d_logit = r.backward(torch.from_numpy(d_image.astype(np.float32)).cuda())
+    d_sr, d_sh = r.codebook_reduce()
+    torch.cuda.synchronize()
+    out = {
+        "image": img.cpu().numpy().astype(np.float64),
+        "rect": r.array(cg.WS_RECT, torch.int16, 4).cpu().numpy().view(np.uint16).reshape(-1, 4),
+        "depth": r.array(cg.WS_DEPTH, torch.int32).cpu().numpy().view(np.uint32),
+        "pairs": r.array(cg.WS_PAIRS, torch.int64).cpu().numpy().view(np.uint64),
+        "ranges": r.array(cg.WS_RANGES, torch.int32, 2).cpu().numpy().view(np.uint32).reshape(-1, 2),
+        "ncontrib": r.array(cg.WS_NCONTRIB, torch.int32).cpu().numpy().view(np.uint32),
+        "tfinal": r.array(cg.WS_TFINAL, torch.float32).cpu().numpy(),
+        "geo": r.array(cg.WS_GEO, torch.float32, 8).cpu().numpy().reshape(-1, 8),
+        "rgbm": r.array(cg.WS_RGB, torch.float32, 4).cpu().numpy().reshape(-1, 4),
+        "dpos": d_pos.cpu().numpy().astype(np.float64),
+        "dlogit": d_logit.cpu().numpy().astype(np.float64),
+        "d_sr": d_sr.cpu().numpy().astype(np.float64),
+        "d_sh": d_sh.cpu().numpy().astype(np.float64),
+        "renderer": r,
+    }
+    return out
+
+
+def _oracle_scene(scene, bf16):
+    if not bf16:
+        return scene
+    s = scene.copy()
+    s.sr_rows = scenes.bf16_round(scene.sr_rows)
+    s.sh_rows = scenes.bf16_round(scene.sh_rows)
+    return s
+
+
+def _l1_grad(ref, target_img):
+    d = np.sign(ref.image - target_img)
+    return d / d.size
+
+
+def _assert_grad(name, got, want):
+    got = got.reshape(want.shape)
+    floor = GRAD_AFLOOR * max(np.abs(want).max(), 1e-30)
+    err = np.abs(got - want)
+    bad = err > GRAD_RTOL * np.abs(want) + floor
+    assert not bad.any(), (f"{name}: {bad.sum()} of {bad.size} entries off; worst rel "
+                           f"{(err / (np.abs(want) + floor)).max():.3e}")
+
+
+def _compare(ref, gpu, check_grads=True):
+    q = ref.rec32
+    vis = q["visible"].astype(bool)
+    # decision records
+    rect_ref = np.stack([q["x0"], q["y0"], q["x1"], q["y1"]], 1).astype(np.uint16)
+    assert np.array_equal(gpu["rect"], rect_ref)
+    assert np.array_equal(gpu["depth"][vis], q["depth_bits"][vis])
+    geo = gpu["geo"]
+    for j, f in enumerate(["mx", "my", "h0", "h1", "h2", "o"]):
+        assert np.array_equal(geo[vis, j].view(np.uint32), q[f][vis].view(np.uint32)), f
+    assert np.array_equal(gpu["rgbm"][vis, 3].astype(np.uint32), q["rgb_clamped"][vis])
+    # sorted pairs and ranges
+    pairs = gpu["pairs"]
+    assert pairs.size == ref.k_pairs
+    assert np.array_equal(pairs >> np.uint64(32), ref.keys >> np.uint64(32))
+    assert np.array_equal((pairs & np.uint64(0xffffffff)).astype(np.uint32), ref.list)
+    assert np.array_equal(gpu["ranges"], ref.ranges)
+    # per-pixel outputs
+    assert np.array_equal(gpu["ncontrib"], ref.n_contrib.astype(np.uint32))
+    assert np.abs(gpu["tfinal"] - ref.t_final).max() < 1e-5
+    assert np.abs(gpu["image"] - ref.image).max() < IMG_ATOL
+    if check_grads:
+        g = ref.grads
+        _assert_grad("d_pos", gpu["dpos"], g["dpos"])
+        _assert_grad("d_logit", gpu["dlogit"], g["dlogit"])
+        _assert_grad("d_sr", gpu["d_sr"][:, :7], g["d_sr"][:, :7])
+        assert np.all(gpu["d_sr"][:, 7] == 0)
+        _assert_grad("d_sh", gpu["d_sh"], g["d_sh"])
+
+
+def _case(scene, cams, tile=16, bg=(0.0, 0.0, 0.0), bf16=False, target=None, batch=0):
+    oscene = _oracle_scene(scene, bf16)
+    ref = oracle.Render(oscene, cams, tile=tile, bg=bg)
+    if target is None:
+        d_image = np.random.default_rng(11).normal(size=ref.image.shape) / ref.image.size
+    else:
+        tref = oracle.Render(_oracle_scene(target, bf16), cams, tile=tile, bg=bg)
+        d_image = _l1_grad(ref, tref.image)
+    ref.grads = ref.backward(d_image)
+    gpu = _run_gpu(scene, cams, d_image, tile=tile, bg=bg, bf16=bf16, batch=batch)
+    return ref, gpu
+
+
+def test_tiny_l1():
+    scene, cams, target = scenes.config_tiny()
+    ref, gpu = _case(scene, cams, target=target)
+    _compare(ref, gpu)
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_tile_sizes_and_background(tile):
+    scene, cams, _ = scenes.config_tiny()
+    cams = [scenes.look_at(cams[0].campos, 150, 97)]  # ragged edge tiles
+    ref, gpu = _case(scene, cams, tile=tile, bg=(0.2, 0.5, 0.9))
+    _compare(ref, gpu)
+
+
+@pytest.mark.parametrize("batch", [32, 64, 128, 256])
+def test_batch_sizes(batch):
+    scene, cams, _ = scenes.config_tiny()
+    ref, gpu = _case(scene, cams, batch=batch)
+    _compare(ref, gpu)
+
+
+def test_single_view_degree3_zipf_reduced():
+    scene, cams = scenes.config_single(n=30_000, k=1024, width=320, height=256)
+    ref, gpu = _case(scene, cams)
+    _compare(ref, gpu)
+
+
+def test_uneven_views_one_launch():
+    scene, _ = scenes.config_single(n=20_000, k=512, width=8, height=8)
+    rng = np.random.default_rng(3)
+    dirs = scenes.fibonacci_dirs(4, rng)
+    res = [(196, 109), (128, 72), (80, 80), (33, 47)]
+    cams = [scenes.look_at(3.2 * d, w, h) for d, (w, h) in zip(dirs, res)]
+    ref, gpu = _case(scene, cams, bg=(0.1, 0.1, 0.1))
+    _compare(ref, gpu)
+
+
+def test_bf16_codebooks():
+    scene, cams = scenes.config_single(n=20_000, k=512, width=160, height=128)
+    ref, gpu = _case(scene, cams, bf16=True)
+    _compare(ref, gpu)
+
+
+def test_deterministic_bitwise():
+    scene, cams = scenes.config_single(n=20_000, k=256, width=160, height=160)
+    d = np.random.default_rng(5).normal(size=3 * 160 * 160) * 1e-3
+    a = _run_gpu(scene, cams, d)
+    b = _run_gpu(scene, cams, d)
+    for k in ("image", "dpos", "dlogit", "d_sr", "d_sh", "pairs"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_index_error_reported():
+    scene, cams, _ = scenes.config_tiny()
+    bad = scene.copy()
+    bad.g2sr = bad.g2sr.copy()
+    bad.g2sr[7] = 64   # == k_sr
+    r = cg.Renderer(cams)
+    with pytest.raises(cg.CgError) as e:
+        r.forward(cg.SceneTensors.from_scene(bad))
+    assert e.value.status == cg.CG_ERR_INDEX
+
+
+def test_capacity_overflow_reported_and_recovered():
+    scene, cams, _ = scenes.config_tiny()
+    ref = oracle.Render(scene, cams)
+    r = cg.Renderer(cams, pair_capacity=100)
+    st = cg.SceneTensors.from_scene(scene)
+    r.forward(st, check=False)
+    status, pairs = r.status()
+    assert status == cg.CG_ERR_CAPACITY and pairs == ref.k_pairs
+    img = r.forward(st)   # grows the workspace and re-renders
+    assert r.pair_capacity >= ref.k_pairs
+    assert np.abs(img.cpu().numpy() - ref.image).max() < IMG_ATOL
+
+
+def test_l1_loss_kernel():
+    rng = np.random.default_rng(2)
+    a = rng.normal(size=100_003).astype(np.float32)
+    b = rng.normal(size=100_003).astype(np.float32)
+    scene, cams, _ = scenes.config_tiny()
+    r = cg.Renderer(cams)
+    r.forward(cg.SceneTensors.from_scene(scene))
+    loss, d = r.l1_loss(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda())
+    ref = np.abs(a.astype(np.float64) - b).mean()
+    assert abs(loss.item() - ref) < 1e-9 * max(1.0, ref)
+    assert np.array_equal(np.sign(d.cpu().numpy()), np.sign(a - b))

@@ -1,0 +1,86 @@
+"""The C ABI library loads, exports every symbol include/cg.h declares, and
+its host twins of the FP32 decision arithmetic agree bit for bit with the
+oracle's.  No GPU needed."""
+import ctypes
+import re
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_03775_gb300 import _build, cg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return cg.load()
+
+
+def test_header_declares_exactly_the_exports(lib):
+    hdr = open(os.path.join(ROOT, "include", "cg.h")).read()
+    declared = sorted(set(re.findall(r"\b(cg_[a-z0-9_]+)\s*\(", hdr)))
+    assert declared == sorted(cg.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_version(lib):
+    assert b"sm_103a" in lib.cg_version()
+
+
+def test_host_exp32_matches_oracle_bitwise(lib):
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.uniform(-90, 90, 20000), rng.uniform(-8, 1, 20000),
+                        [-87.0, -86.99999, 0.0, -0.0, 87.9999, 88.0, np.inf, -np.inf, np.nan]]).astype(np.float32)
+    mine = np.array([lib.cg_host_exp32(float(v)) for v in x], dtype=np.float32)
+    ref = oracle.e32(x)
+    assert np.array_equal(mine.view(np.uint32), ref.view(np.uint32))
+
+
+def test_host_sh_consts_match_oracle_bitwise(lib):
+    out = np.zeros(16, dtype=np.float32)
+    lib.cg_host_sh_consts(out.ctypes.data_as(ctypes.c_void_p))
+    assert np.array_equal(out.view(np.uint32), oracle.sh_consts32().view(np.uint32))
+
+
+def test_host_sigma3_matches_oracle_bitwise(lib):
+    rng = np.random.default_rng(1)
+    for _ in range(2000):
+        row = np.zeros(8, dtype=np.float32)
+        row[:3] = rng.normal(-3, 1.0, 3)
+        row[3:7] = rng.normal(size=4)
+        out = np.zeros(6, dtype=np.float32)
+        lib.cg_host_sigma3(row.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p))
+        assert np.array_equal(out.view(np.uint32), oracle.sr_sigma32(row).view(np.uint32))
+
+
+def test_workspace_bytes_and_argument_checks(lib):
+    from paper_2509_03775_gb300 import scenes
+    scene, cams, _ = scenes.config_tiny()
+    sc = cg.Scene(scene.n, scene.k_sr, scene.k_sh, scene.sh_degree, cg.CG_F32, 16, 16, 16, 16, 16, 16)
+    camarr = cg.camera_array(cams)
+    o = cg.Opts()
+    o.tile, o.batch, o.pair_capacity = 16, 0, 10000
+    n1 = lib.cg_workspace_bytes(ctypes.byref(sc), camarr, 1, ctypes.byref(o))
+    o.pair_capacity = 20000
+    n2 = lib.cg_workspace_bytes(ctypes.byref(sc), camarr, 1, ctypes.byref(o))
+    assert n1 > 0 and n2 > n1
+    # per extra pair: two sort buffers (16 B) + pair gradient (36 B) + sort histograms
+    assert 52 * 10000 <= n2 - n1 <= 54 * 10000 + 4096
+    o.tile = 12
+    assert lib.cg_workspace_bytes(ctypes.byref(sc), camarr, 1, ctypes.byref(o)) == 0
+    o.tile = 16
+    sc.sh_degree = 4
+    assert lib.cg_workspace_bytes(ctypes.byref(sc), camarr, 1, ctypes.byref(o)) == 0
+    sc.sh_degree = 1
+    assert lib.cg_workspace_bytes(ctypes.byref(sc), camarr, 0, ctypes.byref(o)) == 0
+    # host-detectable errors come back before any launch (no GPU needed)
+    ws = ctypes.c_void_p(256)
+    img = ctypes.c_void_p(1024)
+    assert lib.cg_render_fwd(ctypes.byref(sc), camarr, 1, ctypes.byref(o), ws, 16, img, None) == cg.CG_ERR_ARG
+    sc.pos = 0
+    assert lib.cg_render_fwd(ctypes.byref(sc), camarr, 1, ctypes.byref(o), ws, n2, img, None) == cg.CG_ERR_ARG
