@@ -1,0 +1,497 @@
+"""Benchmark of the codebook Gaussian rasterizer's training-step hot path.
+
+One step = forward render of one view (codebook gather, Eq. 2, EWA
+projection, SH colour, keys, radix sort, per-tile compositing of Eq. 3),
+the L1 loss gradient against a resident target image, the backward
+(reverse compositing, per-Gaussian chain rule) and the deterministic
+codebook reduction -- every stage in libcg's kernels.
+
+Default workload (N = 1): the truck-shaped scene, 1.5M Gaussians, SH
+degree 3, 8192 rows per codebook, one 1957x1091 camera, FP32 codebooks.
+With torchrun (N > 1) every rank renders its own view of the same scene
+(weak scaling, no data-path collective; only the timing is reduced).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cg|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd renders/sec at 1.5M Gaussians 1957x1091; % of GB300 HBM roofline"
+HBM_PEAK_FALLBACK = 6800.0
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_NOMINAL = 2070.0
+
+# Algorithmic FP32 operations per (pixel, listed Gaussian) evaluation of the
+# blend kernels (an FMA counts 2): the quadratic form of Eq. 1 (10), exp (19),
+# alpha and the Eq. 3 update (10) in the forward; the same recomputation (30)
+# plus the Eq. 3 derivatives (55) in the backward.
+FLOPS_PER_EVAL = {"blend_fwd": 39, "blend_bwd": 85}
+
+# DRAM bytes per launch measured by ncu for a kernel, keyed by the SHA-256 of
+# the kernel's source file at capture time (summaries under profiles/).  A
+# changed source reports null.
+NCU_TRAFFIC = {}
+
+
+def _src_hash(name: str) -> str:
+    path = os.path.join(ROOT, "paper_2509_03775_gb300", "csrc", name)
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+KERNEL_SOURCE = {"preprocess": "k_preprocess.cu", "sort": "k_sort.cu", "blend_fwd": "k_blend.cu",
+                 "blend_bwd": "k_blend.cu", "gauss_bwd": "k_grad.cu", "reduce": "k_grad.cu"}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+def make_workload(name: str):
+    from paper_2509_03775_gb300 import scenes
+    if name == "truck":
+        scene, cams = scenes.config_truck()
+        desc = ("truck-shaped synthetic scene: 1.5M Gaussians (64-cluster anisotropic mixture, log-scales "
+                "N(-4,0.5)), SH degree 3, 8192 SR + 8192 SH rows (Zipf 1.1 usage), FP32 codebooks, "
+                "one 1957x1091 camera at radius 4, FOV 60 deg, 16x16 tiles")
+    elif name == "single":
+        scene, cams = scenes.config_single()
+        desc = "single view: 200k Gaussians, SH degree 3, 4096+4096 rows (Zipf 1.1), 800x800"
+    elif name == "tiny":
+        scene, cams, _ = scenes.config_tiny()
+        desc = "tiny: 1024 Gaussians, SH degree 1, 64+64 rows, 128x128"
+    else:
+        raise ValueError(name)
+    target = scene.copy()
+    rng = np.random.default_rng(4242)
+    target.pos = (scene.pos + rng.normal(0.0, 0.01, size=scene.pos.shape)).astype(np.float32)
+    return scene, cams, target, desc
+
+
+def rank_camera(cams, rank: int):
+    """The camera of one rank: rank 0 keeps the workload's view, others orbit
+    the scene at the same radius and resolution (same per-rank work shape)."""
+    from paper_2509_03775_gb300 import scenes
+    if rank == 0:
+        return cams
+    c = cams[0]
+    eye = np.asarray(c.campos, dtype=np.float64)
+    ang = 2.0 * math.pi * rank / 16.0
+    rot = np.array([[math.cos(ang), 0.0, math.sin(ang)], [0.0, 1.0, 0.0], [-math.sin(ang), 0.0, math.cos(ang)]])
+    return [scenes.look_at(rot @ eye, c.width, c.height)]
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (host logic; covered by CPU gloo tests)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def whole_job_value(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Weak scaling: every rank processes the same number of units."""
+    return units_per_rank * world / max_seconds
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing
+# ---------------------------------------------------------------------------
+
+def oracle_sample(scene, cams, target_image_cpu, n_tiles_sample: int, seed: int = 0):
+    """Times the FP64 oracle (as it stands) on the workload: per-Gaussian
+    steps and the tile lists in full, the per-pixel forward and backward on
+    a uniform random sample of tiles; returns the estimated seconds of one
+    full forward + backward and a description."""
+    import oracle
+    from paper_2509_03775_gb300 import scenes  # noqa: F401
+    T = sum(-(-c.width // 16) * -(-c.height // 16) for c in cams)
+    rng = np.random.default_rng(seed)
+    sel = rng.choice(T, size=min(n_tiles_sample, T), replace=False)
+    mask = np.zeros(T, dtype=np.uint8)
+    mask[sel] = 1
+    t0 = time.perf_counter()
+    r = oracle.Render(scene, cams, tile_mask=mask)
+    d_image = np.sign(r.image - target_image_cpu) / r.image.size
+    r.backward(d_image)
+    wall = time.perf_counter() - t0
+    tm = r.timing
+    frac = len(sel) / T
+    est = (tm["shadow"] + tm["lists"] + tm["preprocess"] + (tm["blend_fwd"] + tm["blend_bwd"]) / frac +
+           tm["pair_sum"] + tm["gaussian_bwd_reduce"])
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = (f"FP64 oracle on the same workload: per-Gaussian steps, tile lists and codebook reduction in full, "
+            f"per-pixel compositing forward+backward on {len(sel)} of {T} tiles drawn uniformly "
+            f"(scaled by {T}/{len(sel)}); {wall:.1f} s of wall time")
+    return est, wall, threads, desc, tm
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def run_cg(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2509_03775_gb300 import cg
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    scene, cams, target_scene, desc = make_workload(args.workload)
+    cams = rank_camera(cams, rank)
+    r = cg.Renderer(cams, tile=args.tile, batch=args.batch, pair_capacity=1 << 26, device=dev)
+    st = cg.SceneTensors.from_scene(scene, device=dev)
+    tst = cg.SceneTensors.from_scene(target_scene, device=dev)
+    target = r.forward(tst).clone()            # resident target image
+    images = r.forward(st)                     # sizes the pair capacity
+    pairs = r.last_pairs
+    d_images = torch.empty_like(images)
+    loss = torch.empty((1,), dtype=torch.float64, device=dev)
+    d_pos = torch.empty((scene.n, 3), dtype=torch.float32, device=dev)
+    d_logit = torch.empty((scene.n,), dtype=torch.float32, device=dev)
+    nb = (scene.sh_degree + 1) ** 2
+    d_sr = torch.empty((scene.k_sr, 8), dtype=torch.float32, device=dev)
+    d_sh = torch.empty((scene.k_sh, nb, 3), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        r.forward(st, images=images, check=False)
+        r.l1_loss(images, target, d_images=d_images, loss=loss)
+        r.backward(d_images, d_pos=d_pos, d_logit=d_logit)
+        r.codebook_reduce(d_sr=d_sr, d_sh=d_sh)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    status, _ = r.status()
+    if status != cg.CG_OK:
+        raise cg.CgError("warm-up", status)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = cg.launch_count()
+    cg.timing_enable(True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ms_total = e0.elapsed_time(e1)
+    stage = cg.timing_read()
+    cg.timing_enable(False)
+    launches = cg.launch_count() - launches0
+    clk = clocks.stop()
+    seconds = max_over_ranks(ms_total / 1000.0, dev)
+    value = whole_job_value(args.steps, world, seconds)
+    ms_per_step = 1000.0 * seconds / args.steps
+
+    # stage breakdown and the dominant kernel's roofline
+    ncontrib = r.array(cg.WS_NCONTRIB, torch.int32).to(torch.int64).sum().item()
+    stages = {k: {"ms_per_launch": (v[0] / v[1] if v[1] else None), "launches": v[1]} for k, v in stage.items()}
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    hbm_src = "of measured" if hbm_peak else "of fallback"
+    hbm_peak = hbm_peak or HBM_PEAK_FALLBACK
+    n, P = scene.n, sum(c.width * c.height for c in cams)
+    cb_bytes = scene.k_sr * 32 + scene.k_sh * 4 * 3 * nb
+    step_bytes = 200 * n + 44 * pairs + 40 * P + 3 * cb_bytes
+    dominant = max((k for k in stages if stages[k]["ms_per_launch"]), key=lambda k: stages[k]["ms_per_launch"])
+    dom_ms = stages[dominant]["ms_per_launch"]
+    traffic = None
+    rec = NCU_TRAFFIC.get(dominant)
+    if rec and rec.get("src") == _src_hash(KERNEL_SOURCE[dominant]) and rec.get("workload") == args.workload:
+        traffic = rec["bytes"]
+    if dominant in FLOPS_PER_EVAL:
+        flops = FLOPS_PER_EVAL[dominant] * ncontrib
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+        achieved = flops / (dom_ms / 1000.0) / 1e12
+        roofline = {"bound": "alu", "kernel": dominant, "achieved": round(achieved, 3), "peak": round(peak, 2),
+                    "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                    "peak_source": "FP32 lanes 152 x 128 x 2 x 2070 MHz (nominal max clock)",
+                    "work": f"{FLOPS_PER_EVAL[dominant]} FP32 ops x {ncontrib} (pixel, Gaussian) evaluations"}
+    else:
+        algo = {"sort": 48 * pairs + 64 * n, "preprocess": 84 * n + cb_bytes,
+                "reduce": 68 * n + 2 * cb_bytes, "gauss_bwd": 36 * pairs + 60 * n}[dominant]
+        achieved = algo / (dom_ms / 1000.0) / 1e9
+        roofline = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1), "peak": hbm_peak,
+                    "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
+                    "peak_source": hbm_src}
+    step_gbs = step_bytes / (ms_per_step / 1000.0) / 1e9
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, r, scene, target, dev)
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "renders/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "gaussians": n, "pixels": P,
+                   "pairs": pairs, "tile": args.tile, "sh_degree": scene.sh_degree,
+                   "codebook_rows": [scene.k_sr, scene.k_sh],
+                   "l2": "working set per step > 129 MB L2 (pair buffers alone 0.9 GB); no flush",
+                   "parallelism": f"{world} independent view(s), one per GPU"},
+        "hbm_roofline_step": {"algorithmic_bytes": step_bytes, "achieved_gbs": round(step_gbs, 1),
+                              "peak_gbs": hbm_peak, "frac": round(step_gbs / hbm_peak, 4),
+                              "model": "200 N + 44 K + 40 P + codebooks (read twice, gradients once)",
+                              "note": hbm_src},
+        "roofline": roofline,
+        "stages_ms": {k: (round(v["ms_per_launch"], 4) if v["ms_per_launch"] else None) for k, v in stages.items()},
+        "evaluations": int(ncontrib),
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est, wall, threads, sdesc, _ = oracle_sample(scene, cams, target.cpu().numpy().astype(np.float64),
+                                                     args.cpu_tiles)
+        out["cpu_baseline"] = {"value": round(1.0 / est, 5), "unit": "renders/s", "cores": threads,
+                               "kind": "oracle", "sample": sdesc}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, r, scene, target, dev):
+    """Same step through the public API with the inputs in pinned host
+    memory and the results read back every step."""
+    import torch
+    from paper_2509_03775_gb300 import cg
+    host = {
+        "pos": torch.from_numpy(scene.pos).pin_memory(),
+        "logit": torch.from_numpy(scene.opacity_logit).pin_memory(),
+        "g2sr": torch.from_numpy(scene.g2sr.view(np.int16)).pin_memory(),
+        "g2sh": torch.from_numpy(scene.g2sh.view(np.int16)).pin_memory(),
+        "sr": torch.from_numpy(scene.sr_rows).pin_memory(),
+        "sh": torch.from_numpy(scene.sh_rows).pin_memory(),
+        "target": target.cpu().pin_memory(),
+    }
+    dvc = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    st = cg.SceneTensors(dvc["pos"], dvc["logit"], dvc["g2sr"], dvc["g2sh"], dvc["sr"], dvc["sh"], scene.sh_degree)
+    nb = (scene.sh_degree + 1) ** 2
+    outs_dev = {"loss": torch.empty((1,), dtype=torch.float64, device=dev),
+                "d_pos": torch.empty((scene.n, 3), device=dev), "d_logit": torch.empty((scene.n,), device=dev),
+                "d_sr": torch.empty((scene.k_sr, 8), device=dev), "d_sh": torch.empty((scene.k_sh, nb, 3), device=dev)}
+    outs_host = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in outs_dev.items()}
+    images = torch.empty((3 * r.pixels,), device=dev)
+    d_images = torch.empty_like(images)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for k in host:
+            dvc[k].copy_(host[k], non_blocking=True)
+        r.forward(st, images=images, check=False)
+        r.l1_loss(images, dvc["target"], d_images=d_images, loss=outs_dev["loss"])
+        r.backward(d_images, d_pos=outs_dev["d_pos"], d_logit=outs_dev["d_logit"])
+        r.codebook_reduce(d_sr=outs_dev["d_sr"], d_sh=outs_dev["d_sh"])
+        for k in outs_dev:
+            outs_host[k].copy_(outs_dev[k], non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    sec = e0.elapsed_time(e1) / 1000.0
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = sum(v.numel() * v.element_size() for v in outs_host.values())
+    return {"value": round(args.steps / sec, 3), "unit": "renders/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h)}
+
+
+# ---------------------------------------------------------------------------
+# the reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def crop_camera(cam, frac: int, rng):
+    """A tile-aligned window of 1/frac^2 of the image, same pose and focal
+    length (the principal point moves with the window)."""
+    from paper_2509_03775_gb300 import scenes
+    tx, ty = -(-cam.width // 16), -(-cam.height // 16)
+    wt, ht = max(1, tx // frac), max(1, ty // frac)
+    ox, oy = 16 * int(rng.integers(0, tx - wt + 1)), 16 * int(rng.integers(0, ty - ht + 1))
+    w, h = min(16 * wt, cam.width - ox), min(16 * ht, cam.height - oy)
+    c = scenes.Camera(w, h, cam.fx, cam.fy, float(np.float32(cam.cx - ox)), float(np.float32(cam.cy - oy)),
+                      cam.world_to_cam, cam.campos, cam.near)
+    return c
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, on the host cores.
+    Each step renders (forward + backward) a random tile-aligned window of
+    1/16 of the image; the per-Gaussian steps run in full, and the per-pixel
+    and per-pair steps are scaled by the image / window area."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    scene, cams, _, desc = make_workload(args.workload)
+    cam = cams[0]
+    rng = np.random.default_rng(7)
+    ests, walls = [], []
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    for i in range(args.warmup + args.steps):
+        crop = crop_camera(cam, 4, rng)
+        t0 = time.perf_counter()
+        r = oracle.Render(scene, [crop])
+        r.backward(np.full(r.image.shape, 1.0 / r.image.size))
+        wall = time.perf_counter() - t0
+        tm = r.timing
+        scale = (cam.width * cam.height) / (crop.width * crop.height)
+        est = (tm["shadow"] + tm["preprocess"] + tm["gaussian_bwd_reduce"] +
+               scale * (tm["lists"] + tm["blend_fwd"] + tm["blend_bwd"] + tm["pair_sum"]))
+        if i >= args.warmup:
+            ests.append(est)
+            walls.append(wall)
+    est = statistics.mean(ests)
+    value = 1.0 / est
+    sample = (f"FP64 oracle, one random tile-aligned window of 1/16 of the {cam.width}x{cam.height} image per step "
+              f"(forward + backward), per-Gaussian steps in full, per-pixel and per-pair steps scaled by the area "
+              f"ratio; mean over {args.steps} steps, {statistics.mean(walls):.1f} s of wall time per step")
+    out = {"metric": METRIC, "value": round(value, 5), "unit": "renders/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000.0 * est, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": args.workload, "description": desc},
+           "cpu_baseline": {"value": round(value, 5), "unit": "renders/s", "cores": threads, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(value, 5), "unit": "renders/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["cg", "reference"], default="cg")
+    ap.add_argument("--workload", choices=["truck", "single", "tiny"], default="truck")
+    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--cpu-tiles", type=int, default=96, help="tiles in the CPU-baseline sample")
+    ap.add_argument("--ref-tiles", type=int, default=24, help="tiles per step of the reference arm")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cg(args)
+
+
+if __name__ == "__main__":
+    main()

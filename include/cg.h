@@ -182,6 +182,27 @@ float cg_host_exp32(float x);
 void cg_host_sh_consts(float out[16]);
 void cg_host_sigma3(const float row[8], float out[6]);
 
+/* Stage timing for benchmarks.  While enabled, the library records a pair
+ * of CUDA events on the caller's stream around every launch of each stage
+ * below (up to 4096 launches per stage between reads).  cg_timing_read
+ * waits for those events, writes the summed milliseconds and launch counts
+ * per stage (host arrays of CG_STAGE_COUNT entries) and clears them.  Do not
+ * enable it while capturing a CUDA graph. */
+typedef enum {
+  CG_STAGE_PREPROCESS = 0, /* Eq. 2 rows + projection records */
+  CG_STAGE_SORT,           /* compaction, depth sort, pair emission, tile sort, ranges */
+  CG_STAGE_BLEND_FWD,      /* per-tile forward compositing */
+  CG_STAGE_BLEND_BWD,      /* per-tile backward compositing */
+  CG_STAGE_GAUSS_BWD,      /* per-Gaussian backward */
+  CG_STAGE_REDUCE,         /* codebook membership and row sums */
+  CG_STAGE_COUNT
+} cg_stage;
+cg_status cg_timing_enable(int on);
+cg_status cg_timing_read(double *ms_out, uint64_t *launches_out);
+
+/* Number of kernels the library has launched since it was loaded. */
+uint64_t cg_launch_count(void);
+
 /* Library version string. */
 const char *cg_version(void);
 

@@ -26,6 +26,7 @@ import ctypes
 import os
 import subprocess
 import threading
+import time
 
 import numpy as np
 
@@ -94,7 +95,8 @@ def lib():
             L.or_blend_forward.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P,
                                            _P, _P, _P, _P, _P]
             L.or_blend_backward.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P,
-                                            _P, _P, _P, _P, ctypes.c_int64, _P]
+                                            _P, _P, _P, _P, _P]
+            L.or_pair_sum.argtypes = [_P, ctypes.c_int64, _P, ctypes.c_int64, _P]
             L.or_preprocess_backward.argtypes = [_P, _P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]
             L.or_codebook_reduce.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P]
             _lib = L
@@ -235,9 +237,14 @@ class Render:
         self.pix_base = np.concatenate([[0], np.cumsum(self.pix_counts)[:-1]]).astype(np.int64)
         self.P = int(self.pix_counts.sum())
         self.tile_mask = None if tile_mask is None else np.ascontiguousarray(tile_mask, dtype=np.uint8)
+        # wall time of each step (seconds), for the CPU baseline
+        self.timing = {}
+        t0 = time.perf_counter()
         # decisions (FP32) and tile lists
         self.rec32 = np.zeros(self.V * n, dtype=REC32)
         L.or_shadow32(ctypes.byref(self.sb.s), self._c, self.V, self.tile, _ptr(self.rec32))
+        t1 = time.perf_counter()
+        self.timing["shadow"] = t1 - t0
         self.k_pairs = int(L.or_count_pairs(_ptr(self.rec32), self.V * n))
         if self.k_pairs >= 2 ** 32:
             raise ValueError("pair count exceeds 32-bit indexing")
@@ -248,8 +255,13 @@ class Render:
                          self.n_tiles, self.k_pairs, _ptr(self.list), _ptr(self.keys), _ptr(self.ranges))
         self.list = self.list[:self.k_pairs]
         self.keys = self.keys[:self.k_pairs]
+        t2 = time.perf_counter()
+        self.timing["lists"] = t2 - t1
         self.rec64 = self._preprocess(self.sb)
+        t3 = time.perf_counter()
+        self.timing["preprocess"] = t3 - t2
         self.image, self.t_final, self.n_contrib = self._forward(self.rec64)
+        self.timing["blend_fwd"] = time.perf_counter() - t3
 
     # -- steps ---------------------------------------------------------------
     def _preprocess(self, sb: _SceneBuf) -> np.ndarray:
@@ -282,9 +294,18 @@ class Render:
         n_rec = self.V * self.n
         grad9 = np.zeros((n_rec, 9))
         mask = _ptr(self.tile_mask) if self.tile_mask is not None else None
+        pair = np.zeros((max(self.k_pairs, 1), 9))
+        t0 = time.perf_counter()
         L.or_blend_backward(self._c, self.V, self.tile, _ptr(self.bg), self.mode, _ptr(self.rec32),
                             _ptr(self.rec64), _ptr(self.list), _ptr(self.ranges), mask, _ptr(d_image),
-                            n_rec, _ptr(grad9))
+                            _ptr(pair))
+        t1 = time.perf_counter()
+        L.or_pair_sum(_ptr(self.list), self.k_pairs, _ptr(pair), n_rec, _ptr(grad9))
+        t2 = time.perf_counter()
+        del pair
+        self.timing["blend_bwd"] = t1 - t0
+        self.timing["pair_sum"] = t2 - t1
+        t1 = t2
         dpos = np.zeros((self.n, 3))
         dlogit = np.zeros(self.n)
         dsigma = np.zeros((self.n, 6))
@@ -297,6 +318,7 @@ class Render:
         d_sh = np.zeros((self.sb.sh.shape[0], nb, 3))
         L.or_codebook_reduce(ctypes.byref(self.sb.s), self.V, _ptr(self.rec64), _ptr(dsigma), _ptr(drgb),
                              _ptr(d_sr), _ptr(d_sh))
+        self.timing["gaussian_bwd_reduce"] = time.perf_counter() - t1
         return {"grad9": grad9, "dpos": dpos, "dlogit": dlogit, "dsigma": dsigma, "drgb": drgb,
                 "d_sr": d_sr, "d_sh": d_sh}
 

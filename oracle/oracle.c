@@ -648,19 +648,15 @@ void or_blend_forward(const or_camera *cams, int n_views, int tile, const double
  * grad9[rec][9] = dL/d(mean_x, mean_y, conic0, conic1, conic2, opacity, r, g, b).
  * The pixel's contributions are gathered front to back under the same
  * decisions as the forward, then differentiated exactly. */
+/* pair[k_pairs][9] (zero on entry) receives one accumulator row per (tile,
+ * list position); or_pair_sum then adds the rows into their records. */
 void or_blend_backward(const or_camera *cams, int n_views, int tile, const double bg[3], int mode,
                        const or_rec32 *rec32, const or_rec64 *rec64, const uint32_t *list,
                        const uint32_t *ranges, const uint8_t *tile_mask, const double *d_image,
-                       int64_t n_rec, double *grad9) {
+                       double *pair) {
   view_geom vg[64];
   make_geoms(cams, n_views, tile, vg);
   const int64_t n_tiles = vg[n_views - 1].tile_base + (int64_t)vg[n_views - 1].tiles_x * vg[n_views - 1].tiles_y;
-  memset(grad9, 0, sizeof(double) * 9 * (size_t)n_rec);
-  /* one accumulator row per (tile, list position), summed per record after */
-  int64_t total = 0;
-  for (int64_t gt = 0; gt < n_tiles; ++gt)
-    if (ranges[2 * gt + 1] > (uint32_t)total) total = ranges[2 * gt + 1];
-  double *pair = (double *)calloc((size_t)(total > 0 ? total : 1) * 9, sizeof(double));
 #pragma omp parallel
   {
     int cap = 0;
@@ -743,11 +739,15 @@ void or_blend_backward(const or_camera *cams, int n_views, int tile, const doubl
     }
     free(idx); free(alph); free(Gs); free(Ts); free(clampf);
   }
-  for (int64_t i = 0; i < total; ++i) {
+}
+
+/* grad9[rec][9] = sum of the pair rows listing that record. */
+void or_pair_sum(const uint32_t *list, int64_t k_pairs, const double *pair, int64_t n_rec, double *grad9) {
+  memset(grad9, 0, sizeof(double) * 9 * (size_t)n_rec);
+  for (int64_t i = 0; i < k_pairs; ++i) {
     const uint32_t rid = list[i];
     for (int e = 0; e < 9; ++e) grad9[9 * (size_t)rid + e] += pair[9 * (size_t)i + e];
   }
-  free(pair);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -29,7 +29,9 @@ WS_RECT, WS_DEPTH, WS_PAIRS, WS_RANGES, WS_NCONTRIB, WS_TFINAL, WS_DSIGMA, WS_DR
 
 # every symbol include/cg.h declares
 EXPORTS = ["cg_workspace_bytes", "cg_render_fwd", "cg_render_bwd", "cg_codebook_reduce", "cg_last_device_status",
-           "cg_l1_loss", "cg_workspace_array", "cg_host_exp32", "cg_host_sh_consts", "cg_host_sigma3", "cg_version"]
+           "cg_l1_loss", "cg_workspace_array", "cg_host_exp32", "cg_host_sh_consts", "cg_host_sigma3",
+           "cg_timing_enable", "cg_timing_read", "cg_launch_count", "cg_version"]
+STAGES = ["preprocess", "sort", "blend_fwd", "blend_bwd", "gauss_bwd", "reduce"]
 
 
 class CgError(RuntimeError):
@@ -85,12 +87,34 @@ def load(path: str | None = None) -> ctypes.CDLL:
         L.cg_host_sh_consts.argtypes = [P]
         L.cg_host_sigma3.argtypes = [P, P]
         L.cg_version.restype = ctypes.c_char_p
+        L.cg_timing_enable.argtypes = [ctypes.c_int]
+        L.cg_timing_enable.restype = ctypes.c_int
+        L.cg_timing_read.argtypes = [P, P]
+        L.cg_timing_read.restype = ctypes.c_int
+        L.cg_launch_count.restype = ctypes.c_uint64
         for name in ("cg_render_fwd", "cg_render_bwd", "cg_codebook_reduce", "cg_last_device_status", "cg_l1_loss",
                      "cg_workspace_array"):
             getattr(L, name).restype = ctypes.c_int
         if path is None:
             _lib = L
         return L
+
+
+def timing_enable(on: bool = True):
+    load().cg_timing_enable(1 if on else 0)
+
+
+def timing_read() -> dict:
+    """{stage: (milliseconds, launches)} since the last read (waits for the events)."""
+    ms = np.zeros(len(STAGES), dtype=np.float64)
+    n = np.zeros(len(STAGES), dtype=np.uint64)
+    _check("cg_timing_read", load().cg_timing_read(ms.ctypes.data_as(ctypes.c_void_p),
+                                                    n.ctypes.data_as(ctypes.c_void_p)))
+    return {s: (float(ms[i]), int(n[i])) for i, s in enumerate(STAGES)}
+
+
+def launch_count() -> int:
+    return int(load().cg_launch_count())
 
 
 def _check(call: str, status: int):

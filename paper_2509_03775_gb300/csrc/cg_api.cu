@@ -1,14 +1,58 @@
 // cg_api.cu -- the C ABI of include/cg.h: argument checks, workspace layout
 // and the launch sequence of each call.
 #include <algorithm>
+#include <atomic>
 #include <cstddef>
 #include <cstdio>
+#include <mutex>
+#include <vector>
 
 #include "cg_common.cuh"
+
+namespace cg {
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace cg
 
 using namespace cg;
 
 namespace {
+
+// Stage timing (cg_timing_enable / cg_timing_read): event pairs recorded on
+// the caller's stream around each stage.
+constexpr int kMaxTimed = 4096;
+struct Timing {
+  std::mutex m;
+  bool on = false;
+  std::vector<cudaEvent_t> ev[CG_STAGE_COUNT];  // start, stop, start, stop, ...
+  int used[CG_STAGE_COUNT] = {};
+};
+Timing g_timing;
+
+struct StageTimer {
+  int stage = -1;
+  cudaStream_t s = nullptr;
+  StageTimer(int st, cudaStream_t stream) {
+    std::lock_guard<std::mutex> lk(g_timing.m);
+    if (!g_timing.on || g_timing.used[st] >= kMaxTimed) return;
+    auto& v = g_timing.ev[st];
+    const int i = g_timing.used[st];
+    while ((int)v.size() < 2 * (i + 1)) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      v.push_back(e);
+    }
+    if (cudaEventRecord(v[2 * i], stream) != cudaSuccess) return;
+    stage = st;
+    s = stream;
+  }
+  ~StageTimer() {
+    if (stage < 0) return;
+    std::lock_guard<std::mutex> lk(g_timing.m);
+    const int i = g_timing.used[stage];
+    if (cudaEventRecord(g_timing.ev[stage][2 * i + 1], s) == cudaSuccess) g_timing.used[stage] = i + 1;
+  }
+};
 
 constexpr uint64_t kAlign = 256;
 
@@ -161,11 +205,21 @@ cg_status cg_render_fwd(const cg_scene* scene, const cg_camera* cams, int n_view
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const SceneArgs sc = scene_args(scene);
   const int batch = opts->batch ? opts->batch : 256;
-  cudaError_t e = launch_setup(tl_table, L, workspace, s);
-  if (e == cudaSuccess) e = launch_sigma3(sc, L, workspace, s);
-  if (e == cudaSuccess) e = launch_preprocess(sc, L, workspace, s);
-  if (e == cudaSuccess) e = launch_build_pairs(L, workspace, L.tile_bits, s);
-  if (e == cudaSuccess) e = launch_blend_fwd(L, workspace, opts->tile, batch, opts->bg, images, s);
+  cudaError_t e;
+  {
+    StageTimer t(CG_STAGE_PREPROCESS, s);
+    e = launch_setup(tl_table, L, workspace, s);
+    if (e == cudaSuccess) e = launch_sigma3(sc, L, workspace, s);
+    if (e == cudaSuccess) e = launch_preprocess(sc, L, workspace, s);
+  }
+  if (e == cudaSuccess) {
+    StageTimer t(CG_STAGE_SORT, s);
+    e = launch_build_pairs(L, workspace, L.tile_bits, s);
+  }
+  if (e == cudaSuccess) {
+    StageTimer t(CG_STAGE_BLEND_FWD, s);
+    e = launch_blend_fwd(L, workspace, opts->tile, batch, opts->bg, images, s);
+  }
   return cuda_status(e);
 }
 
@@ -181,8 +235,15 @@ cg_status cg_render_bwd(const cg_scene* scene, const cg_camera* cams, int n_view
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const SceneArgs sc = scene_args(scene);
   const int batch = opts->batch ? std::min(opts->batch, 128) : 64;
-  cudaError_t e = launch_blend_bwd(L, workspace, opts->tile, batch, opts->bg, d_images, s);
-  if (e == cudaSuccess) e = launch_gaussian_bwd(sc, L, workspace, d_pos, d_opacity_logit, s);
+  cudaError_t e;
+  {
+    StageTimer t(CG_STAGE_BLEND_BWD, s);
+    e = launch_blend_bwd(L, workspace, opts->tile, batch, opts->bg, d_images, s);
+  }
+  if (e == cudaSuccess) {
+    StageTimer t(CG_STAGE_GAUSS_BWD, s);
+    e = launch_gaussian_bwd(sc, L, workspace, d_pos, d_opacity_logit, s);
+  }
   return cuda_status(e);
 }
 
@@ -194,6 +255,7 @@ cg_status cg_codebook_reduce(const cg_scene* scene, const cg_camera* cams, int n
   if (st == CG_OK && (!d_sr_rows || !d_sh_rows || !aligned(d_sr_rows, 4) || !aligned(d_sh_rows, 4))) st = CG_ERR_ARG;
   if (st != CG_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  StageTimer t(CG_STAGE_REDUCE, s);
   return cuda_status(launch_codebook_reduce(scene_args(scene), L, workspace, d_sr_rows, d_sh_rows, s));
 }
 
@@ -259,6 +321,34 @@ void cg_host_sh_consts(float out[16]) {
 }
 
 void cg_host_sigma3(const float row[8], float out[6]) { sigma3_from_row(row, out); }
+
+cg_status cg_timing_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_timing.m);
+  g_timing.on = on != 0;
+  for (int i = 0; i < CG_STAGE_COUNT; ++i) g_timing.used[i] = 0;
+  return CG_OK;
+}
+
+cg_status cg_timing_read(double* ms_out, uint64_t* launches_out) {
+  if (!ms_out || !launches_out) return CG_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_timing.m);
+  for (int st = 0; st < CG_STAGE_COUNT; ++st) {
+    double acc = 0.0;
+    for (int i = 0; i < g_timing.used[st]; ++i) {
+      float ms = 0.0f;
+      if (cudaEventSynchronize(g_timing.ev[st][2 * i + 1]) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, g_timing.ev[st][2 * i], g_timing.ev[st][2 * i + 1]) != cudaSuccess)
+        return CG_ERR_CUDA;
+      acc += ms;
+    }
+    ms_out[st] = acc;
+    launches_out[st] = (uint64_t)g_timing.used[st];
+    g_timing.used[st] = 0;
+  }
+  return CG_OK;
+}
+
+uint64_t cg_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 const char* cg_version(void) { return "cg 0.1 (sm_103a)"; }
 

@@ -258,6 +258,9 @@ __device__ __forceinline__ int find_view(const ViewInfo* views, int n_views, int
   return v;
 }
 
+// Counts one kernel launch (cg_launch_count).
+void count_launch();
+
 // ----------------------------------------------------------------------------
 // kernel launchers (one translation unit each)
 // ----------------------------------------------------------------------------

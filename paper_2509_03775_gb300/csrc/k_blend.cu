@@ -268,10 +268,10 @@ static cudaError_t fwd_tile(int batch, dim3 grid, cudaStream_t s, const ViewInfo
                             float* images, float* tfinal, uint32_t* ncontrib) {
   constexpr int NT = TILE * TILE < 256 ? TILE * TILE : 256;
   switch (batch) {
-    case 32: k_blend_fwd<TILE, 32><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, bg[0], bg[1], bg[2], images, tfinal, ncontrib); break;
-    case 64: k_blend_fwd<TILE, 64><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, bg[0], bg[1], bg[2], images, tfinal, ncontrib); break;
-    case 128: k_blend_fwd<TILE, 128><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, bg[0], bg[1], bg[2], images, tfinal, ncontrib); break;
-    case 256: k_blend_fwd<TILE, 256><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, bg[0], bg[1], bg[2], images, tfinal, ncontrib); break;
+    case 32: count_launch(), k_blend_fwd<TILE, 32><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, bg[0], bg[1], bg[2], images, tfinal, ncontrib); break;
+    case 64: count_launch(), k_blend_fwd<TILE, 64><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, bg[0], bg[1], bg[2], images, tfinal, ncontrib); break;
+    case 128: count_launch(), k_blend_fwd<TILE, 128><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, bg[0], bg[1], bg[2], images, tfinal, ncontrib); break;
+    case 256: count_launch(), k_blend_fwd<TILE, 256><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, bg[0], bg[1], bg[2], images, tfinal, ncontrib); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -284,9 +284,9 @@ static cudaError_t bwd_tile(int batch, dim3 grid, cudaStream_t s, const ViewInfo
                             const uint32_t* ncontrib, float* pairgrad) {
   constexpr int NT = TILE * TILE < 256 ? TILE * TILE : 256;
   switch (batch) {
-    case 32: k_blend_bwd<TILE, 32><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, rect, offrec, bg[0], bg[1], bg[2], d_images, tfinal, ncontrib, pairgrad); break;
-    case 64: k_blend_bwd<TILE, 64><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, rect, offrec, bg[0], bg[1], bg[2], d_images, tfinal, ncontrib, pairgrad); break;
-    case 128: k_blend_bwd<TILE, 128><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, rect, offrec, bg[0], bg[1], bg[2], d_images, tfinal, ncontrib, pairgrad); break;
+    case 32: count_launch(), k_blend_bwd<TILE, 32><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, rect, offrec, bg[0], bg[1], bg[2], d_images, tfinal, ncontrib, pairgrad); break;
+    case 64: count_launch(), k_blend_bwd<TILE, 64><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, rect, offrec, bg[0], bg[1], bg[2], d_images, tfinal, ncontrib, pairgrad); break;
+    case 128: count_launch(), k_blend_bwd<TILE, 128><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, rect, offrec, bg[0], bg[1], bg[2], d_images, tfinal, ncontrib, pairgrad); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -200,7 +200,7 @@ cudaError_t launch_gaussian_bwd(const SceneArgs& sc, const Layout& L, void* ws, 
   const float* pg = ws_ptr<float>(ws, L.pairgrad);
   float* dsig = ws_ptr<float>(ws, L.dsigma);
   float* drgb = ws_ptr<float>(ws, L.drgb);
-#define CG_GB(NBV) k_gaussian_bwd<NBV><<<grid, 256, 0, s>>>(sc, views, L.n_views, sig, geo, rgbm, nt, off, pg, &hdr->st, d_pos, d_logit, dsig, drgb)
+#define CG_GB(NBV) count_launch(), k_gaussian_bwd<NBV><<<grid, 256, 0, s>>>(sc, views, L.n_views, sig, geo, rgbm, nt, off, pg, &hdr->st, d_pos, d_logit, dsig, drgb)
   switch (sc.nb) {
     case 1: CG_GB(1); break;
     case 4: CG_GB(4); break;
@@ -430,18 +430,18 @@ static cudaError_t build_csr(void* ws, const Layout& L, const uint16_t* idx, int
   uint64_t* k1 = ws_ptr<uint64_t>(ws, L.dkeys1);
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
   const int gk = std::max(1, std::min((k + 255) / 256, 152 * 8));
-  k_zero_counts<<<gk, 256, 0, s>>>(counts, k);
-  k_row_keys<<<g, 256, 0, s>>>(idx, n, k, k0, counts, slot_a);
+  count_launch(), k_zero_counts<<<gk, 256, 0, s>>>(counts, k);
+  count_launch(), k_row_keys<<<g, 256, 0, s>>>(idx, n, k, k0, counts, slot_a);
   bool in_b = false;
   cudaError_t e = sort_u64(ws, L, k0, k1, slot_a, n, 32, k >= 65536 ? 3 : 2, &in_b, s);
   if (e != cudaSuccess) return e;
-  k_ids_from_keys<<<g, 256, 0, s>>>(in_b ? k1 : k0, n, ids);
-  k_chunk_counts<<<gk, 256, 0, s>>>(counts, k, chunk_base, slot_b);
+  count_launch(), k_ids_from_keys<<<g, 256, 0, s>>>(in_b ? k1 : k0, n, ids);
+  count_launch(), k_chunk_counts<<<gk, 256, 0, s>>>(counts, k, chunk_base, slot_b);
   e = scan_u32(ws, L, counts, row_off, slot_b, k, slot_a, s);  // slot_a <- n (total)
   if (e != cudaSuccess) return e;
   e = scan_u32(ws, L, chunk_base, chunk_base, slot_b, k, slot_a, s);  // slot_a <- chunk count
   if (e != cudaSuccess) return e;
-  k_fill_chunks<<<gk, 256, 0, s>>>(row_off, counts, chunk_base, k, chunks);
+  count_launch(), k_fill_chunks<<<gk, 256, 0, s>>>(row_off, counts, chunk_base, k, chunks);
   return cudaGetLastError();
 }
 
@@ -459,9 +459,9 @@ cudaError_t launch_codebook_reduce(const SceneArgs& sc, const Layout& L, void* w
                             ws_ptr<uint32_t>(ws, L.csr_ids_sr), cnt, cbase, chunks, slot_a, slot_b, s);
   if (e != cudaSuccess) return e;
   const int gw = 152 * 8;
-  k_sr_partials<<<gw, 256, 0, s>>>(chunks, slot_a, ws_ptr<uint32_t>(ws, L.csr_ids_sr), ws_ptr<float>(ws, L.dsigma),
+  count_launch(), k_sr_partials<<<gw, 256, 0, s>>>(chunks, slot_a, ws_ptr<uint32_t>(ws, L.csr_ids_sr), ws_ptr<float>(ws, L.dsigma),
                                   part);
-  k_sr_rows<<<(sc.k_sr + 127) / 128, 128, 0, s>>>(cnt, cbase, sc.k_sr, part, sc.sr_rows, sc.dtype, d_sr);
+  count_launch(), k_sr_rows<<<(sc.k_sr + 127) / 128, 128, 0, s>>>(cnt, cbase, sc.k_sr, part, sc.sr_rows, sc.dtype, d_sr);
   // SH rows
   uint32_t* cnt2 = ws_ptr<uint32_t>(ws, L.csr_off_sh) + (L.k_sh + 1);
   uint32_t* cbase2 = cnt2 + L.k_sh;
@@ -471,7 +471,7 @@ cudaError_t launch_codebook_reduce(const SceneArgs& sc, const Layout& L, void* w
   const ViewInfo* views = ws_ptr<ViewInfo>(ws, L.views);
   const uint32_t* ids = ws_ptr<uint32_t>(ws, L.csr_ids_sh);
   const float* drgb = ws_ptr<float>(ws, L.drgb);
-#define CG_SHP(NBV) k_sh_partials<NBV><<<gw, 256, 0, s>>>(chunks, slot_a, ids, sc.pos, views, L.n_views, L.n, drgb, part)
+#define CG_SHP(NBV) count_launch(), k_sh_partials<NBV><<<gw, 256, 0, s>>>(chunks, slot_a, ids, sc.pos, views, L.n_views, L.n, drgb, part)
   switch (sc.nb) {
     case 1: CG_SHP(1); break;
     case 4: CG_SHP(4); break;
@@ -482,7 +482,7 @@ cudaError_t launch_codebook_reduce(const SceneArgs& sc, const Layout& L, void* w
 #undef CG_SHP
   const int width = sc.nb * 3;
   const int64_t tot = (int64_t)sc.k_sh * width;
-  k_sh_rows<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(cnt2, cbase2, sc.k_sh, width, part, d_sh);
+  count_launch(), k_sh_rows<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(cnt2, cbase2, sc.k_sh, width, part, d_sh);
   return cudaGetLastError();
 }
 
@@ -532,8 +532,8 @@ __global__ void k_l1_final(const double* __restrict__ part, int64_t count, doubl
 cudaError_t launch_l1(const float* img, const float* tgt, int64_t count, float* d_img, double* loss,
                       const Layout& L, void* ws, cudaStream_t s) {
   double* part = ws_ptr<double>(ws, L.l1);
-  k_l1<<<kL1Blocks, 256, 0, s>>>(img, tgt, count, d_img, part);
-  k_l1_final<<<1, 256, 0, s>>>(part, count, loss);
+  count_launch(), k_l1<<<kL1Blocks, 256, 0, s>>>(img, tgt, count, d_img, part);
+  count_launch(), k_l1_final<<<1, 256, 0, s>>>(part, count, loss);
   return cudaGetLastError();
 }
 

@@ -21,7 +21,7 @@ __global__ void k_setup(const __grid_constant__ ViewTable table, const __grid_co
 }
 
 cudaError_t launch_setup(const ViewTable& table, const Layout& L, void* ws, cudaStream_t s) {
-  k_setup<<<1, 64, 0, s>>>(table, L, ws);
+  count_launch(), k_setup<<<1, 64, 0, s>>>(table, L, ws);
   return cudaGetLastError();
 }
 
@@ -40,7 +40,7 @@ __global__ void k_sigma3(const void* __restrict__ rows, int dtype, int k_sr, flo
 }
 
 cudaError_t launch_sigma3(const SceneArgs& sc, const Layout& L, void* ws, cudaStream_t s) {
-  k_sigma3<<<(sc.k_sr + 127) / 128, 128, 0, s>>>(sc.sr_rows, sc.dtype, sc.k_sr, ws_ptr<float>(ws, L.sigma3));
+  count_launch(), k_sigma3<<<(sc.k_sr + 127) / 128, 128, 0, s>>>(sc.sr_rows, sc.dtype, sc.k_sr, ws_ptr<float>(ws, L.sigma3));
   return cudaGetLastError();
 }
 
@@ -152,10 +152,10 @@ cudaError_t launch_preprocess(const SceneArgs& sc, const Layout& L, void* ws, cu
   uint32_t* dp = ws_ptr<uint32_t>(ws, L.depth);
   DeviceState* st = &hdr->st;
   switch (sc.nb) {
-    case 1: k_preprocess<1><<<grid, 256, 0, s>>>(sc, views, L.n_views, L.tile, sig, geo, rgbm, rect, nt, dp, st); break;
-    case 4: k_preprocess<4><<<grid, 256, 0, s>>>(sc, views, L.n_views, L.tile, sig, geo, rgbm, rect, nt, dp, st); break;
-    case 9: k_preprocess<9><<<grid, 256, 0, s>>>(sc, views, L.n_views, L.tile, sig, geo, rgbm, rect, nt, dp, st); break;
-    case 16: k_preprocess<16><<<grid, 256, 0, s>>>(sc, views, L.n_views, L.tile, sig, geo, rgbm, rect, nt, dp, st); break;
+    case 1: count_launch(), k_preprocess<1><<<grid, 256, 0, s>>>(sc, views, L.n_views, L.tile, sig, geo, rgbm, rect, nt, dp, st); break;
+    case 4: count_launch(), k_preprocess<4><<<grid, 256, 0, s>>>(sc, views, L.n_views, L.tile, sig, geo, rgbm, rect, nt, dp, st); break;
+    case 9: count_launch(), k_preprocess<9><<<grid, 256, 0, s>>>(sc, views, L.n_views, L.tile, sig, geo, rgbm, rect, nt, dp, st); break;
+    case 16: count_launch(), k_preprocess<16><<<grid, 256, 0, s>>>(sc, views, L.n_views, L.tile, sig, geo, rgbm, rect, nt, dp, st); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -186,9 +186,9 @@ cudaError_t sort_u64(void* ws, const Layout& L, uint64_t* a, uint64_t* b, const 
   uint64_t* dst = b;
   for (int p = 0; p < passes; ++p) {
     const int shift = lo_bit + 8 * p;
-    k_sort_upsweep<<<grid, kSortThreads, 0, s>>>(src, count_dev, count_cap, shift, hist, L.sort_blocks_cap);
-    k_sort_scan_rows<<<256, 1024, 0, s>>>(hist, count_dev, count_cap, L.sort_blocks_cap, digit_tot);
-    k_sort_downsweep<<<grid, kSortThreads, 0, s>>>(src, dst, count_dev, count_cap, shift, hist, digit_tot,
+    count_launch(), k_sort_upsweep<<<grid, kSortThreads, 0, s>>>(src, count_dev, count_cap, shift, hist, L.sort_blocks_cap);
+    count_launch(), k_sort_scan_rows<<<256, 1024, 0, s>>>(hist, count_dev, count_cap, L.sort_blocks_cap, digit_tot);
+    count_launch(), k_sort_downsweep<<<grid, kSortThreads, 0, s>>>(src, dst, count_dev, count_cap, shift, hist, digit_tot,
                                                    L.sort_blocks_cap);
     uint64_t* t = src;
     src = dst;
@@ -297,9 +297,9 @@ cudaError_t scan_u32(void* ws, const Layout& L, const uint32_t* in, uint32_t* ou
   const int64_t nb_cap = (count_cap + kScanTile - 1) / kScanTile;
   if (nb_cap > L.scan_blocks_cap) return cudaErrorInvalidValue;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nb_cap, kGrid));
-  k_scan_reduce<<<grid, kScanThreads, 0, s>>>(in, count_dev, count_cap, bsum);
-  k_scan_blocks<<<1, 1024, 0, s>>>(bsum, count_dev, count_cap, total_dev);
-  k_scan_down<<<grid, kScanThreads, 0, s>>>(in, out, count_dev, count_cap, bsum);
+  count_launch(), k_scan_reduce<<<grid, kScanThreads, 0, s>>>(in, count_dev, count_cap, bsum);
+  count_launch(), k_scan_blocks<<<1, 1024, 0, s>>>(bsum, count_dev, count_cap, total_dev);
+  count_launch(), k_scan_down<<<grid, kScanThreads, 0, s>>>(in, out, count_dev, count_cap, bsum);
   return cudaGetLastError();
 }
 
@@ -390,24 +390,24 @@ cudaError_t launch_build_pairs(const Layout& L, void* ws, int tile_bits, cudaStr
   const int64_t R = L.R;
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>((R + 255) / 256, kGrid));
   // 1. compact visible records, keyed by FP32 depth bits (record index low)
-  k_visible_flags<<<g, 256, 0, s>>>(ntiles, scan, R, &st->scan_total);
+  count_launch(), k_visible_flags<<<g, 256, 0, s>>>(ntiles, scan, R, &st->scan_total);
   cudaError_t e = scan_u32(ws, L, scan, scan, &st->scan_total, R, &st->visible, s);
   if (e != cudaSuccess) return e;
-  k_compact_depth<<<g, 256, 0, s>>>(ntiles, depth, scan, dk0, R);
+  count_launch(), k_compact_depth<<<g, 256, 0, s>>>(ntiles, depth, scan, dk0, R);
   // 2. stable sort by depth (records in index order for equal depth)
   bool in_b = false;
   e = sort_u64(ws, L, dk0, dk1, &st->visible, R, 32, 4, &in_b, s);
   if (e != cudaSuccess) return e;
   const uint64_t* dsorted = in_b ? dk1 : dk0;
   // 3. pair offsets in depth order, total pair count and capacity check
-  k_gather_ntiles<<<g, 256, 0, s>>>(dsorted, ntiles, scan, &st->visible);
+  count_launch(), k_gather_ntiles<<<g, 256, 0, s>>>(dsorted, ntiles, scan, &st->visible);
   e = scan_u32(ws, L, scan, scan, &st->visible, R, &st->scan_total, s);
   if (e != cudaSuccess) return e;
-  k_capacity<<<1, 1, 0, s>>>(st, L.Kc);
+  count_launch(), k_capacity<<<1, 1, 0, s>>>(st, L.Kc);
   // 4. emit pairs in depth order
   uint64_t* p0 = ws_ptr<uint64_t>(ws, L.pairs0);
   uint64_t* p1 = ws_ptr<uint64_t>(ws, L.pairs1);
-  k_emit_pairs<<<g, 256, 0, s>>>(dsorted, scan, ws_ptr<const ushort4>(ws, L.rect), ws_ptr<ViewInfo>(ws, L.views),
+  count_launch(), k_emit_pairs<<<g, 256, 0, s>>>(dsorted, scan, ws_ptr<const ushort4>(ws, L.rect), ws_ptr<ViewInfo>(ws, L.views),
                                  L.n, ws_ptr<uint32_t>(ws, L.offrec), p0, st);
   // 5. stable sort on the tile bits
   const int passes = (tile_bits + 7) / 8;
@@ -417,9 +417,9 @@ cudaError_t launch_build_pairs(const Layout& L, void* ws, int tile_bits, cudaStr
   // 6. per-tile ranges
   uint2* ranges = ws_ptr<uint2>(ws, L.ranges);
   const int gt = (int)std::max<int64_t>(1, std::min<int64_t>((2 * L.T + 255) / 256, kGrid));
-  k_zero_u32<<<gt, 256, 0, s>>>(reinterpret_cast<uint32_t*>(ranges), 2 * L.T);
+  count_launch(), k_zero_u32<<<gt, 256, 0, s>>>(reinterpret_cast<uint32_t*>(ranges), 2 * L.T);
   const int gk = (int)std::max<int64_t>(1, std::min<int64_t>((L.Kc + 255) / 256, kGrid));
-  k_ranges<<<gk, 256, 0, s>>>(psorted, ranges, st);
+  count_launch(), k_ranges<<<gk, 256, 0, s>>>(psorted, ranges, st);
   return cudaGetLastError();
 }
 
