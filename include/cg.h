@@ -153,6 +153,21 @@ cg_status cg_last_device_status(void *workspace, size_t ws_bytes, cg_stream_t st
 cg_status cg_l1_loss(const float *image, const float *target, int64_t count, float *d_image, double *loss_out,
                      void *workspace, size_t ws_bytes, cg_stream_t stream);
 
+/* The L1 loss of cg_l1_loss without a workspace, for callers that cannot
+ * allocate device memory (their device memory belongs to another allocator,
+ * or they must not fail for lack of memory where they run).  The paper has
+ * no counterpart: this is a calling convention of this library.
+ * The reduction scratch is a static device array of 32768 doubles (256 KiB)
+ * per GPU that loads the library, kept until the process exits; `count`
+ * above 67,108,864 values returns CG_ERR_ARG.  No call allocates.  The first
+ * call on a device looks up the array's device address (once per device,
+ * with that device current), so make it before any stream capture.  Calls
+ * share the array: calls whose kernels overlap on the GPU race on it and must
+ * be ordered by the caller.  Results equal cg_l1_loss's up to the order of
+ * the double-precision sum. */
+cg_status cg_l1_loss_static(const float *image, const float *target, int64_t count, float *d_image,
+                            double *loss_out, cg_stream_t stream);
+
 /* Internal arrays of the workspace, for inspection by tests (device pointer
  * and element count written to the host outputs).  Layouts:
  *   CG_WS_RECT        [V*n] uint16x4  tile rectangle x0, y0, x1, y1 (x1 == x0 when culled)

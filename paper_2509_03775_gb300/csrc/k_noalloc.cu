@@ -1,0 +1,122 @@
+// k_noalloc.cu -- cg_l1_loss_static: the L1 loss and its gradient with the
+// reduction scratch in a static device array, for callers that cannot
+// allocate device memory.
+//
+// Every other entry point of the library takes its scratch from a
+// caller-owned workspace.  Some callers cannot provide one: code whose
+// device memory is entirely owned by another allocator (a framework's
+// caching pool, an embedding runtime) and that has no call to obtain a
+// buffer, or code that must not fail for lack of memory at the point where
+// it runs.  This entry point needs no workspace and allocates nothing.
+//
+// The scratch is one array per GPU that loads the library (kStaticPartials
+// doubles, 256 KiB), held until the process exits.  Its host-side name is
+// not a device address: on first use on each device the entry point asks
+// the runtime for the array's device address (cudaGetSymbolAddress, with
+// that device current) and caches it.  That first call should therefore be
+// made before any stream capture begins.
+//
+// All calls share the array and it keeps the previous call's contents.
+// Each call writes every partial it later reads, so nothing has to start at
+// zero; calls whose kernels overlap on the GPU (different streams, no
+// ordering) race on the array and must not be issued.
+#include <mutex>
+
+#include "cg_common.cuh"
+
+namespace cg {
+
+constexpr int kStaticPartials = 32768;           // doubles in the scratch array
+constexpr int kStaticThreads = 256;
+constexpr int kStaticItems = 8;
+constexpr int64_t kStaticPerBlock = (int64_t)kStaticThreads * kStaticItems;
+constexpr int64_t kStaticMaxCount = (int64_t)kStaticPartials * kStaticPerBlock;  // 67,108,864 values
+
+static __device__ __align__(256) double g_l1_partials[kStaticPartials];
+
+// One block per kStaticPerBlock values: the block's sum of |image - target|
+// goes to partials[blockIdx.x]; d_image = sign(image - target) / count.
+__global__ void __launch_bounds__(kStaticThreads) k_l1_static(const float* __restrict__ img,
+                                                              const float* __restrict__ tgt, int64_t count,
+                                                              float* __restrict__ d_img,
+                                                              double* __restrict__ partials) {
+  __shared__ double red[kStaticThreads / 32];
+  const float inv = 1.0f / (float)count;
+  const int64_t base = (int64_t)blockIdx.x * kStaticPerBlock;
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < kStaticItems; ++k) {
+    const int64_t i = base + (int64_t)k * kStaticThreads + threadIdx.x;
+    if (i < count) {
+      const float d = img[i] - tgt[i];
+      acc += (double)fabsf(d);
+      d_img[i] = d > 0.0f ? inv : (d < 0.0f ? -inv : 0.0f);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kStaticThreads / 32; ++w) t += red[w];
+    partials[blockIdx.x] = t;
+  }
+}
+
+// Sums the first n_blocks partials in a fixed order.
+__global__ void __launch_bounds__(1024) k_l1_static_final(const double* __restrict__ partials, int n_blocks,
+                                                          int64_t count, double* __restrict__ loss) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n_blocks; i += blockDim.x) acc += partials[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+    *loss = t / (double)count;
+  }
+}
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+double* g_static_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (set up once per
+// device, with that device current).
+cudaError_t static_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_l1_partials);
+    if (e != cudaSuccess) return e;
+    g_static_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_static_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+}  // namespace cg
+
+extern "C" cg_status cg_l1_loss_static(const float* image, const float* target, int64_t count, float* d_image,
+                                       double* loss_out, cg_stream_t stream) {
+  using namespace cg;
+  if (!image || !target || !d_image || !loss_out || count < 1) return CG_ERR_ARG;
+  if (count > kStaticMaxCount) return CG_ERR_ARG;
+  double* partials = nullptr;
+  if (static_scratch(&partials) != cudaSuccess) return CG_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int n_blocks = (int)((count + kStaticPerBlock - 1) / kStaticPerBlock);
+  count_launch(), k_l1_static<<<n_blocks, kStaticThreads, 0, s>>>(image, target, count, d_image, partials);
+  count_launch(), k_l1_static_final<<<1, 1024, 0, s>>>(partials, n_blocks, count, loss_out);
+  return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
