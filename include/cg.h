@@ -6,13 +6,13 @@
  * The method (ContraGS, arXiv 2509.03775):
  *   State S = {G, C} (Sec. 3.1).  A Gaussian g_i = {p_i, o_i, g2sr_i, g2sh_i}
  *   holds a position, an opacity and two integer indices; its scale and
- *   rotation come from row g2sr_i of the SR codebook ("scaling + quaternion
- *   concatenated", Fig. 4) and its SH colour coefficients from row g2sh_i of
+ *   rotation come from row g2sr_i of the SR codebook (its scales followed by
+ *   its quaternion, Fig. 4) and its SH colour coefficients from row g2sh_i of
  *   the SH codebook.  The image I_P(G, C) of camera P (the posterior of
  *   Sec. 3.2 is a function of it) is Eq. 3 over Gaussians whose density is
  *   Eq. 1 with the covariance of Eq. 2, projected onto the image plane.
  *   Training updates p, o, SH and SR with the gradient of the loss
- *   (Sec. 3.4, "S_diff", and the SGLD steps of Appendix A.1); a codebook
+ *   (the differentiable set S_diff of Sec. 3.4, and the SGLD steps of Appendix A.1); a codebook
  *   row's gradient is the sum over the Gaussians that index it.
  *
  * Conventions shared by every call:

@@ -10,9 +10,9 @@
  *     (Sec. 3.1): every Gaussian reads its scale+rotation from SR[g2sr_i]
  *     and its SH colour coefficients from SH[g2sh_i];
  *   - Eq. 2: Sigma = R(q) S S^T R(q)^T;
- *   - Eq. 1 projected onto the image plane (Sec. 2.1: "alpha_i is the 2D
- *     Gaussian projected from the 3D density"), with the local affine (EWA)
- *     Jacobian of the pinhole map;
+ *   - Eq. 1 projected onto the image plane (Sec. 2.1 defines alpha_i as that
+ *     projected 2D Gaussian), with the local affine (EWA) Jacobian of the
+ *     pinhole map;
  *   - c_i: the SH colour seen along the viewing direction (Sec. 2.1);
  *   - Eq. 3: front-to-back compositing C = sum_k alpha_k c_k prod_{i<k}(1-alpha_i);
  *   - the exact chain rule of all of the above (the gradient that the
