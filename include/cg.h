@@ -92,14 +92,21 @@ typedef struct {
 
 /* tile: 8, 16 or 32 pixels (square tiles; the tile size changes which
  * Gaussians a tile lists, so it is part of the image definition).
- * batch: Gaussians staged in shared memory per step of the blend kernels,
- * 0 = default; one of 32, 64, 128, 256.  bg: background colour added with
- * the final transmittance.  pair_capacity: (tile, Gaussian) pairs the
- * workspace has room for (1 <= pair_capacity < 2^32); every call on a
- * workspace must pass the value it was sized with. */
+ * batch, batch_bwd: Gaussians staged in shared memory per step of the
+ * forward / backward blend kernel (0 = default; forward 64, 128 or 256,
+ * backward 32, 64 or 128).  ppt_fwd, ppt_bwd: pixels per thread of the
+ * blend kernels (0 = default; 1 or 2 for 8x8 tiles, 1, 2 or 4 for 16x16,
+ * 4 for 32x32).  These four change speed only, never results.
+ * bg: background colour added with the final transmittance.
+ * pair_capacity: (tile, Gaussian) pairs the workspace has room for
+ * (1 <= pair_capacity < 2^32); every call on a workspace must pass the value
+ * it was sized with. */
 typedef struct {
   int tile;
   int batch;
+  int batch_bwd;
+  int ppt_fwd;
+  int ppt_bwd;
   float bg[3];
   uint32_t pair_capacity;
 } cg_opts;

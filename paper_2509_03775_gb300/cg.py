@@ -54,7 +54,8 @@ class Scene(ctypes.Structure):
 
 
 class Opts(ctypes.Structure):
-    _fields_ = [("tile", ctypes.c_int), ("batch", ctypes.c_int), ("bg", ctypes.c_float * 3),
+    _fields_ = [("tile", ctypes.c_int), ("batch", ctypes.c_int), ("batch_bwd", ctypes.c_int),
+                ("ppt_fwd", ctypes.c_int), ("ppt_bwd", ctypes.c_int), ("bg", ctypes.c_float * 3),
                 ("pair_capacity", ctypes.c_uint32)]
 
 
@@ -211,11 +212,13 @@ class Renderer:
     """
 
     def __init__(self, cams: Sequence, tile: int = 16, batch: int = 0, bg=(0.0, 0.0, 0.0),
-                 pair_capacity: int = 1 << 20, device: str | torch.device = "cuda"):
+                 pair_capacity: int = 1 << 20, device: str | torch.device = "cuda", batch_bwd: int = 0,
+                 ppt_fwd: int = 0, ppt_bwd: int = 0):
         self.lib = load()
         self.cams = list(cams)
         self._cams = camera_array(self.cams)
         self.tile, self.batch = int(tile), int(batch)
+        self.batch_bwd, self.ppt_fwd, self.ppt_bwd = int(batch_bwd), int(ppt_fwd), int(ppt_bwd)
         self.bg = tuple(float(b) for b in bg)
         self.pair_capacity = int(pair_capacity)
         self.device = torch.device(device)
@@ -226,7 +229,8 @@ class Renderer:
 
     def opts(self) -> Opts:
         o = Opts()
-        o.tile, o.batch = self.tile, self.batch
+        o.tile, o.batch, o.batch_bwd = self.tile, self.batch, self.batch_bwd
+        o.ppt_fwd, o.ppt_bwd = self.ppt_fwd, self.ppt_bwd
         for i in range(3):
             o.bg[i] = self.bg[i]
         o.pair_capacity = self.pair_capacity

@@ -75,7 +75,10 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
   if (s->cb_dtype != CG_F32 && s->cb_dtype != CG_BF16) return CG_ERR_ARG;
   if (n_views < 1 || n_views > CG_MAX_VIEWS) return CG_ERR_ARG;
   if (o->tile != 8 && o->tile != 16 && o->tile != 32) return CG_ERR_ARG;
-  if (o->batch != 0 && o->batch != 32 && o->batch != 64 && o->batch != 128 && o->batch != 256) return CG_ERR_ARG;
+  if (o->batch != 0 && o->batch != 64 && o->batch != 128 && o->batch != 256) return CG_ERR_ARG;
+  if (o->batch_bwd != 0 && o->batch_bwd != 32 && o->batch_bwd != 64 && o->batch_bwd != 128) return CG_ERR_ARG;
+  if (o->ppt_fwd != 0 && !blend_ppt_ok(o->tile, o->ppt_fwd)) return CG_ERR_ARG;
+  if (o->ppt_bwd != 0 && !blend_ppt_ok(o->tile, o->ppt_bwd)) return CG_ERR_ARG;
   if (o->pair_capacity < 1) return CG_ERR_ARG;
   const int64_t n = s->n;
   const int64_t R = n * n_views;
@@ -107,7 +110,7 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
   L->n = n; L->R = R; L->T = T; L->P = P; L->Kc = Kc;
   L->k_sr = s->k_sr; L->k_sh = s->k_sh; L->nb = nb; L->n_views = n_views; L->tile = o->tile;
   L->tile_bits = std::max(1, ceil_log2(T));
-  L->sort_blocks_cap = (std::max(Kc, R) + 4095) / 4096 + 1;
+  L->sort_blocks_cap = (std::max(Kc, R) + 4095) / 4096 + 1;  // 4096 keys per sort block
   const int64_t kmax = std::max(s->k_sr, s->k_sh) + 1;
   L->scan_blocks_cap = (std::max(R, kmax) + 4095) / 4096 + 1;
   L->chunks_cap = (n + 255) / 256 + kmax;
@@ -134,9 +137,13 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
   L->ranges = take(sizeof(uint32_t) * 2 * T);
   L->tfinal = take(sizeof(float) * P);
   L->ncontrib = take(sizeof(uint32_t) * P);
-  L->pairgrad = take(sizeof(float) * 9 * Kc);
+  L->pairgrad = take(sizeof(float4) * 2 * Kc);   // 8 sums per pair, one 32-byte sector
+  L->pairgrad1 = take(sizeof(float) * Kc);        // the opacity sum per pair
+  L->recgrad = take(sizeof(float) * 10 * R);
   L->dsigma = take(sizeof(float) * 6 * n);
   L->drgb = take(sizeof(float) * 3 * R);
+  L->csr_keys0 = take(sizeof(uint64_t) * n);
+  L->csr_keys1 = take(sizeof(uint64_t) * n);
   L->csr_off_sr = take(sizeof(uint32_t) * (3 * (int64_t)s->k_sr + 1));
   L->csr_off_sh = take(sizeof(uint32_t) * (3 * (int64_t)s->k_sh + 1));
   L->csr_ids_sr = take(sizeof(uint32_t) * n);
@@ -163,6 +170,12 @@ cg_status check_ws(void* ws, size_t ws_bytes, const Layout& L) {
   if (!ws || !aligned(ws, kAlign) || ws_bytes < L.total) return CG_ERR_ARG;
   return CG_OK;
 }
+
+// Blend launch shape: defaults per tile size (measured on GB300).
+int fwd_batch(const cg_opts* o) { return o->batch ? o->batch : 256; }
+int bwd_batch(const cg_opts* o) { return o->batch_bwd ? o->batch_bwd : 64; }
+int fwd_ppt(const cg_opts* o) { return o->ppt_fwd ? o->ppt_fwd : (o->tile == 32 ? 4 : 1); }
+int bwd_ppt(const cg_opts* o) { return o->ppt_bwd ? o->ppt_bwd : (o->tile == 32 ? 4 : 2); }
 
 SceneArgs scene_args(const cg_scene* s) {
   SceneArgs a;
@@ -204,7 +217,6 @@ cg_status cg_render_fwd(const cg_scene* scene, const cg_camera* cams, int n_view
   if (st != CG_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const SceneArgs sc = scene_args(scene);
-  const int batch = opts->batch ? opts->batch : 256;
   cudaError_t e;
   {
     StageTimer t(CG_STAGE_PREPROCESS, s);
@@ -218,7 +230,7 @@ cg_status cg_render_fwd(const cg_scene* scene, const cg_camera* cams, int n_view
   }
   if (e == cudaSuccess) {
     StageTimer t(CG_STAGE_BLEND_FWD, s);
-    e = launch_blend_fwd(L, workspace, opts->tile, batch, opts->bg, images, s);
+    e = launch_blend_fwd(L, workspace, opts->tile, fwd_batch(opts), fwd_ppt(opts), opts->bg, images, s);
   }
   return cuda_status(e);
 }
@@ -234,11 +246,10 @@ cg_status cg_render_bwd(const cg_scene* scene, const cg_camera* cams, int n_view
   if (st != CG_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const SceneArgs sc = scene_args(scene);
-  const int batch = opts->batch ? std::min(opts->batch, 128) : 64;
   cudaError_t e;
   {
     StageTimer t(CG_STAGE_BLEND_BWD, s);
-    e = launch_blend_bwd(L, workspace, opts->tile, batch, opts->bg, d_images, s);
+    e = launch_blend_bwd(L, workspace, opts->tile, bwd_batch(opts), bwd_ppt(opts), opts->bg, d_images, s);
   }
   if (e == cudaSuccess) {
     StageTimer t(CG_STAGE_GAUSS_BWD, s);

@@ -209,7 +209,7 @@ struct ViewTable {
 struct Layout {
   uint64_t total;
   uint64_t hdr, views, sigma3, geo, rgbm, rect, ntiles, depth, offrec, scan, dkeys0, dkeys1, pairs0, pairs1,
-      ranges, tfinal, ncontrib, pairgrad, dsigma, drgb, csr_off_sr, csr_off_sh, csr_ids_sr, csr_ids_sh, chunks,
+      ranges, tfinal, ncontrib, pairgrad, pairgrad1, recgrad, dsigma, drgb, csr_keys0, csr_keys1, csr_off_sr, csr_off_sh, csr_ids_sr, csr_ids_sh, chunks,
       partials, hist, blocksums, l1;
   // sizes
   int64_t n, R, T, P, Kc;
@@ -228,6 +228,7 @@ struct DeviceState {
   uint64_t scan_total;  // scratch total written by the scan kernels
   uint32_t pairs_ok;    // 1 if pairs <= capacity
   uint32_t pad;
+  uint64_t red_a, red_b;  // counts used by the codebook reduction
 };
 
 struct WsHeader {
@@ -278,16 +279,20 @@ cudaError_t launch_setup(const ViewTable& table, const Layout& L, void* ws, cuda
 cudaError_t launch_sigma3(const SceneArgs& sc, const Layout& L, void* ws, cudaStream_t s);
 cudaError_t launch_preprocess(const SceneArgs& sc, const Layout& L, void* ws, cudaStream_t s);
 cudaError_t launch_build_pairs(const Layout& L, void* ws, int tile_bits, cudaStream_t s);
-cudaError_t launch_blend_fwd(const Layout& L, void* ws, int tile, int batch, const float bg[3], float* images,
-                             cudaStream_t s);
-cudaError_t launch_blend_bwd(const Layout& L, void* ws, int tile, int batch, const float bg[3],
+cudaError_t launch_blend_fwd(const Layout& L, void* ws, int tile, int batch, int ppt, const float bg[3],
+                             float* images, cudaStream_t s);
+cudaError_t launch_blend_bwd(const Layout& L, void* ws, int tile, int batch, int ppt, const float bg[3],
                              const float* d_images, cudaStream_t s);
+bool blend_ppt_ok(int tile, int ppt);
 cudaError_t launch_gaussian_bwd(const SceneArgs& sc, const Layout& L, void* ws, float* d_pos, float* d_logit,
                                 cudaStream_t s);
 cudaError_t launch_codebook_reduce(const SceneArgs& sc, const Layout& L, void* ws, float* d_sr, float* d_sh,
                                    cudaStream_t s);
 cudaError_t launch_l1(const float* img, const float* tgt, int64_t count, float* d_img, double* loss,
                       const Layout& L, void* ws, cudaStream_t s);
+
+// The depth-sorted visible records (4 sort passes end in dkeys0).
+inline uint64_t* depth_sorted(void* ws, const Layout& L) { return ws_ptr<uint64_t>(ws, L.dkeys0); }
 
 // Radix sort of `count` (device value) uint64 keys on bits [lo, lo + 8 * passes),
 // stable, ping-pong between a and b; returns in *result_in_b whether the

@@ -1,29 +1,53 @@
 // k_blend.cu -- per-tile compositing of Eq. 3 (forward) and its reverse
-// (backward), one CTA per tile.
+// (backward), one CTA per tile, PPT vertically adjacent pixels per thread.
 //
 // Forward: the tile's sorted Gaussians are staged in shared memory in
-// batches; every thread walks them front to back for its pixel(s) with the
+// batches; every thread walks them front to back for its pixels with the
 // decision arithmetic (skip alpha < 1/255, clamp at 0.99, stop before the
 // transmittance would fall below 1e-4), and writes the colour, the final
 // transmittance and the position after the last contributor.
 //
 // Backward: the tile's list is walked back to front from the largest
 // contributor position of the tile.  Each pixel recomputes alpha with the
-// same arithmetic (so it takes the forward's decisions exactly) and
-// undoes the transmittance by division.  The nine per-pixel gradient terms of
-// every (tile, Gaussian) pair -- mean x/y, conic 0/1/2, opacity, colour
-// r/g/b -- are summed over the tile's pixels in a fixed order (registers,
-// warp butterfly, warps in index order) and written to the pair's slot, so
-// the per-Gaussian gradient later sums a fixed set of slots in a fixed order.
+// same arithmetic (so it takes the forward's decisions exactly) and undoes
+// the transmittance by division.  The nine per-pixel gradient terms of every
+// (tile, Gaussian) pair -- mean x/y, conic 0/1/2, opacity, colour r/g/b --
+// are summed in a fixed order: over a thread's pixels, then across the warp
+// by a reduce-scatter butterfly over groups of three Gaussians (27 values,
+// 31 shuffles, lane l ends with value l), then over the warps in index order.
+// The pair's sums go to its slot (slots of a Gaussian are contiguous, in
+// tile order): eight of them as one aligned 32-byte sector (mean x/y,
+// conic 0/1/2, colour r/g/b), the opacity sum in a separate array.  The
+// per-Gaussian gradient later sums a fixed set of slots in a fixed order.
+// No floating-point atomics.
+//
+// The backward takes the forward's decisions exactly, but it only needs
+// alpha as a value: it uses the hardware exp and recomputes the library's
+// exact exp32 only when the value lies within 1e-5 (relative) of the skip
+// or clamp threshold, where the two could decide differently (both are
+// within 1e-6 of exp).
 #include <algorithm>
 
 #include "cg_common.cuh"
 
 namespace cg {
 
-struct BlendGeo {
-  float4 a;  // mean x, mean y, h0, h1
-  float4 b;  // h2, opacity, skip bound, 0
+struct BlendArgs {
+  const ViewInfo* views;
+  int n_views;
+  const uint2* ranges;
+  const uint64_t* pairs;
+  const float4* geo;
+  const float4* rgbm;
+  const ushort4* rect;
+  const uint32_t* offrec;
+  float bg0, bg1, bg2;
+  float* images;          // forward output
+  const float* d_images;  // backward input
+  float* tfinal;
+  uint32_t* ncontrib;
+  float4* pairgrad;   // [K][2]
+  float* pairgrad1;   // [K]
 };
 
 // power = h0 dx^2 + h1 dx dy + h2 dy^2 with d = mean - pixel centre
@@ -35,36 +59,40 @@ __device__ __forceinline__ float gauss_power(const float4& a, const float4& b, f
   return fmaf(a.z * dx, dx, fmaf(b.x * dy, dy, (a.w * dx) * dy));
 }
 
-template <int TILE, int BATCH>
-__global__ void __launch_bounds__(TILE* TILE < 256 ? TILE* TILE : 256)
-    k_blend_fwd(const ViewInfo* __restrict__ views, int n_views, const uint2* __restrict__ ranges,
-                const uint64_t* __restrict__ pairs, const float4* __restrict__ geo, const float4* __restrict__ rgbm,
-                float bg0, float bg1, float bg2, float* __restrict__ images, float* __restrict__ tfinal,
-                uint32_t* __restrict__ ncontrib) {
-  constexpr int NT = TILE * TILE < 256 ? TILE * TILE : 256;
-  constexpr int PPT = TILE * TILE / NT;
+template <int TILE, int PPT>
+struct TileShape {
+  static constexpr int NT = TILE * TILE / PPT;
+  static constexpr int NW = NT / 32;
+  static_assert(NT % 32 == 0 && NT <= 256, "unsupported tile / pixels-per-thread");
+  // pixel k of thread t: column t % TILE, row (t / TILE) * PPT + k
+  __device__ static int px(int t) { return t % TILE; }
+  __device__ static int py(int t, int k) { return (t / TILE) * PPT + k; }
+};
+
+template <int TILE, int BATCH, int PPT>
+__global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_fwd(const BlendArgs args) {
+  using S = TileShape<TILE, PPT>;
+  constexpr int NT = S::NT;
   __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
   const int64_t gt = blockIdx.x;
-  const int v = find_view(views, n_views, gt);
-  const ViewInfo& cam = views[v];
+  const int v = find_view(args.views, args.n_views, gt);
+  const ViewInfo& cam = args.views[v];
   const int64_t lt = gt - cam.tile_base;
   const int tx = (int)(lt % cam.tiles_x), ty = (int)(lt / cam.tiles_x);
-  const uint2 rg = ranges[gt];
-  float pxc[PPT], pyc[PPT], T[PPT], C[PPT][3];
+  const uint2 rg = args.ranges[gt];
+  const int x = tx * TILE + S::px(threadIdx.x);
+  const float pxc = (float)x + 0.5f;
+  float pyc[PPT], T[PPT], C[PPT][3];
   uint32_t last[PPT];
   bool done[PPT];
-  int px[PPT], py[PPT];
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
-    const int p = threadIdx.x + k * NT;
-    px[k] = tx * TILE + p % TILE;
-    py[k] = ty * TILE + p / TILE;
-    pxc[k] = (float)px[k] + 0.5f;
-    pyc[k] = (float)py[k] + 0.5f;
+    const int y = ty * TILE + S::py(threadIdx.x, k);
+    pyc[k] = (float)y + 0.5f;
     T[k] = 1.0f;
     C[k][0] = C[k][1] = C[k][2] = 0.0f;
     last[k] = 0;
-    done[k] = !(px[k] < cam.width && py[k] < cam.height);
+    done[k] = !(x < cam.width && y < cam.height);
   }
   for (uint32_t b0 = rg.x; b0 < rg.y; b0 += BATCH) {
     bool mine = true;
@@ -73,10 +101,10 @@ __global__ void __launch_bounds__(TILE* TILE < 256 ? TILE* TILE : 256)
     if (__syncthreads_and(mine)) break;
     const int n_in = (int)min((uint32_t)BATCH, rg.y - b0);
     for (int j = threadIdx.x; j < n_in; j += NT) {
-      const uint32_t rec = (uint32_t)pairs[b0 + j];
-      sA[j] = geo[2 * (size_t)rec];
-      sB[j] = geo[2 * (size_t)rec + 1];
-      sC[j] = rgbm[rec];
+      const uint32_t rec = (uint32_t)args.pairs[b0 + j];
+      sA[j] = args.geo[2 * (size_t)rec];
+      sB[j] = args.geo[2 * (size_t)rec + 1];
+      sC[j] = args.rgbm[rec];
     }
     __syncthreads();
     for (int j = 0; j < n_in; ++j) {
@@ -85,7 +113,7 @@ __global__ void __launch_bounds__(TILE* TILE < 256 ? TILE* TILE : 256)
       for (int k = 0; k < PPT; ++k) {
         if (done[k]) continue;
         float dx, dy;
-        const float power = gauss_power(a, b, pxc[k], pyc[k], dx, dy);
+        const float power = gauss_power(a, b, pxc, pyc[k], dx, dy);
         if (power > 0.0f || power < b.z) continue;
         const float vv = b.y * exp32(power);
         const float alpha = vv > kAlphaMax ? kAlphaMax : vv;
@@ -108,67 +136,138 @@ __global__ void __launch_bounds__(TILE* TILE < 256 ? TILE* TILE : 256)
   const int64_t hw = (int64_t)cam.width * cam.height;
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
-    if (!(px[k] < cam.width && py[k] < cam.height)) continue;
-    const int64_t pix = cam.pix_base + (int64_t)py[k] * cam.width + px[k];
-    float* img = images + 3 * cam.pix_base + (int64_t)py[k] * cam.width + px[k];
-    img[0] = fmaf(T[k], bg0, C[k][0]);
-    img[hw] = fmaf(T[k], bg1, C[k][1]);
-    img[2 * hw] = fmaf(T[k], bg2, C[k][2]);
-    tfinal[pix] = T[k];
-    ncontrib[pix] = last[k];
+    const int y = ty * TILE + S::py(threadIdx.x, k);
+    if (!(x < cam.width && y < cam.height)) continue;
+    const int64_t pix = cam.pix_base + (int64_t)y * cam.width + x;
+    float* img = args.images + 3 * cam.pix_base + (int64_t)y * cam.width + x;
+    img[0] = fmaf(T[k], args.bg0, C[k][0]);
+    img[hw] = fmaf(T[k], args.bg1, C[k][1]);
+    img[2 * hw] = fmaf(T[k], args.bg2, C[k][2]);
+    args.tfinal[pix] = T[k];
+    args.ncontrib[pix] = last[k];
   }
 }
 
-template <int TILE, int BATCH>
-__global__ void __launch_bounds__(TILE* TILE < 256 ? TILE* TILE : 256)
-    k_blend_bwd(const ViewInfo* __restrict__ views, int n_views, const uint2* __restrict__ ranges,
-                const uint64_t* __restrict__ pairs, const float4* __restrict__ geo, const float4* __restrict__ rgbm,
-                const ushort4* __restrict__ rect, const uint32_t* __restrict__ offrec, float bg0, float bg1,
-                float bg2, const float* __restrict__ d_images, const float* __restrict__ tfinal,
-                const uint32_t* __restrict__ ncontrib, float* __restrict__ pairgrad) {
-  constexpr int NT = TILE * TILE < 256 ? TILE * TILE : 256;
-  constexpr int PPT = TILE * TILE / NT;
-  constexpr int NW = NT / 32;
+// Reduce-scatter of 32 values across the warp: returns, in lane l, the sum
+// over the 32 lanes of value l.  Fixed butterfly, so bitwise reproducible.
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
+  const unsigned lane = threadIdx.x & 31u;
+#define CG_RS_STAGE(O)                                        \
+  {                                                           \
+    const bool up = (lane & (O)) != 0u;                       \
+    _Pragma("unroll") for (int i = 0; i < (O); ++i) {         \
+      const float send = up ? v[i] : v[i + (O)];              \
+      const float keep = up ? v[i + (O)] : v[i];              \
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, (O));  \
+    }                                                         \
+  }
+  CG_RS_STAGE(16)
+  CG_RS_STAGE(8)
+  CG_RS_STAGE(4)
+  CG_RS_STAGE(2)
+  CG_RS_STAGE(1)
+#undef CG_RS_STAGE
+  return v[0];
+}
+
+template <int PPT>
+struct PixelBwd {
+  float pyc[PPT], T[PPT], dC[PPT][3], acc[PPT][3], bgdot[PPT];
+  uint32_t nc[PPT];
+};
+
+// Per-pixel backward of one Gaussian at list position `pos`; adds its nine
+// terms (summed over the thread's pixels) into g[9 * S ...].
+template <int PPT, int S>
+__device__ __forceinline__ bool bwd_gaussian(const float4& a, const float4& b, const float4& c, uint32_t pos,
+                                             float pxc, PixelBwd<PPT>& px, float (&g)[32]) {
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    if (pos >= px.nc[k]) continue;
+    float dx, dy;
+    const float power = gauss_power(a, b, pxc, px.pyc[k], dx, dy);
+    if (power > 0.0f || power < b.z) continue;
+    float ex = __expf(power);
+    float vv = b.y * ex;
+    if (fabsf(vv - kAlphaMin) < 1e-5f * kAlphaMin || fabsf(vv - kAlphaMax) < 1e-5f * kAlphaMax) {
+      ex = exp32(power);
+      vv = b.y * ex;
+    }
+    const bool clamped = vv > kAlphaMax;
+    const float alpha = clamped ? kAlphaMax : vv;
+    if (alpha < kAlphaMin) continue;
+    any = true;
+    const float om = 1.0f - alpha;
+    const float rom = __fdividef(1.0f, om);
+    const float Tk = px.T[k] * rom;
+    const float w = alpha * Tk;
+    g[9 * S + 6] = fmaf(w, px.dC[k][0], g[9 * S + 6]);
+    g[9 * S + 7] = fmaf(w, px.dC[k][1], g[9 * S + 7]);
+    g[9 * S + 8] = fmaf(w, px.dC[k][2], g[9 * S + 8]);
+    const float dot = fmaf(c.x - px.acc[k][0], px.dC[k][0],
+                           fmaf(c.y - px.acc[k][1], px.dC[k][1], (c.z - px.acc[k][2]) * px.dC[k][2]));
+    const float dalpha = fmaf(Tk, dot, -px.bgdot[k] * rom);
+    if (!clamped) {
+      const float dpow = alpha * dalpha;
+      g[9 * S + 0] = fmaf(dpow, fmaf(2.0f * a.z, dx, a.w * dy), g[9 * S + 0]);
+      g[9 * S + 1] = fmaf(dpow, fmaf(2.0f * b.x, dy, a.w * dx), g[9 * S + 1]);
+      g[9 * S + 2] = fmaf(dpow, -0.5f * dx * dx, g[9 * S + 2]);
+      g[9 * S + 3] = fmaf(dpow, -dx * dy, g[9 * S + 3]);
+      g[9 * S + 4] = fmaf(dpow, -0.5f * dy * dy, g[9 * S + 4]);
+      g[9 * S + 5] = fmaf(ex, dalpha, g[9 * S + 5]);
+    }
+    px.acc[k][0] = fmaf(alpha, c.x - px.acc[k][0], px.acc[k][0]);
+    px.acc[k][1] = fmaf(alpha, c.y - px.acc[k][1], px.acc[k][1]);
+    px.acc[k][2] = fmaf(alpha, c.z - px.acc[k][2], px.acc[k][2]);
+    px.T[k] = Tk;
+  }
+  return any;
+}
+
+template <int TILE, int BATCH, int PPT>
+__global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const BlendArgs args) {
+  using S = TileShape<TILE, PPT>;
+  constexpr int NT = S::NT, NW = S::NW;
   __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
   __shared__ uint32_t sSlot[BATCH];
   __shared__ float part[NW][BATCH][9];
   __shared__ uint32_t s_maxc;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t gt = blockIdx.x;
-  const int v = find_view(views, n_views, gt);
-  const ViewInfo& cam = views[v];
+  const int v = find_view(args.views, args.n_views, gt);
+  const ViewInfo& cam = args.views[v];
   const int64_t lt = gt - cam.tile_base;
   const int tx = (int)(lt % cam.tiles_x), ty = (int)(lt / cam.tiles_x);
-  const uint2 rg = ranges[gt];
+  const uint2 rg = args.ranges[gt];
   const int64_t hw = (int64_t)cam.width * cam.height;
-  float pxc[PPT], pyc[PPT], T[PPT], tfin[PPT], dC[PPT][3], acc[PPT][3], bgdot[PPT];
-  uint32_t nc[PPT];
+  const int x = tx * TILE + S::px(threadIdx.x);
+  const float pxc = (float)x + 0.5f;
+  PixelBwd<PPT> px;
   if (threadIdx.x == 0) s_maxc = 0;
   __syncthreads();
   uint32_t my_max = 0;
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
-    const int p = threadIdx.x + k * NT;
-    const int x = tx * TILE + p % TILE, y = ty * TILE + p / TILE;
-    pxc[k] = (float)x + 0.5f;
-    pyc[k] = (float)y + 0.5f;
-    acc[k][0] = acc[k][1] = acc[k][2] = 0.0f;
+    const int y = ty * TILE + S::py(threadIdx.x, k);
+    px.pyc[k] = (float)y + 0.5f;
+    px.acc[k][0] = px.acc[k][1] = px.acc[k][2] = 0.0f;
+    float tf = 1.0f;
     if (x < cam.width && y < cam.height) {
       const int64_t pix = cam.pix_base + (int64_t)y * cam.width + x;
-      const float* dimg = d_images + 3 * cam.pix_base + (int64_t)y * cam.width + x;
-      dC[k][0] = dimg[0];
-      dC[k][1] = dimg[hw];
-      dC[k][2] = dimg[2 * hw];
-      tfin[k] = tfinal[pix];
-      nc[k] = ncontrib[pix];
+      const float* dimg = args.d_images + 3 * cam.pix_base + (int64_t)y * cam.width + x;
+      px.dC[k][0] = dimg[0];
+      px.dC[k][1] = dimg[hw];
+      px.dC[k][2] = dimg[2 * hw];
+      tf = args.tfinal[pix];
+      px.nc[k] = args.ncontrib[pix];
     } else {
-      dC[k][0] = dC[k][1] = dC[k][2] = 0.0f;
-      tfin[k] = 1.0f;
-      nc[k] = 0;
+      px.dC[k][0] = px.dC[k][1] = px.dC[k][2] = 0.0f;
+      px.nc[k] = 0;
     }
-    T[k] = tfin[k];
-    bgdot[k] = tfin[k] * fmaf(bg0, dC[k][0], fmaf(bg1, dC[k][1], bg2 * dC[k][2]));
-    my_max = max(my_max, nc[k]);
+    px.T[k] = tf;
+    px.bgdot[k] = tf * fmaf(args.bg0, px.dC[k][0], fmaf(args.bg1, px.dC[k][1], args.bg2 * px.dC[k][2]));
+    my_max = max(my_max, px.nc[k]);
   }
   atomicMax(&s_maxc, my_max);
   __syncthreads();
@@ -176,117 +275,91 @@ __global__ void __launch_bounds__(TILE* TILE < 256 ? TILE* TILE : 256)
   const uint32_t len = rg.y - rg.x;
   // pairs past the last contributor of every pixel get zero gradient
   for (uint32_t j = maxc + threadIdx.x; j < len; j += NT) {
-    const uint32_t rec = (uint32_t)pairs[rg.x + j];
-    const ushort4 r = rect[rec];
-    const uint32_t slot = offrec[rec] + (uint32_t)(ty - r.y) * (uint32_t)(r.z - r.x) + (uint32_t)(tx - r.x);
-#pragma unroll
-    for (int e = 0; e < 9; ++e) pairgrad[9 * (size_t)slot + e] = 0.0f;
+    const uint32_t rec = (uint32_t)args.pairs[rg.x + j];
+    const ushort4 r = args.rect[rec];
+    const uint32_t slot = args.offrec[rec] + (uint32_t)(ty - r.y) * (uint32_t)(r.z - r.x) + (uint32_t)(tx - r.x);
+    const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    args.pairgrad[2 * (size_t)slot] = z;
+    args.pairgrad[2 * (size_t)slot + 1] = z;
+    args.pairgrad1[slot] = 0.0f;
   }
-  // batches from the back: [b0, b1) with b1 - rg.x a multiple of BATCH except the first
+  // batches from the back: [b0, b1)
   for (int64_t b1 = (int64_t)rg.x + maxc; b1 > (int64_t)rg.x; b1 -= BATCH) {
     const int64_t b0 = max((int64_t)rg.x, b1 - BATCH);
     const int n_in = (int)(b1 - b0);
     __syncthreads();
     for (int j = threadIdx.x; j < n_in; j += NT) {
-      const uint32_t rec = (uint32_t)pairs[b0 + j];
-      sA[j] = geo[2 * (size_t)rec];
-      sB[j] = geo[2 * (size_t)rec + 1];
-      sC[j] = rgbm[rec];
-      const ushort4 r = rect[rec];
-      sSlot[j] = offrec[rec] + (uint32_t)(ty - r.y) * (uint32_t)(r.z - r.x) + (uint32_t)(tx - r.x);
+      const uint32_t rec = (uint32_t)args.pairs[b0 + j];
+      sA[j] = args.geo[2 * (size_t)rec];
+      sB[j] = args.geo[2 * (size_t)rec + 1];
+      sC[j] = args.rgbm[rec];
+      const ushort4 r = args.rect[rec];
+      sSlot[j] = args.offrec[rec] + (uint32_t)(ty - r.y) * (uint32_t)(r.z - r.x) + (uint32_t)(tx - r.x);
     }
     __syncthreads();
-    for (int j = n_in - 1; j >= 0; --j) {
-      const float4 a = sA[j], b = sB[j], c = sC[j];
-      const uint32_t pos = (uint32_t)(b0 - rg.x) + j;
-      float g[9];
+    const uint32_t pos0 = (uint32_t)(b0 - rg.x);
+    for (int j = n_in - 1; j >= 0; j -= 3) {
+      float g[32];
 #pragma unroll
-      for (int e = 0; e < 9; ++e) g[e] = 0.0f;
-      bool any = false;
-#pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        if (pos >= nc[k]) continue;
-        float dx, dy;
-        const float power = gauss_power(a, b, pxc[k], pyc[k], dx, dy);
-        if (power > 0.0f || power < b.z) continue;
-        const float ex = exp32(power);
-        const float vv = b.y * ex;
-        const bool clamped = vv > kAlphaMax;
-        const float alpha = clamped ? kAlphaMax : vv;
-        if (alpha < kAlphaMin) continue;
-        any = true;
-        const float om = 1.0f - alpha;
-        const float Tk = __fdividef(T[k], om);
-        const float w = alpha * Tk;
-        g[6] = fmaf(w, dC[k][0], g[6]);
-        g[7] = fmaf(w, dC[k][1], g[7]);
-        g[8] = fmaf(w, dC[k][2], g[8]);
-        const float dot = fmaf(c.x - acc[k][0], dC[k][0], fmaf(c.y - acc[k][1], dC[k][1], (c.z - acc[k][2]) * dC[k][2]));
-        const float dalpha = Tk * dot - __fdividef(bgdot[k], om);
-        if (!clamped) {
-          const float dpow = alpha * dalpha;
-          g[0] = fmaf(dpow, fmaf(2.0f * a.z, dx, a.w * dy), g[0]);
-          g[1] = fmaf(dpow, fmaf(2.0f * b.x, dy, a.w * dx), g[1]);
-          g[2] = fmaf(dpow, -0.5f * dx * dx, g[2]);
-          g[3] = fmaf(dpow, -dx * dy, g[3]);
-          g[4] = fmaf(dpow, -0.5f * dy * dy, g[4]);
-          g[5] = fmaf(ex, dalpha, g[5]);
-        }
-        acc[k][0] = fmaf(alpha, c.x - acc[k][0], acc[k][0]);
-        acc[k][1] = fmaf(alpha, c.y - acc[k][1], acc[k][1]);
-        acc[k][2] = fmaf(alpha, c.z - acc[k][2], acc[k][2]);
-        T[k] = Tk;
-      }
-      if (__any_sync(0xffffffffu, any)) {
-#pragma unroll
-        for (int e = 0; e < 9; ++e) {
-          float x = g[e];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-          g[e] = x;
-        }
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int e = 0; e < 9; ++e) part[wid][j][e] = g[e];
+      for (int e = 0; e < 32; ++e) g[e] = 0.0f;
+      bool any = bwd_gaussian<PPT, 0>(sA[j], sB[j], sC[j], pos0 + j, pxc, px, g);
+      if (j >= 1) any |= bwd_gaussian<PPT, 1>(sA[j - 1], sB[j - 1], sC[j - 1], pos0 + j - 1, pxc, px, g);
+      if (j >= 2) any |= bwd_gaussian<PPT, 2>(sA[j - 2], sB[j - 2], sC[j - 2], pos0 + j - 2, pxc, px, g);
+      float mine = 0.0f;
+      if (__any_sync(0xffffffffu, any)) mine = warp_reduce_scatter32(g);
+      if (lane < 27) {
+        const int s = lane / 9, e = lane - 9 * s;
+        if (j - s >= 0) part[wid][j - s][e] = mine;
       }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < n_in * 9; i += NT) {
-      const int j = i / 9, e = i - 9 * j;
-      float s = 0.0f;
+    // sums over the warps, in warp order; components (0..3), (4, 6, 7, 8), 5
+    for (int i = threadIdx.x; i < n_in * 3; i += NT) {
+      const int j = i / 3, q = i - 3 * j;
+      if (q < 2) {
+        const int e0 = q == 0 ? 0 : 4, e1 = q == 0 ? 1 : 6, e2 = q == 0 ? 2 : 7, e3 = q == 0 ? 3 : 8;
+        float4 t = make_float4(part[0][j][e0], part[0][j][e1], part[0][j][e2], part[0][j][e3]);
 #pragma unroll
-      for (int w = 0; w < NW; ++w) s += part[w][j][e];
-      pairgrad[9 * (size_t)sSlot[j] + e] = s;
+        for (int w = 1; w < NW; ++w) {
+          t.x += part[w][j][e0];
+          t.y += part[w][j][e1];
+          t.z += part[w][j][e2];
+          t.w += part[w][j][e3];
+        }
+        args.pairgrad[2 * (size_t)sSlot[j] + q] = t;
+      } else {
+        float t = part[0][j][5];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) t += part[w][j][5];
+        args.pairgrad1[sSlot[j]] = t;
+      }
     }
   }
 }
 
-template <int TILE>
-static cudaError_t fwd_tile(int batch, dim3 grid, cudaStream_t s, const ViewInfo* views, int nv, const uint2* rg,
-                            const uint64_t* pairs, const float4* geo, const float4* rgbm, const float* bg,
-                            float* images, float* tfinal, uint32_t* ncontrib) {
-  constexpr int NT = TILE * TILE < 256 ? TILE * TILE : 256;
+// ---------------------------------------------------------------------------
+// dispatch
+// ---------------------------------------------------------------------------
+
+template <int TILE, int PPT>
+static cudaError_t fwd_batch(int batch, dim3 grid, cudaStream_t s, const BlendArgs& a) {
+  constexpr int NT = TileShape<TILE, PPT>::NT;
   switch (batch) {
-    case 32: count_launch(), k_blend_fwd<TILE, 32><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, bg[0], bg[1], bg[2], images, tfinal, ncontrib); break;
-    case 64: count_launch(), k_blend_fwd<TILE, 64><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, bg[0], bg[1], bg[2], images, tfinal, ncontrib); break;
-    case 128: count_launch(), k_blend_fwd<TILE, 128><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, bg[0], bg[1], bg[2], images, tfinal, ncontrib); break;
-    case 256: count_launch(), k_blend_fwd<TILE, 256><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, bg[0], bg[1], bg[2], images, tfinal, ncontrib); break;
+    case 64: count_launch(), k_blend_fwd<TILE, 64, PPT><<<grid, NT, 0, s>>>(a); break;
+    case 128: count_launch(), k_blend_fwd<TILE, 128, PPT><<<grid, NT, 0, s>>>(a); break;
+    case 256: count_launch(), k_blend_fwd<TILE, 256, PPT><<<grid, NT, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-template <int TILE>
-static cudaError_t bwd_tile(int batch, dim3 grid, cudaStream_t s, const ViewInfo* views, int nv, const uint2* rg,
-                            const uint64_t* pairs, const float4* geo, const float4* rgbm, const ushort4* rect,
-                            const uint32_t* offrec, const float* bg, const float* d_images, const float* tfinal,
-                            const uint32_t* ncontrib, float* pairgrad) {
-  constexpr int NT = TILE * TILE < 256 ? TILE * TILE : 256;
+template <int TILE, int PPT>
+static cudaError_t bwd_batch(int batch, dim3 grid, cudaStream_t s, const BlendArgs& a) {
+  constexpr int NT = TileShape<TILE, PPT>::NT;
   switch (batch) {
-    case 32: count_launch(), k_blend_bwd<TILE, 32><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, rect, offrec, bg[0], bg[1], bg[2], d_images, tfinal, ncontrib, pairgrad); break;
-    case 64: count_launch(), k_blend_bwd<TILE, 64><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, rect, offrec, bg[0], bg[1], bg[2], d_images, tfinal, ncontrib, pairgrad); break;
-    case 128: count_launch(), k_blend_bwd<TILE, 128><<<grid, NT, 0, s>>>(views, nv, rg, pairs, geo, rgbm, rect, offrec, bg[0], bg[1], bg[2], d_images, tfinal, ncontrib, pairgrad); break;
+    case 32: count_launch(), k_blend_bwd<TILE, 32, PPT><<<grid, NT, 0, s>>>(a); break;
+    case 64: count_launch(), k_blend_bwd<TILE, 64, PPT><<<grid, NT, 0, s>>>(a); break;
+    case 128: count_launch(), k_blend_bwd<TILE, 128, PPT><<<grid, NT, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -297,46 +370,63 @@ static const uint64_t* final_pairs(const Layout& L, void* ws) {
   return (passes & 1) ? ws_ptr<const uint64_t>(ws, L.pairs1) : ws_ptr<const uint64_t>(ws, L.pairs0);
 }
 
-cudaError_t launch_blend_fwd(const Layout& L, void* ws, int tile, int batch, const float bg[3], float* images,
-                             cudaStream_t s) {
-  if (L.T <= 0) return cudaSuccess;
-  const dim3 grid((unsigned)L.T);
-  const ViewInfo* views = ws_ptr<ViewInfo>(ws, L.views);
-  const uint2* rg = ws_ptr<uint2>(ws, L.ranges);
-  const float4* geo = ws_ptr<float4>(ws, L.geo);
-  const float4* rgbm = ws_ptr<float4>(ws, L.rgbm);
-  float* tf = ws_ptr<float>(ws, L.tfinal);
-  uint32_t* nc = ws_ptr<uint32_t>(ws, L.ncontrib);
-  const uint64_t* pairs = final_pairs(L, ws);
-  switch (tile) {
-    case 8: return fwd_tile<8>(batch, grid, s, views, L.n_views, rg, pairs, geo, rgbm, bg, images, tf, nc);
-    case 16: return fwd_tile<16>(batch, grid, s, views, L.n_views, rg, pairs, geo, rgbm, bg, images, tf, nc);
-    case 32: return fwd_tile<32>(batch, grid, s, views, L.n_views, rg, pairs, geo, rgbm, bg, images, tf, nc);
-    default: return cudaErrorInvalidValue;
-  }
+static BlendArgs blend_args(const Layout& L, void* ws, const float bg[3]) {
+  BlendArgs a;
+  a.views = ws_ptr<ViewInfo>(ws, L.views);
+  a.n_views = L.n_views;
+  a.ranges = ws_ptr<uint2>(ws, L.ranges);
+  a.pairs = final_pairs(L, ws);
+  a.geo = ws_ptr<float4>(ws, L.geo);
+  a.rgbm = ws_ptr<float4>(ws, L.rgbm);
+  a.rect = ws_ptr<ushort4>(ws, L.rect);
+  a.offrec = ws_ptr<uint32_t>(ws, L.offrec);
+  a.bg0 = bg[0];
+  a.bg1 = bg[1];
+  a.bg2 = bg[2];
+  a.images = nullptr;
+  a.d_images = nullptr;
+  a.tfinal = ws_ptr<float>(ws, L.tfinal);
+  a.ncontrib = ws_ptr<uint32_t>(ws, L.ncontrib);
+  a.pairgrad = ws_ptr<float4>(ws, L.pairgrad);
+  a.pairgrad1 = ws_ptr<float>(ws, L.pairgrad1);
+  return a;
 }
 
-cudaError_t launch_blend_bwd(const Layout& L, void* ws, int tile, int batch, const float bg[3],
+bool blend_ppt_ok(int tile, int ppt) {
+  if (tile == 8) return ppt == 1 || ppt == 2;
+  if (tile == 16) return ppt == 1 || ppt == 2 || ppt == 4;
+  if (tile == 32) return ppt == 4;
+  return false;
+}
+
+cudaError_t launch_blend_fwd(const Layout& L, void* ws, int tile, int batch, int ppt, const float bg[3],
+                             float* images, cudaStream_t s) {
+  if (L.T <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)L.T);
+  BlendArgs a = blend_args(L, ws, bg);
+  a.images = images;
+  if (tile == 8 && ppt == 1) return fwd_batch<8, 1>(batch, grid, s, a);
+  if (tile == 8 && ppt == 2) return fwd_batch<8, 2>(batch, grid, s, a);
+  if (tile == 16 && ppt == 1) return fwd_batch<16, 1>(batch, grid, s, a);
+  if (tile == 16 && ppt == 2) return fwd_batch<16, 2>(batch, grid, s, a);
+  if (tile == 16 && ppt == 4) return fwd_batch<16, 4>(batch, grid, s, a);
+  if (tile == 32 && ppt == 4) return fwd_batch<32, 4>(batch, grid, s, a);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_blend_bwd(const Layout& L, void* ws, int tile, int batch, int ppt, const float bg[3],
                              const float* d_images, cudaStream_t s) {
   if (L.T <= 0) return cudaSuccess;
   const dim3 grid((unsigned)L.T);
-  const ViewInfo* views = ws_ptr<ViewInfo>(ws, L.views);
-  const uint2* rg = ws_ptr<uint2>(ws, L.ranges);
-  const float4* geo = ws_ptr<float4>(ws, L.geo);
-  const float4* rgbm = ws_ptr<float4>(ws, L.rgbm);
-  const ushort4* rect = ws_ptr<ushort4>(ws, L.rect);
-  const uint32_t* offrec = ws_ptr<uint32_t>(ws, L.offrec);
-  const float* tf = ws_ptr<float>(ws, L.tfinal);
-  const uint32_t* nc = ws_ptr<uint32_t>(ws, L.ncontrib);
-  float* pg = ws_ptr<float>(ws, L.pairgrad);
-  const uint64_t* pairs = final_pairs(L, ws);
-  const int bb = batch > 128 ? 128 : batch;
-  switch (tile) {
-    case 8: return bwd_tile<8>(bb, grid, s, views, L.n_views, rg, pairs, geo, rgbm, rect, offrec, bg, d_images, tf, nc, pg);
-    case 16: return bwd_tile<16>(bb, grid, s, views, L.n_views, rg, pairs, geo, rgbm, rect, offrec, bg, d_images, tf, nc, pg);
-    case 32: return bwd_tile<32>(bb, grid, s, views, L.n_views, rg, pairs, geo, rgbm, rect, offrec, bg, d_images, tf, nc, pg);
-    default: return cudaErrorInvalidValue;
-  }
+  BlendArgs a = blend_args(L, ws, bg);
+  a.d_images = d_images;
+  if (tile == 8 && ppt == 1) return bwd_batch<8, 1>(batch, grid, s, a);
+  if (tile == 8 && ppt == 2) return bwd_batch<8, 2>(batch, grid, s, a);
+  if (tile == 16 && ppt == 1) return bwd_batch<16, 1>(batch, grid, s, a);
+  if (tile == 16 && ppt == 2) return bwd_batch<16, 2>(batch, grid, s, a);
+  if (tile == 16 && ppt == 4) return bwd_batch<16, 4>(batch, grid, s, a);
+  if (tile == 32 && ppt == 4) return bwd_batch<32, 4>(batch, grid, s, a);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace cg

@@ -56,159 +56,208 @@ __device__ __forceinline__ void sh_basis_only(float x, float y, float z, float* 
 // per-Gaussian backward
 // ---------------------------------------------------------------------------
 
+// One thread per visible (view, Gaussian) record, in depth order (the order
+// in which the record's pair slots were laid out, so neighbouring threads
+// read neighbouring slots).  Sums the record's slots in tile order and
+// applies the chain rule of the opacity, the colour (clamp mask, SH
+// direction) and the projection.  Writes the record's position, logit and
+// Sigma gradients to rg[rec][10] and its masked colour gradient to drgb.
 template <int NB>
-__global__ void __launch_bounds__(256) k_gaussian_bwd(const SceneArgs sc, const ViewInfo* __restrict__ views,
-                                                      int n_views, const float* __restrict__ sig3,
-                                                      const float4* __restrict__ geo, const float4* __restrict__ rgbm,
-                                                      const uint32_t* __restrict__ ntiles,
-                                                      const uint32_t* __restrict__ offrec,
-                                                      const float* __restrict__ pairgrad, const DeviceState* st,
-                                                      float* __restrict__ d_pos, float* __restrict__ d_logit,
-                                                      float* __restrict__ dsigma, float* __restrict__ drgb) {
-  const bool ok = st->pairs_ok != 0;
+__global__ void __launch_bounds__(256) k_record_bwd(const SceneArgs sc, const ViewInfo* __restrict__ views,
+                                                    const float* __restrict__ sig3, const float4* __restrict__ geo,
+                                                    const float4* __restrict__ rgbm,
+                                                    const uint32_t* __restrict__ ntiles,
+                                                    const uint32_t* __restrict__ offrec,
+                                                    const float4* __restrict__ pairgrad,
+                                                    const float* __restrict__ pairgrad1,
+                                                    const uint64_t* __restrict__ dsorted, const DeviceState* st,
+                                                    float* __restrict__ rg, float* __restrict__ drgb) {
+  if (st->pairs_ok == 0) return;
+  const int64_t vis = (int64_t)st->visible;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < sc.n; g += stride) {
-    float dp[3] = {0.0f, 0.0f, 0.0f}, dl = 0.0f, dsg[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vis; i += stride) {
+    const uint32_t rec = (uint32_t)dsorted[i];
+    const int v = (int)(rec / (uint32_t)sc.n);
+    const int64_t g = (int64_t)rec - (int64_t)v * sc.n;
+    const uint32_t nt = ntiles[rec];
+    // slot sums: mean x/y, conic 0/1/2, opacity, colour r/g/b
+    float gs[9] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    const uint32_t off = offrec[rec];
+    const float4* src = pairgrad + 2 * (size_t)off;
+    const float* src1 = pairgrad1 + off;
+#pragma unroll 2
+    for (uint32_t t = 0; t < nt; ++t) {
+      const float4 u = src[2 * (size_t)t], w = src[2 * (size_t)t + 1];
+      gs[0] += u.x;
+      gs[1] += u.y;
+      gs[2] += u.z;
+      gs[3] += u.w;
+      gs[4] += w.x;
+      gs[6] += w.y;
+      gs[7] += w.z;
+      gs[8] += w.w;
+      gs[5] += src1[t];
+    }
     const float p[3] = {sc.pos[3 * g], sc.pos[3 * g + 1], sc.pos[3 * g + 2]};
     const uint32_t isr = sc.g2sr[g], ish = sc.g2sh[g];
-    for (int v = 0; v < n_views; ++v) {
-      const int64_t rec = (int64_t)v * sc.n + g;
-      const uint32_t nt = ok ? ntiles[rec] : 0u;
-      if (nt == 0) {
-        drgb[3 * rec] = drgb[3 * rec + 1] = drgb[3 * rec + 2] = 0.0f;
-        continue;
-      }
-      // sum of the pair slots of this record, in tile order
-      float gs[9] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-      const float* src = pairgrad + 9 * (size_t)offrec[rec];
-      for (uint32_t i = 0; i < nt; ++i) {
+    const ViewInfo& cam = views[v];
+    const float* W = cam.w2c;
+    float dp[3] = {0.0f, 0.0f, 0.0f}, dsg[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    const float o = geo[2 * (size_t)rec + 1].y;
+    const float dl = gs[5] * (o * (1.0f - o));
+    // colour -> clamp mask -> SH direction
+    const uint32_t mask = (uint32_t)rgbm[rec].w;
+    float dc[3];
 #pragma unroll
-        for (int e = 0; e < 9; ++e) gs[e] += src[9 * (size_t)i + e];
-      }
-      const ViewInfo& cam = views[v];
-      const float* W = cam.w2c;
-      const float4 gb = geo[2 * rec + 1];
-      const float o = gb.y;
-      dl = fmaf(gs[5], o * (1.0f - o), dl);
-      // colour -> clamp mask -> SH direction
-      const uint32_t mask = (uint32_t)rgbm[rec].w;
-      float dc[3];
+    for (int c = 0; c < 3; ++c) dc[c] = (mask >> c & 1u) ? 0.0f : gs[6 + c];
+    drgb[3 * (size_t)rec] = dc[0];
+    drgb[3 * (size_t)rec + 1] = dc[1];
+    drgb[3 * (size_t)rec + 2] = dc[2];
+    const float dv[3] = {p[0] - cam.campos[0], p[1] - cam.campos[1], p[2] - cam.campos[2]};
+    const float dist = sqrtf(fmaf(dv[0], dv[0], fmaf(dv[1], dv[1], dv[2] * dv[2])));
+    const float inv = 1.0f / dist;
+    const float dir[3] = {dv[0] * inv, dv[1] * inv, dv[2] * inv};
+    float Y[kMaxBasis], Dx[kMaxBasis], Dy[kMaxBasis], Dz[kMaxBasis];
+    sh_basis_grad<NB>(dir[0], dir[1], dir[2], Y, Dx, Dy, Dz);
+    float dd[3] = {0.0f, 0.0f, 0.0f};
+    const size_t rb = (size_t)ish * NB * 3;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) dc[c] = (mask >> c & 1u) ? 0.0f : gs[6 + c];
-      drgb[3 * rec] = dc[0];
-      drgb[3 * rec + 1] = dc[1];
-      drgb[3 * rec + 2] = dc[2];
-      const float dv[3] = {p[0] - cam.campos[0], p[1] - cam.campos[1], p[2] - cam.campos[2]};
-      const float dist = sqrtf(fmaf(dv[0], dv[0], fmaf(dv[1], dv[1], dv[2] * dv[2])));
-      const float inv = 1.0f / dist;
-      const float dir[3] = {dv[0] * inv, dv[1] * inv, dv[2] * inv};
-      float Y[kMaxBasis], Dx[kMaxBasis], Dy[kMaxBasis], Dz[kMaxBasis];
-      sh_basis_grad<NB>(dir[0], dir[1], dir[2], Y, Dx, Dy, Dz);
-      float dd[3] = {0.0f, 0.0f, 0.0f};
-      const size_t rb = (size_t)ish * NB * 3;
-#pragma unroll
-      for (int k = 0; k < NB; ++k) {
-        const float dyk = fmaf(dc[0], load_row(sc.sh_rows, sc.dtype, rb + 3 * k),
-                               fmaf(dc[1], load_row(sc.sh_rows, sc.dtype, rb + 3 * k + 1),
-                                    dc[2] * load_row(sc.sh_rows, sc.dtype, rb + 3 * k + 2)));
-        dd[0] = fmaf(dyk, Dx[k], dd[0]);
-        dd[1] = fmaf(dyk, Dy[k], dd[1]);
-        dd[2] = fmaf(dyk, Dz[k], dd[2]);
-      }
-      const float ddot = fmaf(dd[0], dir[0], fmaf(dd[1], dir[1], dd[2] * dir[2]));
-#pragma unroll
-      for (int a = 0; a < 3; ++a) dp[a] = fmaf(dd[a] - dir[a] * ddot, inv, dp[a]);
-      // projection
-      float t[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) t[a] = fmaf(W[4 * a], p[0], fmaf(W[4 * a + 1], p[1], fmaf(W[4 * a + 2], p[2], W[4 * a + 3])));
-      const float iz = 1.0f / t[2];
-      const float fx = cam.fx, fy = cam.fy;
-      const float J00 = fx * iz, J02 = -fx * t[0] * iz * iz, J11 = fy * iz, J12 = -fy * t[1] * iz * iz;
-      float T[6];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        T[j] = fmaf(J00, W[j], J02 * W[8 + j]);
-        T[3 + j] = fmaf(J11, W[4 + j], J12 * W[8 + j]);
-      }
-      const float* sg = sig3 + (size_t)isr * 6;
-      const float S[9] = {sg[0], sg[1], sg[2], sg[1], sg[3], sg[4], sg[2], sg[4], sg[5]};
-      float ST0[3], ST1[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        ST0[i] = fmaf(S[3 * i], T[0], fmaf(S[3 * i + 1], T[1], S[3 * i + 2] * T[2]));
-        ST1[i] = fmaf(S[3 * i], T[3], fmaf(S[3 * i + 1], T[4], S[3 * i + 2] * T[5]));
-      }
-      const float A = fmaf(T[0], ST0[0], fmaf(T[1], ST0[1], T[2] * ST0[2])) + kDilation;
-      const float B = fmaf(T[3], ST0[0], fmaf(T[4], ST0[1], T[5] * ST0[2]));
-      const float C = fmaf(T[3], ST1[0], fmaf(T[4], ST1[1], T[5] * ST1[2])) + kDilation;
-      const float det = fmaf(A, C, -(B * B));
-      const float id2 = 1.0f / (det * det);
-      const float g0 = gs[2], g1 = gs[3], g2 = gs[4];
-      const float da = (-g0 * C * C + g1 * B * C - g2 * B * B) * id2;
-      const float db = (2.0f * g0 * B * C - g1 * (A * C + B * B) + 2.0f * g2 * A * B) * id2;
-      const float dcc = (-g0 * B * B + g1 * A * B - g2 * A * A) * id2;
-      float dT[6];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        dT[j] = fmaf(2.0f * da, ST0[j], db * ST1[j]);
-        dT[3 + j] = fmaf(db, ST0[j], 2.0f * dcc * ST1[j]);
-      }
-      const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-      for (int e = 0; e < 6; ++e) {
-        const int i = ia[e], j = ib[e];
-        float f = fmaf(da * T[i], T[j], fmaf(db * T[i], T[3 + j], dcc * T[3 + i] * T[3 + j]));
-        if (i != j) f += fmaf(da * T[j], T[i], fmaf(db * T[j], T[3 + i], dcc * T[3 + j] * T[3 + i]));
-        dsg[e] += f;
-      }
-      float dJ[6];
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-          dJ[3 * a + k] = fmaf(dT[3 * a], W[4 * k], fmaf(dT[3 * a + 1], W[4 * k + 1], dT[3 * a + 2] * W[4 * k + 2]));
-      const float gmx = gs[0], gmy = gs[1];
-      const float iz2 = iz * iz;
-      float dt[3];
-      dt[0] = fmaf(-fx * iz2, dJ[2], fx * iz * gmx);
-      dt[1] = fmaf(-fy * iz2, dJ[5], fy * iz * gmy);
-      dt[2] = -fx * iz2 * dJ[0] + 2.0f * fx * t[0] * iz2 * iz * dJ[2] - fy * iz2 * dJ[4] +
-              2.0f * fy * t[1] * iz2 * iz * dJ[5] - fx * t[0] * iz2 * gmx - fy * t[1] * iz2 * gmy;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) dp[k] += fmaf(W[k], dt[0], fmaf(W[4 + k], dt[1], W[8 + k] * dt[2]));
+    for (int k = 0; k < NB; ++k) {
+      const float dyk = fmaf(dc[0], load_row(sc.sh_rows, sc.dtype, rb + 3 * k),
+                             fmaf(dc[1], load_row(sc.sh_rows, sc.dtype, rb + 3 * k + 1),
+                                  dc[2] * load_row(sc.sh_rows, sc.dtype, rb + 3 * k + 2)));
+      dd[0] = fmaf(dyk, Dx[k], dd[0]);
+      dd[1] = fmaf(dyk, Dy[k], dd[1]);
+      dd[2] = fmaf(dyk, Dz[k], dd[2]);
     }
-    d_pos[3 * g] = dp[0];
-    d_pos[3 * g + 1] = dp[1];
-    d_pos[3 * g + 2] = dp[2];
-    d_logit[g] = dl;
+    const float ddot = fmaf(dd[0], dir[0], fmaf(dd[1], dir[1], dd[2] * dir[2]));
 #pragma unroll
-    for (int e = 0; e < 6; ++e) dsigma[6 * g + e] = dsg[e];
+    for (int a = 0; a < 3; ++a) dp[a] = fmaf(dd[a] - dir[a] * ddot, inv, dp[a]);
+    // projection
+    float t[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) t[a] = fmaf(W[4 * a], p[0], fmaf(W[4 * a + 1], p[1], fmaf(W[4 * a + 2], p[2], W[4 * a + 3])));
+    const float iz = 1.0f / t[2];
+    const float fx = cam.fx, fy = cam.fy;
+    const float J00 = fx * iz, J02 = -fx * t[0] * iz * iz, J11 = fy * iz, J12 = -fy * t[1] * iz * iz;
+    float T[6];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      T[j] = fmaf(J00, W[j], J02 * W[8 + j]);
+      T[3 + j] = fmaf(J11, W[4 + j], J12 * W[8 + j]);
+    }
+    const float* sgp = sig3 + (size_t)isr * 6;
+    const float S[9] = {sgp[0], sgp[1], sgp[2], sgp[1], sgp[3], sgp[4], sgp[2], sgp[4], sgp[5]};
+    float ST0[3], ST1[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      ST0[q] = fmaf(S[3 * q], T[0], fmaf(S[3 * q + 1], T[1], S[3 * q + 2] * T[2]));
+      ST1[q] = fmaf(S[3 * q], T[3], fmaf(S[3 * q + 1], T[4], S[3 * q + 2] * T[5]));
+    }
+    const float A = fmaf(T[0], ST0[0], fmaf(T[1], ST0[1], T[2] * ST0[2])) + kDilation;
+    const float B = fmaf(T[3], ST0[0], fmaf(T[4], ST0[1], T[5] * ST0[2]));
+    const float C = fmaf(T[3], ST1[0], fmaf(T[4], ST1[1], T[5] * ST1[2])) + kDilation;
+    const float det = fmaf(A, C, -(B * B));
+    const float id2 = 1.0f / (det * det);
+    const float g0 = gs[2], g1 = gs[3], g2 = gs[4];
+    const float da = (-g0 * C * C + g1 * B * C - g2 * B * B) * id2;
+    const float db = (2.0f * g0 * B * C - g1 * (A * C + B * B) + 2.0f * g2 * A * B) * id2;
+    const float dcc = (-g0 * B * B + g1 * A * B - g2 * A * A) * id2;
+    float dT[6];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      dT[j] = fmaf(2.0f * da, ST0[j], db * ST1[j]);
+      dT[3 + j] = fmaf(db, ST0[j], 2.0f * dcc * ST1[j]);
+    }
+    const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      const int q = ia[e], j = ib[e];
+      float f = fmaf(da * T[q], T[j], fmaf(db * T[q], T[3 + j], dcc * T[3 + q] * T[3 + j]));
+      if (q != j) f += fmaf(da * T[j], T[q], fmaf(db * T[j], T[3 + q], dcc * T[3 + j] * T[3 + q]));
+      dsg[e] = f;
+    }
+    float dJ[6];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        dJ[3 * a + k] = fmaf(dT[3 * a], W[4 * k], fmaf(dT[3 * a + 1], W[4 * k + 1], dT[3 * a + 2] * W[4 * k + 2]));
+    const float gmx = gs[0], gmy = gs[1];
+    const float iz2 = iz * iz;
+    float dt[3];
+    dt[0] = fmaf(-fx * iz2, dJ[2], fx * iz * gmx);
+    dt[1] = fmaf(-fy * iz2, dJ[5], fy * iz * gmy);
+    dt[2] = -fx * iz2 * dJ[0] + 2.0f * fx * t[0] * iz2 * iz * dJ[2] - fy * iz2 * dJ[4] +
+            2.0f * fy * t[1] * iz2 * iz * dJ[5] - fx * t[0] * iz2 * gmx - fy * t[1] * iz2 * gmy;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dp[k] += fmaf(W[k], dt[0], fmaf(W[4 + k], dt[1], W[8 + k] * dt[2]));
+    float* out = rg + 10 * (size_t)rec;
+    out[0] = dp[0];
+    out[1] = dp[1];
+    out[2] = dp[2];
+    out[3] = dl;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) out[4 + e] = dsg[e];
+  }
+}
+
+// Per Gaussian: the sum over views, in view order, of its visible records'
+// gradients; culled records contribute zero (and get a zero colour gradient).
+__global__ void __launch_bounds__(256) k_gauss_sum(int64_t n, int n_views, const uint32_t* __restrict__ ntiles,
+                                                   const float* __restrict__ rg, const DeviceState* st,
+                                                   float* __restrict__ d_pos, float* __restrict__ d_logit,
+                                                   float* __restrict__ dsigma, float* __restrict__ drgb) {
+  const bool ok = st->pairs_ok != 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += stride) {
+    float acc[10] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    for (int v = 0; v < n_views; ++v) {
+      const int64_t rec = (int64_t)v * n + g;
+      if (ok && ntiles[rec] > 0) {
+        const float* r = rg + 10 * (size_t)rec;
+#pragma unroll
+        for (int e = 0; e < 10; ++e) acc[e] += r[e];
+      } else {
+        drgb[3 * rec] = drgb[3 * rec + 1] = drgb[3 * rec + 2] = 0.0f;
+      }
+    }
+    d_pos[3 * g] = acc[0];
+    d_pos[3 * g + 1] = acc[1];
+    d_pos[3 * g + 2] = acc[2];
+    d_logit[g] = acc[3];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) dsigma[6 * g + e] = acc[4 + e];
   }
 }
 
 cudaError_t launch_gaussian_bwd(const SceneArgs& sc, const Layout& L, void* ws, float* d_pos, float* d_logit,
                                 cudaStream_t s) {
   WsHeader* hdr = ws_ptr<WsHeader>(ws, L.hdr);
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((L.n + 255) / 256, 152 * 16));
   const ViewInfo* views = ws_ptr<ViewInfo>(ws, L.views);
   const float* sig = ws_ptr<float>(ws, L.sigma3);
   const float4* geo = ws_ptr<float4>(ws, L.geo);
   const float4* rgbm = ws_ptr<float4>(ws, L.rgbm);
   const uint32_t* nt = ws_ptr<uint32_t>(ws, L.ntiles);
   const uint32_t* off = ws_ptr<uint32_t>(ws, L.offrec);
-  const float* pg = ws_ptr<float>(ws, L.pairgrad);
+  const float4* pg = ws_ptr<float4>(ws, L.pairgrad);
+  const float* pg1 = ws_ptr<float>(ws, L.pairgrad1);
+  float* rg = ws_ptr<float>(ws, L.recgrad);
   float* dsig = ws_ptr<float>(ws, L.dsigma);
   float* drgb = ws_ptr<float>(ws, L.drgb);
-#define CG_GB(NBV) count_launch(), k_gaussian_bwd<NBV><<<grid, 256, 0, s>>>(sc, views, L.n_views, sig, geo, rgbm, nt, off, pg, &hdr->st, d_pos, d_logit, dsig, drgb)
+  const uint64_t* dsorted = depth_sorted(ws, L);
+  const int grid_r = (int)std::max<int64_t>(1, std::min<int64_t>((L.R + 255) / 256, 152 * 16));
+#define CG_RB(NBV) count_launch(), k_record_bwd<NBV><<<grid_r, 256, 0, s>>>(sc, views, sig, geo, rgbm, nt, off, pg, pg1, dsorted, &hdr->st, rg, drgb)
   switch (sc.nb) {
-    case 1: CG_GB(1); break;
-    case 4: CG_GB(4); break;
-    case 9: CG_GB(9); break;
-    case 16: CG_GB(16); break;
+    case 1: CG_RB(1); break;
+    case 4: CG_RB(4); break;
+    case 9: CG_RB(9); break;
+    case 16: CG_RB(16); break;
     default: return cudaErrorInvalidValue;
   }
-#undef CG_GB
+#undef CG_RB
+  const int grid_g = (int)std::max<int64_t>(1, std::min<int64_t>((L.n + 255) / 256, 152 * 16));
+  count_launch(), k_gauss_sum<<<grid_g, 256, 0, s>>>(L.n, L.n_views, nt, rg, &hdr->st, d_pos, d_logit, dsig, drgb);
   return cudaGetLastError();
 }
 
@@ -217,15 +266,13 @@ cudaError_t launch_gaussian_bwd(const SceneArgs& sc, const Layout& L, void* ws, 
 // ---------------------------------------------------------------------------
 
 // Keys (row << 32 | g); an index >= k (already reported by the forward) is
-// keyed past the last row and counted nowhere.
+// keyed past the last row.
 __global__ void k_row_keys(const uint16_t* __restrict__ idx, int64_t n, int k, uint64_t* __restrict__ keys,
-                           uint32_t* __restrict__ counts, uint64_t* count_slot) {
+                           uint64_t* count_slot) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += stride) {
     const uint32_t r = idx[g];
-    const bool ok = r < (uint32_t)k;
-    keys[g] = ((uint64_t)(ok ? r : (uint32_t)k) << 32) | (uint64_t)g;
-    if (ok) atomicAdd(&counts[r], 1u);
+    keys[g] = ((uint64_t)(r < (uint32_t)k ? r : (uint32_t)k) << 32) | (uint64_t)g;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *count_slot = (uint64_t)n;
 }
@@ -235,29 +282,39 @@ __global__ void k_zero_counts(uint32_t* c, int64_t m) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) c[i] = 0u;
 }
 
-// chunks per row: ceil(count / kChunk)
-__global__ void k_chunk_counts(const uint32_t* __restrict__ counts, int k, uint32_t* __restrict__ nch,
-                               uint64_t* count_slot) {
+// Member ids and [start, end) of every row from the keys sorted by row
+// (rows without members keep start = end = 0).
+__global__ void k_row_bounds(const uint64_t* __restrict__ keys, int64_t n, int k, uint32_t* __restrict__ start,
+                             uint32_t* __restrict__ end, uint32_t* __restrict__ ids) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < k; r += stride)
-    nch[r] = (counts[r] + kChunk - 1) / kChunk;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *count_slot = (uint64_t)k;
-}
-
-// chunk c of row r covers member positions [off_r + c*kChunk, min(.., off_{r+1}))
-__global__ void k_fill_chunks(const uint32_t* __restrict__ row_off, const uint32_t* __restrict__ counts,
-                              const uint32_t* __restrict__ chunk_base, int k, uint4* __restrict__ chunks) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < k; r += stride) {
-    const uint32_t cnt = counts[r], base = row_off[r], cb = chunk_base[r];
-    for (uint32_t c = 0; c * kChunk < cnt; ++c)
-      chunks[cb + c] = make_uint4((uint32_t)r, base + c * kChunk, base + min(cnt, (c + 1) * kChunk), 0u);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint64_t key = keys[i];
+    const uint32_t r = (uint32_t)(key >> 32);
+    ids[i] = (uint32_t)key;
+    if (r >= (uint32_t)k) continue;
+    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != r) start[r] = (uint32_t)i;
+    if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != r) end[r] = (uint32_t)(i + 1);
   }
 }
 
-__global__ void k_ids_from_keys(const uint64_t* __restrict__ keys, int64_t n, uint32_t* __restrict__ ids) {
+// chunks per row: ceil(count / kChunk)
+__global__ void k_chunk_counts(const uint32_t* __restrict__ start, const uint32_t* __restrict__ end, int k,
+                               uint32_t* __restrict__ nch, uint64_t* count_slot) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) ids[i] = (uint32_t)keys[i];
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < k; r += stride)
+    nch[r] = (end[r] - start[r] + kChunk - 1) / kChunk;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *count_slot = (uint64_t)k;
+}
+
+// chunk c of row r covers member positions [start_r + c*kChunk, min(.., end_r))
+__global__ void k_fill_chunks(const uint32_t* __restrict__ start, const uint32_t* __restrict__ end,
+                              const uint32_t* __restrict__ chunk_base, int k, uint4* __restrict__ chunks) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < k; r += stride) {
+    const uint32_t b = start[r], e = end[r], cb = chunk_base[r];
+    for (uint32_t c = 0; b + c * kChunk < e; ++c)
+      chunks[cb + c] = make_uint4((uint32_t)r, b + c * kChunk, min(e, b + (c + 1) * kChunk), 0u);
+  }
 }
 
 // warp per chunk: SR terms are the 6 entries of dL/dSigma of each member
@@ -389,16 +446,25 @@ __device__ void sigma3_backward(const float* row, const float* g, float* drow) {
   drow[7] = 0.0f;
 }
 
-__global__ void k_sr_rows(const uint32_t* __restrict__ counts, const uint32_t* __restrict__ chunk_base, int k_sr,
-                          const float* __restrict__ part, const void* __restrict__ rows, int dtype,
-                          float* __restrict__ d_sr) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+// Warp per SR row: lanes take the row's chunks in a fixed stride, the warp
+// butterfly adds them, lane 0 pushes the sum through Eq. 2.
+__global__ void __launch_bounds__(256) k_sr_rows(const uint32_t* __restrict__ start, const uint32_t* __restrict__ end,
+                                                 const uint32_t* __restrict__ chunk_base, int k_sr,
+                                                 const float* __restrict__ part, const void* __restrict__ rows,
+                                                 int dtype, float* __restrict__ d_sr) {
+  const int lane = threadIdx.x & 31;
+  const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (r >= k_sr) return;
-  const uint32_t nch = (counts[r] + kChunk - 1) / kChunk, cb = chunk_base[r];
+  const uint32_t nch = (end[r] - start[r] + kChunk - 1) / kChunk, cb = chunk_base[r];
   float g[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-  for (uint32_t c = 0; c < nch; ++c)
+  for (uint32_t c = lane; c < nch; c += 32)
 #pragma unroll
     for (int e = 0; e < 6; ++e) g[e] += part[6 * (size_t)(cb + c) + e];
+#pragma unroll
+  for (int e = 0; e < 6; ++e)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) g[e] += __shfl_xor_sync(0xffffffffu, g[e], o);
+  if (lane != 0) return;
   float row[8];
 #pragma unroll
   for (int i = 0; i < 7; ++i) row[i] = load_row(rows, dtype, (size_t)r * CG_SR_WIDTH + i);
@@ -409,69 +475,70 @@ __global__ void k_sr_rows(const uint32_t* __restrict__ counts, const uint32_t* _
   for (int i = 0; i < 8; ++i) d_sr[(size_t)r * 8 + i] = drow[i];
 }
 
-__global__ void k_sh_rows(const uint32_t* __restrict__ counts, const uint32_t* __restrict__ chunk_base, int k_sh,
-                          int width, const float* __restrict__ part, float* __restrict__ d_sh) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)k_sh * width) return;
-  const int r = (int)(i / width), e = (int)(i - (int64_t)r * width);
-  const uint32_t nch = (counts[r] + kChunk - 1) / kChunk, cb = chunk_base[r];
-  float s = 0.0f;
-  for (uint32_t c = 0; c < nch; ++c) s += part[(size_t)width * (cb + c) + e];
-  d_sh[i] = s;
+// Warp per SH row: lane e sums component e over the row's chunks in order.
+__global__ void __launch_bounds__(256) k_sh_rows(const uint32_t* __restrict__ start, const uint32_t* __restrict__ end,
+                                                 const uint32_t* __restrict__ chunk_base, int k_sh, int width,
+                                                 const float* __restrict__ part, float* __restrict__ d_sh) {
+  const int lane = threadIdx.x & 31;
+  const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (r >= k_sh) return;
+  const uint32_t nch = (end[r] - start[r] + kChunk - 1) / kChunk, cb = chunk_base[r];
+  for (int e = lane; e < width; e += 32) {
+    float s = 0.0f;
+#pragma unroll 4
+    for (uint32_t c = 0; c < nch; ++c) s += part[(size_t)width * (cb + c) + e];
+    d_sh[(size_t)r * width + e] = s;
+  }
 }
 
-// CSR of one index array; returns member ids (sorted by row, then Gaussian),
-// counts, row offsets, chunk bases and chunk table (chunk count in *nch_dev).
-static cudaError_t build_csr(void* ws, const Layout& L, const uint16_t* idx, int k, uint32_t* row_off,
-                             uint32_t* ids, uint32_t* counts, uint32_t* chunk_base, uint4* chunks, uint64_t* slot_a,
-                             uint64_t* slot_b, cudaStream_t s) {
+// CSR of one index array: member ids (by row, then Gaussian), row bounds,
+// chunk bases and the chunk table (chunk count in *chunks_dev).
+static cudaError_t build_csr(void* ws, const Layout& L, const uint16_t* idx, int k, uint32_t* csr, uint32_t* ids,
+                             uint4* chunks, DeviceState* st, cudaStream_t s) {
   const int64_t n = L.n;
-  uint64_t* k0 = ws_ptr<uint64_t>(ws, L.dkeys0);
-  uint64_t* k1 = ws_ptr<uint64_t>(ws, L.dkeys1);
+  uint32_t* start = csr;
+  uint32_t* end = csr + k;
+  uint32_t* cbase = csr + 2 * (int64_t)k;
+  uint64_t* k0 = ws_ptr<uint64_t>(ws, L.csr_keys0);
+  uint64_t* k1 = ws_ptr<uint64_t>(ws, L.csr_keys1);
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
-  const int gk = std::max(1, std::min((k + 255) / 256, 152 * 8));
-  count_launch(), k_zero_counts<<<gk, 256, 0, s>>>(counts, k);
-  count_launch(), k_row_keys<<<g, 256, 0, s>>>(idx, n, k, k0, counts, slot_a);
+  const int gk = std::max(1, std::min((2 * k + 255) / 256, 152 * 8));
+  count_launch(), k_zero_counts<<<gk, 256, 0, s>>>(start, 2 * (int64_t)k);
+  count_launch(), k_row_keys<<<g, 256, 0, s>>>(idx, n, k, k0, &st->red_a);
   bool in_b = false;
-  cudaError_t e = sort_u64(ws, L, k0, k1, slot_a, n, 32, k >= 65536 ? 3 : 2, &in_b, s);
+  cudaError_t e = sort_u64(ws, L, k0, k1, &st->red_a, n, 32, k >= 65536 ? 3 : 2, &in_b, s);
   if (e != cudaSuccess) return e;
-  count_launch(), k_ids_from_keys<<<g, 256, 0, s>>>(in_b ? k1 : k0, n, ids);
-  count_launch(), k_chunk_counts<<<gk, 256, 0, s>>>(counts, k, chunk_base, slot_b);
-  e = scan_u32(ws, L, counts, row_off, slot_b, k, slot_a, s);  // slot_a <- n (total)
+  count_launch(), k_row_bounds<<<g, 256, 0, s>>>(in_b ? k1 : k0, n, k, start, end, ids);
+  count_launch(), k_chunk_counts<<<gk, 256, 0, s>>>(start, end, k, cbase, &st->red_b);
+  e = scan_u32(ws, L, cbase, cbase, &st->red_b, k, &st->red_a, s);  // red_a <- chunk count
   if (e != cudaSuccess) return e;
-  e = scan_u32(ws, L, chunk_base, chunk_base, slot_b, k, slot_a, s);  // slot_a <- chunk count
-  if (e != cudaSuccess) return e;
-  count_launch(), k_fill_chunks<<<gk, 256, 0, s>>>(row_off, counts, chunk_base, k, chunks);
+  count_launch(), k_fill_chunks<<<gk, 256, 0, s>>>(start, end, cbase, k, chunks);
   return cudaGetLastError();
 }
 
 cudaError_t launch_codebook_reduce(const SceneArgs& sc, const Layout& L, void* ws, float* d_sr, float* d_sh,
                                    cudaStream_t s) {
   WsHeader* hdr = ws_ptr<WsHeader>(ws, L.hdr);
-  uint64_t* slot_a = &hdr->st.scan_total;
-  uint64_t* slot_b = &hdr->st.visible;  // scratch here; rewritten by the next forward
+  DeviceState* st = &hdr->st;
   uint4* chunks = ws_ptr<uint4>(ws, L.chunks);
   float* part = ws_ptr<float>(ws, L.partials);
-  uint32_t* cnt = ws_ptr<uint32_t>(ws, L.csr_off_sr) + (L.k_sr + 1);  // counts after offsets
-  uint32_t* cbase = cnt + L.k_sr;
-  // SR rows
-  cudaError_t e = build_csr(ws, L, sc.g2sr, sc.k_sr, ws_ptr<uint32_t>(ws, L.csr_off_sr),
-                            ws_ptr<uint32_t>(ws, L.csr_ids_sr), cnt, cbase, chunks, slot_a, slot_b, s);
-  if (e != cudaSuccess) return e;
   const int gw = 152 * 8;
-  count_launch(), k_sr_partials<<<gw, 256, 0, s>>>(chunks, slot_a, ws_ptr<uint32_t>(ws, L.csr_ids_sr), ws_ptr<float>(ws, L.dsigma),
-                                  part);
-  count_launch(), k_sr_rows<<<(sc.k_sr + 127) / 128, 128, 0, s>>>(cnt, cbase, sc.k_sr, part, sc.sr_rows, sc.dtype, d_sr);
+  // SR rows
+  uint32_t* csr_sr = ws_ptr<uint32_t>(ws, L.csr_off_sr);
+  cudaError_t e = build_csr(ws, L, sc.g2sr, sc.k_sr, csr_sr, ws_ptr<uint32_t>(ws, L.csr_ids_sr), chunks, st, s);
+  if (e != cudaSuccess) return e;
+  count_launch(), k_sr_partials<<<gw, 256, 0, s>>>(chunks, &st->red_a, ws_ptr<uint32_t>(ws, L.csr_ids_sr),
+                                                   ws_ptr<float>(ws, L.dsigma), part);
+  count_launch(), k_sr_rows<<<(sc.k_sr + 7) / 8, 256, 0, s>>>(csr_sr, csr_sr + sc.k_sr, csr_sr + 2 * (int64_t)sc.k_sr,
+                                                              sc.k_sr, part, sc.sr_rows, sc.dtype, d_sr);
   // SH rows
-  uint32_t* cnt2 = ws_ptr<uint32_t>(ws, L.csr_off_sh) + (L.k_sh + 1);
-  uint32_t* cbase2 = cnt2 + L.k_sh;
-  e = build_csr(ws, L, sc.g2sh, sc.k_sh, ws_ptr<uint32_t>(ws, L.csr_off_sh), ws_ptr<uint32_t>(ws, L.csr_ids_sh), cnt2,
-                cbase2, chunks, slot_a, slot_b, s);
+  uint32_t* csr_sh = ws_ptr<uint32_t>(ws, L.csr_off_sh);
+  e = build_csr(ws, L, sc.g2sh, sc.k_sh, csr_sh, ws_ptr<uint32_t>(ws, L.csr_ids_sh), chunks, st, s);
   if (e != cudaSuccess) return e;
   const ViewInfo* views = ws_ptr<ViewInfo>(ws, L.views);
   const uint32_t* ids = ws_ptr<uint32_t>(ws, L.csr_ids_sh);
   const float* drgb = ws_ptr<float>(ws, L.drgb);
-#define CG_SHP(NBV) count_launch(), k_sh_partials<NBV><<<gw, 256, 0, s>>>(chunks, slot_a, ids, sc.pos, views, L.n_views, L.n, drgb, part)
+#define CG_SHP(NBV) count_launch(), k_sh_partials<NBV><<<gw, 256, 0, s>>>(chunks, &st->red_a, ids, sc.pos, views, L.n_views, L.n, drgb, part)
   switch (sc.nb) {
     case 1: CG_SHP(1); break;
     case 4: CG_SHP(4); break;
@@ -481,8 +548,8 @@ cudaError_t launch_codebook_reduce(const SceneArgs& sc, const Layout& L, void* w
   }
 #undef CG_SHP
   const int width = sc.nb * 3;
-  const int64_t tot = (int64_t)sc.k_sh * width;
-  count_launch(), k_sh_rows<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(cnt2, cbase2, sc.k_sh, width, part, d_sh);
+  count_launch(), k_sh_rows<<<(sc.k_sh + 7) / 8, 256, 0, s>>>(csr_sh, csr_sh + sc.k_sh, csr_sh + 2 * (int64_t)sc.k_sh,
+                                                              sc.k_sh, width, part, d_sh);
   return cudaGetLastError();
 }
 

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(1024) k_sort_scan_rows(uint32_t* __restrict__ 
   if (threadIdx.x == 0) digit_tot[blockIdx.x] = carry;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_downsweep(const uint64_t* __restrict__ in,
+__global__ void __launch_bounds__(kSortThreads, 3) k_sort_downsweep(const uint64_t* __restrict__ in,
                                                                  uint64_t* __restrict__ out,
                                                                  const uint64_t* count_dev, int64_t count_cap,
                                                                  int shift, const uint32_t* __restrict__ hist,
@@ -340,27 +340,49 @@ __global__ void k_capacity(DeviceState* st, int64_t cap) {
 }
 
 // Pairs of one record: (global tile << 32) | record, tiles of its rectangle
-// in row-major order starting at its offset.
-__global__ void k_emit_pairs(const uint64_t* __restrict__ dkeys, const uint32_t* __restrict__ off_sorted,
-                             const ushort4* __restrict__ rect, const ViewInfo* __restrict__ views, int64_t n,
-                             uint32_t* __restrict__ offrec, uint64_t* __restrict__ pairs,
-                             const DeviceState* st) {
+// in row-major order starting at its offset.  A warp takes 32 consecutive
+// records (depth order) and writes their pairs one record at a time with all
+// lanes, so the stores of a record are contiguous.
+__global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__ dkeys,
+                                                    const uint32_t* __restrict__ off_sorted,
+                                                    const ushort4* __restrict__ rect,
+                                                    const ViewInfo* __restrict__ views, int64_t n,
+                                                    uint32_t* __restrict__ offrec, uint64_t* __restrict__ pairs,
+                                                    const DeviceState* st) {
   const int64_t vis = (int64_t)st->visible;
   const bool ok = st->pairs_ok != 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vis; i += stride) {
-    const uint32_t rec = (uint32_t)dkeys[i];
-    const uint32_t off = off_sorted[i];
-    offrec[rec] = off;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = warp * 32; base < vis; base += nwarps * 32) {
+    const int64_t i = base + lane;
+    uint32_t rec = 0, off = 0, r01 = 0, r23 = 0;
+    if (i < vis) {
+      rec = (uint32_t)dkeys[i];
+      off = off_sorted[i];
+      offrec[rec] = off;
+      const ushort4 r = rect[rec];
+      r01 = (uint32_t)r.x | ((uint32_t)r.y << 16);
+      r23 = (uint32_t)r.z | ((uint32_t)r.w << 16);
+    }
     if (!ok) continue;
-    const ushort4 r = rect[rec];
-    const int v = (int)(rec / (uint64_t)n);
-    const int64_t tb = views[v].tile_base;
-    const int tx = views[v].tiles_x;
-    uint32_t k = off;
-    for (int y = r.y; y < r.w; ++y)
-      for (int x = r.x; x < r.z; ++x)
-        pairs[k++] = ((uint64_t)(tb + (int64_t)y * tx + x) << 32) | rec;
+    const int cnt = (int)min((int64_t)32, vis - base);
+    for (int q = 0; q < cnt; ++q) {
+      const uint32_t qrec = __shfl_sync(0xffffffffu, rec, q);
+      const uint32_t qoff = __shfl_sync(0xffffffffu, off, q);
+      const uint32_t q01 = __shfl_sync(0xffffffffu, r01, q);
+      const uint32_t q23 = __shfl_sync(0xffffffffu, r23, q);
+      const int x0 = (int)(q01 & 0xffffu), y0 = (int)(q01 >> 16);
+      const int w = (int)(q23 & 0xffffu) - x0, h = (int)(q23 >> 16) - y0;
+      const ViewInfo& cam = views[qrec / (uint64_t)n];
+      const int64_t tb = cam.tile_base;
+      const int tx = cam.tiles_x;
+      const int total = w * h;
+      for (int t = lane; t < total; t += 32) {
+        const int yy = t / w, xx = t - yy * w;
+        pairs[qoff + t] = ((uint64_t)(tb + (int64_t)(y0 + yy) * tx + (x0 + xx)) << 32) | qrec;
+      }
+    }
   }
 }
 
@@ -399,6 +421,7 @@ cudaError_t launch_build_pairs(const Layout& L, void* ws, int tile_bits, cudaStr
   e = sort_u64(ws, L, dk0, dk1, &st->visible, R, 32, 4, &in_b, s);
   if (e != cudaSuccess) return e;
   const uint64_t* dsorted = in_b ? dk1 : dk0;
+  if (dsorted != depth_sorted(ws, L)) return cudaErrorInvalidValue;
   // 3. pair offsets in depth order, total pair count and capacity check
   count_launch(), k_gather_ntiles<<<g, 256, 0, s>>>(dsorted, ntiles, scan, &st->visible);
   e = scan_u32(ws, L, scan, scan, &st->visible, R, &st->scan_total, s);

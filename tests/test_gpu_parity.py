@@ -21,8 +21,9 @@ GRAD_RTOL = 1e-3
 GRAD_AFLOOR = 1e-6
 
 
-def _run_gpu(scene, cams, d_image, tile=16, batch=0, bg=(0.0, 0.0, 0.0), bf16=False, pair_capacity=1 << 16):
-    r = cg.Renderer(cams, tile=tile, batch=batch, bg=bg, pair_capacity=pair_capacity)
+def _run_gpu(scene, cams, d_image, tile=16, batch=0, bg=(0.0, 0.0, 0.0), bf16=False, pair_capacity=1 << 16,
+             **shape):
+    r = cg.Renderer(cams, tile=tile, batch=batch, bg=bg, pair_capacity=pair_capacity, **shape)
     st = cg.SceneTensors.from_scene(scene, codebook_dtype=torch.bfloat16 if bf16 else torch.float32)
     img = r.forward(st)
     d_pos, d_logit = r.backward(torch.from_numpy(d_image.astype(np.float32)).cuda())
@@ -100,7 +101,7 @@ def _compare(ref, gpu, check_grads=True):
         _assert_grad("d_sh", gpu["d_sh"], g["d_sh"])
 
 
-def _case(scene, cams, tile=16, bg=(0.0, 0.0, 0.0), bf16=False, target=None, batch=0):
+def _case(scene, cams, tile=16, bg=(0.0, 0.0, 0.0), bf16=False, target=None, batch=0, **shape):
     oscene = _oracle_scene(scene, bf16)
     ref = oracle.Render(oscene, cams, tile=tile, bg=bg)
     if target is None:
@@ -109,7 +110,7 @@ def _case(scene, cams, tile=16, bg=(0.0, 0.0, 0.0), bf16=False, target=None, bat
         tref = oracle.Render(_oracle_scene(target, bf16), cams, tile=tile, bg=bg)
         d_image = _l1_grad(ref, tref.image)
     ref.grads = ref.backward(d_image)
-    gpu = _run_gpu(scene, cams, d_image, tile=tile, bg=bg, bf16=bf16, batch=batch)
+    gpu = _run_gpu(scene, cams, d_image, tile=tile, bg=bg, bf16=bf16, batch=batch, **shape)
     return ref, gpu
 
 
@@ -127,10 +128,15 @@ def test_tile_sizes_and_background(tile):
     _compare(ref, gpu)
 
 
-@pytest.mark.parametrize("batch", [32, 64, 128, 256])
-def test_batch_sizes(batch):
+@pytest.mark.parametrize("tile,batch,batch_bwd,ppt_fwd,ppt_bwd", [
+    (16, 64, 32, 1, 1), (16, 128, 64, 2, 2), (16, 256, 128, 4, 4), (16, 256, 64, 1, 2),
+    (8, 64, 32, 2, 2), (8, 128, 128, 1, 1), (32, 64, 32, 4, 4)])
+def test_launch_shapes(tile, batch, batch_bwd, ppt_fwd, ppt_bwd):
+    """Batch sizes and pixels per thread change speed only: same bits for the
+    discrete outputs, same tolerances for the rest."""
     scene, cams, _ = scenes.config_tiny()
-    ref, gpu = _case(scene, cams, batch=batch)
+    cams = [scenes.look_at(cams[0].campos, 150, 97)]
+    ref, gpu = _case(scene, cams, tile=tile, batch=batch, batch_bwd=batch_bwd, ppt_fwd=ppt_fwd, ppt_bwd=ppt_bwd)
     _compare(ref, gpu)
 
 
