@@ -57,6 +57,9 @@ typedef enum { CG_F32 = 0, CG_BF16 = 1 } cg_dtype;
 #define CG_MAX_VIEWS 64
 #define CG_SR_WIDTH 8
 
+/* Size limits: n * n_views < 2^26 records, fewer than 2^17 tiles per view
+ * and 2^21 tiles over all views (the layout of the sorted pair keys). */
+
 /* Pinhole camera, OpenCV axes (x right, y down, z forward).  A point p maps
  * to t = R p + t_w with world_to_cam = [R | t_w] (row-major 3x4) and to the
  * pixel (fx t_x / t_z + cx, fy t_y / t_z + cy); pixel (x, y) has its centre
@@ -116,8 +119,9 @@ typedef struct {
 size_t cg_workspace_bytes(const cg_scene *scene, const cg_camera *cams, int n_views, const cg_opts *opts);
 
 /* Forward render I_P(G, C) of every view (Eqs. 1-3, Sec. 3.1 indirection):
- * codebook gather, Eq. 2, EWA projection, SH colour, tile/depth keys, radix
- * sort, per-tile front-to-back compositing.
+ * codebook gather, Eq. 2, EWA projection, SH colour, tile/depth keys (a
+ * Gaussian is listed in the tiles of its 3-sigma rectangle where alpha can
+ * reach 1/255), radix sort, per-tile front-to-back compositing.
  *   cams      host array of n_views cameras (1 <= n_views <= CG_MAX_VIEWS)
  *   images    device float, views packed one after the other, each [3][H][W]
  * The workspace keeps what the backward needs (per-Gaussian records, sorted
@@ -179,7 +183,8 @@ cg_status cg_l1_loss_static(const float *image, const float *target, int64_t cou
  * and element count written to the host outputs).  Layouts:
  *   CG_WS_RECT        [V*n] uint16x4  tile rectangle x0, y0, x1, y1 (x1 == x0 when culled)
  *   CG_WS_DEPTH       [V*n] uint32    IEEE bits of the FP32 camera depth
- *   CG_WS_PAIRS       [K]   uint64    sorted (global tile << 32) | (v*n + g)
+ *   CG_WS_PAIRS       [K]   uint64    sorted (global tile << 43) | (rank << 26) | (v*n + g),
+ *                                     rank = index among the record's listed tiles
  *   CG_WS_RANGES      [T]   uint32x2  [start, end) of each global tile in the pairs
  *   CG_WS_NCONTRIB    [P]   uint32    position after the last contributor, per pixel
  *   CG_WS_TFINAL      [P]   float     final transmittance per pixel
@@ -199,10 +204,15 @@ cg_status cg_workspace_array(void *workspace, size_t ws_bytes, cg_ws_array which
  * source as the kernels, so it can be checked without a GPU:
  *   cg_host_exp32       the binary32 exp of the decision arithmetic
  *   cg_host_sh_consts   the 16 SH basis constants (with signs) in FP32
- *   cg_host_sigma3      Eq. 2 of one SR row (8 floats) -> 6 floats */
+ *   cg_host_sigma3      Eq. 2 of one SR row (8 floats) -> 6 floats
+ *   cg_host_tile_keep   the tile test that decides whether a Gaussian is
+ *                       listed in a tile of its 3-sigma rectangle: geo =
+ *                       mean x, mean y, -c0/2, -c1, -c2/2, opacity; 1 when
+ *                       alpha >= 1/255 is reachable at a pixel of the tile */
 float cg_host_exp32(float x);
 void cg_host_sh_consts(float out[16]);
 void cg_host_sigma3(const float row[8], float out[6]);
+int cg_host_tile_keep(const float geo[6], int tx, int ty, int tile);
 
 /* Stage timing for benchmarks.  While enabled, the library records a pair
  * of CUDA events on the caller's stream around every launch of each stage

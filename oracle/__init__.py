@@ -88,10 +88,12 @@ def lib():
             L.or_sr_sigma_backward.argtypes = [_P, _P, _P]
             L.or_shadow32.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P]
             L.or_preprocess64.argtypes = [_P, _P, ctypes.c_int, _P, _P]
-            L.or_count_pairs.argtypes = [_P, ctypes.c_int64]
+            L.or_count_pairs.argtypes = [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_int]
             L.or_count_pairs.restype = ctypes.c_int64
             L.or_build_lists.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int64,
-                                         ctypes.c_int64, _P, _P, _P]
+                                         ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P, _P, _P]
+            L.or_tile_keep32.argtypes = [ctypes.c_float] * 6 + [ctypes.c_int] * 3
+            L.or_tile_keep32.restype = ctypes.c_int
             L.or_blend_forward.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P,
                                            _P, _P, _P, _P, _P]
             L.or_blend_backward.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P,
@@ -126,6 +128,11 @@ def sh_basis(degree: int, direction) -> tuple[np.ndarray, np.ndarray]:
     lib().or_sh_basis(degree, _ptr(d), _ptr(Y), _ptr(dY))
     nb = (degree + 1) ** 2
     return Y[:nb], dY[:nb]
+
+
+def tile_keep32(mx, my, h0, h1, h2, o, tx, ty, tile) -> bool:
+    """The FP32 tile test of the lists."""
+    return bool(lib().or_tile_keep32(mx, my, h0, h1, h2, o, tx, ty, tile))
 
 
 def sh_consts32() -> np.ndarray:
@@ -211,10 +218,14 @@ class Render:
     termination below transmittance 1e-4, decided in FP32); mode 1: Eq. 3 as
     printed.  ``tile_mask`` (uint8 per global tile) restricts the per-pixel
     work to a subset of tiles (for sampled checks of large workloads).
+    ``cull`` lists a record only in the tiles of its rectangle that pass the
+    FP32 tile test (or_tile_keep32); without it, in every tile of it.  The
+    default culls under the rasterizer rules (mode 0) and not for Eq. 3 as
+    printed (mode 1), where every listed Gaussian contributes.
     """
 
     def __init__(self, scene, cams, tile: int = 16, bg=(0.0, 0.0, 0.0), mode: int = 0,
-                 tile_mask: np.ndarray | None = None):
+                 tile_mask: np.ndarray | None = None, cull: bool | None = None):
         if len(cams) > 64:
             raise ValueError("the oracle handles at most 64 views")
         L = lib()
@@ -245,14 +256,16 @@ class Render:
         L.or_shadow32(ctypes.byref(self.sb.s), self._c, self.V, self.tile, _ptr(self.rec32))
         t1 = time.perf_counter()
         self.timing["shadow"] = t1 - t0
-        self.k_pairs = int(L.or_count_pairs(_ptr(self.rec32), self.V * n))
+        self.cull = (self.mode == 0) if cull is None else bool(cull)
+        self.k_pairs = int(L.or_count_pairs(_ptr(self.rec32), self.V * n, self.tile, int(self.cull)))
         if self.k_pairs >= 2 ** 32:
             raise ValueError("pair count exceeds 32-bit indexing")
         self.list = np.zeros(max(self.k_pairs, 1), dtype=np.uint32)
         self.keys = np.zeros(max(self.k_pairs, 1), dtype=np.uint64)
         self.ranges = np.zeros((self.n_tiles, 2), dtype=np.uint32)
         L.or_build_lists(_ptr(self.rec32), n, self.V, _ptr(self.tiles_x), _ptr(self.tile_base),
-                         self.n_tiles, self.k_pairs, _ptr(self.list), _ptr(self.keys), _ptr(self.ranges))
+                         self.n_tiles, self.k_pairs, self.tile, int(self.cull), _ptr(self.list), _ptr(self.keys),
+                         _ptr(self.ranges))
         self.list = self.list[:self.k_pairs]
         self.keys = self.keys[:self.k_pairs]
         t2 = time.perf_counter()

@@ -483,8 +483,50 @@ void or_preprocess64(const or_scene *s, const or_camera *cams, int n_views, cons
 
 /* ------------------------------------------------------------------------ */
 /* Tile lists: every visible (view, Gaussian) record is listed in each tile  */
-/* of its rectangle; a tile's list is ordered by FP32 depth, ties by record. */
+/* of its rectangle (that passes the tile test); a tile's list is ordered by */
+/* FP32 depth, ties by record.                                               */
 /* ------------------------------------------------------------------------ */
+
+/* Whether a Gaussian can reach alpha >= 1/255 at some pixel centre of tile
+ * (tx, ty), decided in FP32.  The exponent h0 dx^2 + h1 dx dy + h2 dy^2 is
+ * concave with maximum 0 at the mean; over the box of the tile's pixel
+ * centres its maximum is 0 when the mean is inside, otherwise it lies on one
+ * of the (at most two) edges that face the mean, at the stationary point of
+ * the edge clamped to the edge (with the reciprocals 1/(2 h0), 1/(2 h2)
+ * rounded once).  Kept when o * exp(pmax + 0.01) >= 1/255
+ * (0.01 absorbs the rounding of pmax, so a dropped tile is one where every
+ * pixel skips the Gaussian). */
+int or_tile_keep32(float mx, float my, float h0, float h1, float h2, float o, int tx, int ty, int tile) {
+  const float xl = (float)(tx * tile) + 0.5f, xh = (float)(tx * tile + tile - 1) + 0.5f;
+  const float yl = (float)(ty * tile) + 0.5f, yh = (float)(ty * tile + tile - 1) + 0.5f;
+  const int xin = mx >= xl && mx <= xh, yin = my >= yl && my <= yh;
+  if (xin && yin) return o * or_e32(0.0f + 0.01f) >= 1.0f / 255.0f;
+  const float inv2h0 = 1.0f / (2.0f * h0), inv2h2 = 1.0f / (2.0f * h2);
+  float best = -3.0e38f;
+  if (!xin) {
+    const float ex = mx < xl ? xl : xh;
+    const float dx = mx - ex;
+    const float stat = -(h1 * dx) * inv2h2;  /* d/d(dy) = h1 dx + 2 h2 dy = 0 */
+    const float lo = my - yh, hi = my - yl;
+    const float dy = stat < lo ? lo : (stat > hi ? hi : stat);
+    const float v = fmaf(h0 * dx, dx, fmaf(h2 * dy, dy, (h1 * dx) * dy));
+    if (v > best) best = v;
+  }
+  if (!yin) {
+    const float ey = my < yl ? yl : yh;
+    const float dy = my - ey;
+    const float stat = -(h1 * dy) * inv2h0;
+    const float lo = mx - xh, hi = mx - xl;
+    const float dx = stat < lo ? lo : (stat > hi ? hi : stat);
+    const float v = fmaf(h0 * dx, dx, fmaf(h2 * dy, dy, (h1 * dx) * dy));
+    if (v > best) best = v;
+  }
+  return o * or_e32(best + 0.01f) >= 1.0f / 255.0f;
+}
+
+static int keep_tile(const or_rec32 *r, int tx, int ty, int tile, int cull) {
+  return !cull || or_tile_keep32(r->mx, r->my, r->h0, r->h1, r->h2, r->o, tx, ty, tile);
+}
 
 typedef struct { uint64_t key; uint32_t rec; } or_pair;
 
@@ -494,11 +536,16 @@ static int pair_cmp(const void *a, const void *b) {
   return p->rec < q->rec ? -1 : (p->rec > q->rec);
 }
 
-/* Count of (tile, record) pairs. */
-int64_t or_count_pairs(const or_rec32 *rec32, int64_t n_rec) {
+/* Count of listed (tile, record) pairs: tiles of each visible record's
+ * rectangle, with cull != 0 only those that pass or_tile_keep32. */
+int64_t or_count_pairs(const or_rec32 *rec32, int64_t n_rec, int tile, int cull) {
   int64_t k = 0;
-  for (int64_t i = 0; i < n_rec; ++i)
-    if (rec32[i].visible) k += (int64_t)(rec32[i].x1 - rec32[i].x0) * (rec32[i].y1 - rec32[i].y0);
+  for (int64_t i = 0; i < n_rec; ++i) {
+    const or_rec32 *r = &rec32[i];
+    if (!r->visible) continue;
+    for (int y = r->y0; y < r->y1; ++y)
+      for (int x = r->x0; x < r->x1; ++x) k += keep_tile(r, x, y, tile, cull);
+  }
   return k;
 }
 
@@ -506,7 +553,8 @@ int64_t or_count_pairs(const or_rec32 *rec32, int64_t n_rec) {
  * Writes list[k_pairs] (record indices v*n+g), keys[k_pairs] and
  * ranges[n_tiles][2]. */
 void or_build_lists(const or_rec32 *rec32, int n, int n_views, const int *tiles_x, const int64_t *tile_base,
-                    int64_t n_tiles, int64_t k_pairs, uint32_t *list, uint64_t *keys, uint32_t *ranges) {
+                    int64_t n_tiles, int64_t k_pairs, int tile, int cull, uint32_t *list, uint64_t *keys,
+                    uint32_t *ranges) {
   or_pair *pairs = (or_pair *)malloc(sizeof(or_pair) * (size_t)(k_pairs > 0 ? k_pairs : 1));
   int64_t k = 0;
   for (int v = 0; v < n_views; ++v)
@@ -515,6 +563,7 @@ void or_build_lists(const or_rec32 *rec32, int n, int n_views, const int *tiles_
       if (!r->visible) continue;
       for (int y = r->y0; y < r->y1; ++y)
         for (int x = r->x0; x < r->x1; ++x) {
+          if (!keep_tile(r, x, y, tile, cull)) continue;
           const uint64_t gt = (uint64_t)(tile_base[v] + (int64_t)y * tiles_x[v] + x);
           pairs[k].key = (gt << 32) | r->depth_bits;
           pairs[k].rec = (uint32_t)((size_t)v * n + g);

@@ -30,7 +30,7 @@ WS_RECT, WS_DEPTH, WS_PAIRS, WS_RANGES, WS_NCONTRIB, WS_TFINAL, WS_DSIGMA, WS_DR
 # every symbol include/cg.h declares
 EXPORTS = ["cg_workspace_bytes", "cg_render_fwd", "cg_render_bwd", "cg_codebook_reduce", "cg_last_device_status",
            "cg_l1_loss", "cg_workspace_array", "cg_host_exp32", "cg_host_sh_consts", "cg_host_sigma3",
-           "cg_timing_enable", "cg_timing_read", "cg_launch_count", "cg_version", "cg_l1_loss_static"]
+           "cg_host_tile_keep", "cg_timing_enable", "cg_timing_read", "cg_launch_count", "cg_version", "cg_l1_loss_static"]
 STAGES = ["preprocess", "sort", "blend_fwd", "blend_bwd", "gauss_bwd", "reduce"]
 
 
@@ -87,6 +87,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         L.cg_host_exp32.restype = ctypes.c_float
         L.cg_host_sh_consts.argtypes = [P]
         L.cg_host_sigma3.argtypes = [P, P]
+        L.cg_host_tile_keep.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.cg_host_tile_keep.restype = ctypes.c_int
         L.cg_version.restype = ctypes.c_char_p
         L.cg_timing_enable.argtypes = [ctypes.c_int]
         L.cg_timing_enable.restype = ctypes.c_int

@@ -103,7 +103,11 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
     T += (int64_t)vi.tiles_x * vi.tiles_y;
     P += (int64_t)c.width * c.height;
   }
-  if (T >= (int64_t(1) << 31)) return CG_ERR_ARG;
+  // key layout (pair_key): records < 2^26, tiles per view < 2^17, tiles < 2^21
+  if (R > (int64_t)kKeyRecMask + 1) return CG_ERR_ARG;
+  for (int v = 0; v < n_views; ++v)
+    if ((int64_t)table->v[v].tiles_x * table->v[v].tiles_y > (int64_t)kKeyRankMask + 1) return CG_ERR_ARG;
+  if (T > (int64_t(1) << (64 - kKeyTileShift))) return CG_ERR_ARG;
   memset(L, 0, sizeof(*L));
   const int nb = (s->sh_degree + 1) * (s->sh_degree + 1);
   const int64_t Kc = (int64_t)o->pair_capacity;
@@ -113,7 +117,7 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
   L->sort_blocks_cap = (std::max(Kc, R) + 4095) / 4096 + 1;  // 4096 keys per sort block
   const int64_t kmax = std::max(s->k_sr, s->k_sh) + 1;
   L->scan_blocks_cap = (std::max(R, kmax) + 4095) / 4096 + 1;
-  L->chunks_cap = (n + 255) / 256 + kmax;
+  L->chunks_cap = (n + 1023) / 1024 + kmax;  // chunks of 1024 members
   uint64_t off = 0;
   auto take = [&](uint64_t bytes) {
     const uint64_t at = off;
@@ -129,6 +133,8 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
   L->ntiles = take(sizeof(uint32_t) * R);
   L->depth = take(sizeof(uint32_t) * R);
   L->offrec = take(sizeof(uint32_t) * R);
+  L->nemit = take(sizeof(uint32_t) * R);
+  L->kmask = take(sizeof(uint64_t) * R);
   L->scan = take(sizeof(uint32_t) * std::max(R, kmax));
   L->dkeys0 = take(sizeof(uint64_t) * R);
   L->dkeys1 = take(sizeof(uint64_t) * R);
@@ -305,7 +311,7 @@ cg_status cg_workspace_array(void* workspace, size_t ws_bytes, cg_ws_array which
   const Layout& L = h.layout;
   char* b = reinterpret_cast<char*>(workspace);
   uint64_t off = 0, cnt = 0;
-  const int passes = (L.tile_bits + 7) / 8;
+  const int passes = tile_passes(L);
   switch (which) {
     case CG_WS_RECT: off = L.rect; cnt = L.R; break;
     case CG_WS_DEPTH: off = L.depth; cnt = L.R; break;
@@ -332,6 +338,10 @@ void cg_host_sh_consts(float out[16]) {
 }
 
 void cg_host_sigma3(const float row[8], float out[6]) { sigma3_from_row(row, out); }
+
+int cg_host_tile_keep(const float geo[6], int tx, int ty, int tile) {
+  return tile_keep(geo[0], geo[1], geo[2], geo[3], geo[4], geo[5], tx, ty, tile) ? 1 : 0;
+}
 
 cg_status cg_timing_enable(int on) {
   std::lock_guard<std::mutex> lk(g_timing.m);

@@ -183,6 +183,62 @@ CG_HD void sigma3_from_row(const float* row, float* sig) {
   }
 }
 
+// Whether a Gaussian can reach alpha >= 1/255 at some pixel centre of tile
+// (tx, ty) (decision arithmetic).  The exponent power(d) = h0 dx^2 +
+// h1 dx dy + h2 dy^2 (d = mean - pixel) is concave with its maximum 0 at the
+// mean; over the box of the tile's pixel centres it is largest at the mean if
+// the mean is inside, else on an edge facing the mean (at most two), where
+// the maximum over the edge is at the clamped stationary point.  The pair is
+// kept when o * exp32(pmax + 0.01) >= 1/255: the 0.01 margin covers the
+// rounding of pmax, so a dropped pair is skipped by every pixel of the tile.
+// ih0 = 1 / (2 h0) and ih2 = 1 / (2 h2) are computed once per Gaussian.
+CG_HD float tile_pmax(float mx, float my, float h0, float h1, float h2, float ih0, float ih2, int tx, int ty,
+                      int tile) {
+  const float xl = (float)(tx * tile) + 0.5f, xh = (float)(tx * tile + tile - 1) + 0.5f;
+  const float yl = (float)(ty * tile) + 0.5f, yh = (float)(ty * tile + tile - 1) + 0.5f;
+  const bool xin = mx >= xl && mx <= xh, yin = my >= yl && my <= yh;
+  if (xin && yin) return 0.0f;
+  float pmax = -3.0e38f;
+  if (!xin) {
+    const float dx = mx - (mx < xl ? xl : xh);
+    const float ds = -(h1 * dx) * ih2;
+    const float lo = my - yh, hi = my - yl;
+    const float dy = ds < lo ? lo : (ds > hi ? hi : ds);
+    const float p = fmaf(h0 * dx, dx, fmaf(h2 * dy, dy, (h1 * dx) * dy));
+    pmax = p > pmax ? p : pmax;
+  }
+  if (!yin) {
+    const float dy = my - (my < yl ? yl : yh);
+    const float ds = -(h1 * dy) * ih0;
+    const float lo = mx - xh, hi = mx - xl;
+    const float dx = ds < lo ? lo : (ds > hi ? hi : ds);
+    const float p = fmaf(h0 * dx, dx, fmaf(h2 * dy, dy, (h1 * dx) * dy));
+    pmax = p > pmax ? p : pmax;
+  }
+  return pmax;
+}
+
+CG_HD bool tile_keep(float mx, float my, float h0, float h1, float h2, float o, int tx, int ty, int tile) {
+  const float ih0 = 1.0f / (2.0f * h0), ih2 = 1.0f / (2.0f * h2);
+  const float pmax = tile_pmax(mx, my, h0, h1, h2, ih0, ih2, tx, ty, tile);
+  return o * exp32(pmax + 0.01f) >= kAlphaMin;
+}
+
+// Sort key of a (tile, Gaussian) pair: global tile in the top 21 bits, the
+// pair's rank among its record's kept tiles (row-major) in the next 17, the
+// record v * n + g in the low 26.  Only the tile bits are sorted.
+constexpr int kKeyRecBits = 26;
+constexpr int kKeyRankBits = 17;
+constexpr int kKeyTileShift = kKeyRecBits + kKeyRankBits;  // 43
+constexpr uint64_t kKeyRecMask = (1ull << kKeyRecBits) - 1;
+constexpr uint64_t kKeyRankMask = (1ull << kKeyRankBits) - 1;
+CG_HD uint64_t pair_key(uint64_t tile, uint32_t rank, uint32_t rec) {
+  return (tile << kKeyTileShift) | ((uint64_t)rank << kKeyRecBits) | (uint64_t)rec;
+}
+CG_HD uint32_t key_tile(uint64_t k) { return (uint32_t)(k >> kKeyTileShift); }
+CG_HD uint32_t key_rank(uint64_t k) { return (uint32_t)((k >> kKeyRecBits) & kKeyRankMask); }
+CG_HD uint32_t key_rec(uint64_t k) { return (uint32_t)(k & kKeyRecMask); }
+
 // ----------------------------------------------------------------------------
 // views and workspace
 // ----------------------------------------------------------------------------
@@ -209,7 +265,7 @@ struct ViewTable {
 struct Layout {
   uint64_t total;
   uint64_t hdr, views, sigma3, geo, rgbm, rect, ntiles, depth, offrec, scan, dkeys0, dkeys1, pairs0, pairs1,
-      ranges, tfinal, ncontrib, pairgrad, pairgrad1, recgrad, dsigma, drgb, csr_keys0, csr_keys1, csr_off_sr, csr_off_sh, csr_ids_sr, csr_ids_sh, chunks,
+      ranges, tfinal, ncontrib, pairgrad, pairgrad1, recgrad, nemit, kmask, dsigma, drgb, csr_keys0, csr_keys1, csr_off_sr, csr_off_sh, csr_ids_sr, csr_ids_sh, chunks,
       partials, hist, blocksums, l1;
   // sizes
   int64_t n, R, T, P, Kc;
@@ -293,6 +349,11 @@ cudaError_t launch_l1(const float* img, const float* tgt, int64_t count, float* 
 
 // The depth-sorted visible records (4 sort passes end in dkeys0).
 inline uint64_t* depth_sorted(void* ws, const Layout& L) { return ws_ptr<uint64_t>(ws, L.dkeys0); }
+// The tile-sorted pairs (tile passes of 8 bits: an odd count ends in pairs1).
+inline int tile_passes(const Layout& L) { return (L.tile_bits + 7) / 8; }
+inline uint64_t* sorted_pairs(void* ws, const Layout& L) {
+  return ws_ptr<uint64_t>(ws, (tile_passes(L) & 1) ? L.pairs1 : L.pairs0);
+}
 
 // Radix sort of `count` (device value) uint64 keys on bits [lo, lo + 8 * passes),
 // stable, ping-pong between a and b; returns in *result_in_b whether the

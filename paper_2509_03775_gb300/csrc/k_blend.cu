@@ -15,8 +15,8 @@
 // are summed in a fixed order: over a thread's pixels, then across the warp
 // by a reduce-scatter butterfly over groups of three Gaussians (27 values,
 // 31 shuffles, lane l ends with value l), then over the warps in index order.
-// The pair's sums go to its slot (slots of a Gaussian are contiguous, in
-// tile order): eight of them as one aligned 32-byte sector (mean x/y,
+// The pair's sums go to its slot, offset[record] + rank (the key carries the
+// rank; slots of a Gaussian are contiguous, in tile order): eight of them as one aligned 32-byte sector (mean x/y,
 // conic 0/1/2, colour r/g/b), the opacity sum in a separate array.  The
 // per-Gaussian gradient later sums a fixed set of slots in a fixed order.
 // No floating-point atomics.
@@ -39,7 +39,6 @@ struct BlendArgs {
   const uint64_t* pairs;
   const float4* geo;
   const float4* rgbm;
-  const ushort4* rect;
   const uint32_t* offrec;
   float bg0, bg1, bg2;
   float* images;          // forward output
@@ -101,7 +100,7 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_fwd(const Bl
     if (__syncthreads_and(mine)) break;
     const int n_in = (int)min((uint32_t)BATCH, rg.y - b0);
     for (int j = threadIdx.x; j < n_in; j += NT) {
-      const uint32_t rec = (uint32_t)args.pairs[b0 + j];
+      const uint32_t rec = key_rec(args.pairs[b0 + j]);
       sA[j] = args.geo[2 * (size_t)rec];
       sB[j] = args.geo[2 * (size_t)rec + 1];
       sC[j] = args.rgbm[rec];
@@ -275,9 +274,8 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const Bl
   const uint32_t len = rg.y - rg.x;
   // pairs past the last contributor of every pixel get zero gradient
   for (uint32_t j = maxc + threadIdx.x; j < len; j += NT) {
-    const uint32_t rec = (uint32_t)args.pairs[rg.x + j];
-    const ushort4 r = args.rect[rec];
-    const uint32_t slot = args.offrec[rec] + (uint32_t)(ty - r.y) * (uint32_t)(r.z - r.x) + (uint32_t)(tx - r.x);
+    const uint64_t key = args.pairs[rg.x + j];
+    const uint32_t slot = args.offrec[key_rec(key)] + key_rank(key);
     const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     args.pairgrad[2 * (size_t)slot] = z;
     args.pairgrad[2 * (size_t)slot + 1] = z;
@@ -289,12 +287,12 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const Bl
     const int n_in = (int)(b1 - b0);
     __syncthreads();
     for (int j = threadIdx.x; j < n_in; j += NT) {
-      const uint32_t rec = (uint32_t)args.pairs[b0 + j];
+      const uint64_t key = args.pairs[b0 + j];
+      const uint32_t rec = key_rec(key);
       sA[j] = args.geo[2 * (size_t)rec];
       sB[j] = args.geo[2 * (size_t)rec + 1];
       sC[j] = args.rgbm[rec];
-      const ushort4 r = args.rect[rec];
-      sSlot[j] = args.offrec[rec] + (uint32_t)(ty - r.y) * (uint32_t)(r.z - r.x) + (uint32_t)(tx - r.x);
+      sSlot[j] = args.offrec[rec] + key_rank(key);
     }
     __syncthreads();
     const uint32_t pos0 = (uint32_t)(b0 - rg.x);
@@ -365,20 +363,14 @@ static cudaError_t bwd_batch(int batch, dim3 grid, cudaStream_t s, const BlendAr
   return cudaGetLastError();
 }
 
-static const uint64_t* final_pairs(const Layout& L, void* ws) {
-  const int passes = (L.tile_bits + 7) / 8;
-  return (passes & 1) ? ws_ptr<const uint64_t>(ws, L.pairs1) : ws_ptr<const uint64_t>(ws, L.pairs0);
-}
-
 static BlendArgs blend_args(const Layout& L, void* ws, const float bg[3]) {
   BlendArgs a;
   a.views = ws_ptr<ViewInfo>(ws, L.views);
   a.n_views = L.n_views;
   a.ranges = ws_ptr<uint2>(ws, L.ranges);
-  a.pairs = final_pairs(L, ws);
+  a.pairs = sorted_pairs(ws, L);
   a.geo = ws_ptr<float4>(ws, L.geo);
   a.rgbm = ws_ptr<float4>(ws, L.rgbm);
-  a.rect = ws_ptr<ushort4>(ws, L.rect);
   a.offrec = ws_ptr<uint32_t>(ws, L.offrec);
   a.bg0 = bg[0];
   a.bg1 = bg[1];

@@ -9,7 +9,7 @@
 
 namespace cg {
 
-constexpr int kChunk = 256;  // members per chunk of the codebook reduction
+constexpr int kChunk = 1024;  // members per chunk of the codebook reduction
 
 // Y_k and dY_k/d(x, y, z) (x, y, z treated as independent), FP32.
 template <int NB>
@@ -56,149 +56,202 @@ __device__ __forceinline__ void sh_basis_only(float x, float y, float z, float* 
 // per-Gaussian backward
 // ---------------------------------------------------------------------------
 
-// One thread per visible (view, Gaussian) record, in depth order (the order
-// in which the record's pair slots were laid out, so neighbouring threads
-// read neighbouring slots).  Sums the record's slots in tile order and
-// applies the chain rule of the opacity, the colour (clamp mask, SH
-// direction) and the projection.  Writes the record's position, logit and
-// Sigma gradients to rg[rec][10] and its masked colour gradient to drgb.
+// Chain rule of one record from its nine slot sums gs (mean x/y, conic
+// 0/1/2, opacity, colour r/g/b): opacity -> logit, colour -> clamp mask and
+// SH direction -> position, conic -> 2D covariance -> Sigma and the
+// projection Jacobian -> position.
+template <int NB>
+__device__ __forceinline__ void record_chain(const SceneArgs& sc, const ViewInfo* __restrict__ views,
+                                           const float* __restrict__ sig3, const float4* __restrict__ geo,
+                                           const float4* __restrict__ rgbm, uint32_t rec, const float (&gs)[9],
+                                           float* __restrict__ rg, float* __restrict__ drgb) {
+  const int v = (int)(rec / (uint32_t)sc.n);
+  const int64_t g = (int64_t)rec - (int64_t)v * sc.n;
+  const float p[3] = {sc.pos[3 * g], sc.pos[3 * g + 1], sc.pos[3 * g + 2]};
+  const uint32_t isr = sc.g2sr[g], ish = sc.g2sh[g];
+  const ViewInfo& cam = views[v];
+  const float* W = cam.w2c;
+  float dp[3] = {0.0f, 0.0f, 0.0f}, dsg[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  const float o = geo[2 * (size_t)rec + 1].y;
+  const float dl = gs[5] * (o * (1.0f - o));
+  // colour -> clamp mask -> SH direction
+  const uint32_t mask = (uint32_t)rgbm[rec].w;
+  float dc[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) dc[c] = (mask >> c & 1u) ? 0.0f : gs[6 + c];
+  drgb[3 * (size_t)rec] = dc[0];
+  drgb[3 * (size_t)rec + 1] = dc[1];
+  drgb[3 * (size_t)rec + 2] = dc[2];
+  const float dv[3] = {p[0] - cam.campos[0], p[1] - cam.campos[1], p[2] - cam.campos[2]};
+  const float dist = sqrtf(fmaf(dv[0], dv[0], fmaf(dv[1], dv[1], dv[2] * dv[2])));
+  const float inv = 1.0f / dist;
+  const float dir[3] = {dv[0] * inv, dv[1] * inv, dv[2] * inv};
+  float Y[kMaxBasis], Dx[kMaxBasis], Dy[kMaxBasis], Dz[kMaxBasis];
+  sh_basis_grad<NB>(dir[0], dir[1], dir[2], Y, Dx, Dy, Dz);
+  float dd[3] = {0.0f, 0.0f, 0.0f};
+  const size_t rb = (size_t)ish * NB * 3;
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    const float dyk = fmaf(dc[0], load_row(sc.sh_rows, sc.dtype, rb + 3 * k),
+                           fmaf(dc[1], load_row(sc.sh_rows, sc.dtype, rb + 3 * k + 1),
+                                dc[2] * load_row(sc.sh_rows, sc.dtype, rb + 3 * k + 2)));
+    dd[0] = fmaf(dyk, Dx[k], dd[0]);
+    dd[1] = fmaf(dyk, Dy[k], dd[1]);
+    dd[2] = fmaf(dyk, Dz[k], dd[2]);
+  }
+  const float ddot = fmaf(dd[0], dir[0], fmaf(dd[1], dir[1], dd[2] * dir[2]));
+#pragma unroll
+  for (int a = 0; a < 3; ++a) dp[a] = fmaf(dd[a] - dir[a] * ddot, inv, dp[a]);
+  // projection
+  float t[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) t[a] = fmaf(W[4 * a], p[0], fmaf(W[4 * a + 1], p[1], fmaf(W[4 * a + 2], p[2], W[4 * a + 3])));
+  const float iz = 1.0f / t[2];
+  const float fx = cam.fx, fy = cam.fy;
+  const float J00 = fx * iz, J02 = -fx * t[0] * iz * iz, J11 = fy * iz, J12 = -fy * t[1] * iz * iz;
+  float T[6];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    T[j] = fmaf(J00, W[j], J02 * W[8 + j]);
+    T[3 + j] = fmaf(J11, W[4 + j], J12 * W[8 + j]);
+  }
+  const float* sgp = sig3 + (size_t)isr * 6;
+  const float S[9] = {sgp[0], sgp[1], sgp[2], sgp[1], sgp[3], sgp[4], sgp[2], sgp[4], sgp[5]};
+  float ST0[3], ST1[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    ST0[q] = fmaf(S[3 * q], T[0], fmaf(S[3 * q + 1], T[1], S[3 * q + 2] * T[2]));
+    ST1[q] = fmaf(S[3 * q], T[3], fmaf(S[3 * q + 1], T[4], S[3 * q + 2] * T[5]));
+  }
+  const float A = fmaf(T[0], ST0[0], fmaf(T[1], ST0[1], T[2] * ST0[2])) + kDilation;
+  const float B = fmaf(T[3], ST0[0], fmaf(T[4], ST0[1], T[5] * ST0[2]));
+  const float C = fmaf(T[3], ST1[0], fmaf(T[4], ST1[1], T[5] * ST1[2])) + kDilation;
+  const float det = fmaf(A, C, -(B * B));
+  const float id2 = 1.0f / (det * det);
+  const float g0 = gs[2], g1 = gs[3], g2 = gs[4];
+  const float da = (-g0 * C * C + g1 * B * C - g2 * B * B) * id2;
+  const float db = (2.0f * g0 * B * C - g1 * (A * C + B * B) + 2.0f * g2 * A * B) * id2;
+  const float dcc = (-g0 * B * B + g1 * A * B - g2 * A * A) * id2;
+  float dT[6];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    dT[j] = fmaf(2.0f * da, ST0[j], db * ST1[j]);
+    dT[3 + j] = fmaf(db, ST0[j], 2.0f * dcc * ST1[j]);
+  }
+  const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    const int q = ia[e], j = ib[e];
+    float f = fmaf(da * T[q], T[j], fmaf(db * T[q], T[3 + j], dcc * T[3 + q] * T[3 + j]));
+    if (q != j) f += fmaf(da * T[j], T[q], fmaf(db * T[j], T[3 + q], dcc * T[3 + j] * T[3 + q]));
+    dsg[e] = f;
+  }
+  float dJ[6];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      dJ[3 * a + k] = fmaf(dT[3 * a], W[4 * k], fmaf(dT[3 * a + 1], W[4 * k + 1], dT[3 * a + 2] * W[4 * k + 2]));
+  const float gmx = gs[0], gmy = gs[1];
+  const float iz2 = iz * iz;
+  float dt[3];
+  dt[0] = fmaf(-fx * iz2, dJ[2], fx * iz * gmx);
+  dt[1] = fmaf(-fy * iz2, dJ[5], fy * iz * gmy);
+  dt[2] = -fx * iz2 * dJ[0] + 2.0f * fx * t[0] * iz2 * iz * dJ[2] - fy * iz2 * dJ[4] +
+          2.0f * fy * t[1] * iz2 * iz * dJ[5] - fx * t[0] * iz2 * gmx - fy * t[1] * iz2 * gmy;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) dp[k] += fmaf(W[k], dt[0], fmaf(W[4 + k], dt[1], W[8 + k] * dt[2]));
+  float* out = rg + 10 * (size_t)rec;
+  out[0] = dp[0];
+  out[1] = dp[1];
+  out[2] = dp[2];
+  out[3] = dl;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) out[4 + e] = dsg[e];
+}
+
+// Visible (view, Gaussian) records in depth order, 32 per warp.  The slots
+// of a warp's records form one contiguous range (their offsets were scanned
+// in depth order), which the warp reads coalesced, 32 slots at a time; a
+// segmented shuffle scan over each group of 32 slots (segments = records)
+// adds each record's slots in a fixed order.  Then lane l applies the chain
+// rule of the opacity, the colour (clamp mask, SH direction) and the
+// projection for record l and writes its position, logit and Sigma
+// gradients to rg[rec][10] and its masked colour gradient to drgb.
 template <int NB>
 __global__ void __launch_bounds__(256) k_record_bwd(const SceneArgs sc, const ViewInfo* __restrict__ views,
                                                     const float* __restrict__ sig3, const float4* __restrict__ geo,
                                                     const float4* __restrict__ rgbm,
-                                                    const uint32_t* __restrict__ ntiles,
+                                                    const uint32_t* __restrict__ nemit,
                                                     const uint32_t* __restrict__ offrec,
                                                     const float4* __restrict__ pairgrad,
                                                     const float* __restrict__ pairgrad1,
                                                     const uint64_t* __restrict__ dsorted, const DeviceState* st,
                                                     float* __restrict__ rg, float* __restrict__ drgb) {
+  __shared__ uint32_t sOff[8][32];
+  __shared__ float sAcc[8][32][9];
   if (st->pairs_ok == 0) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t vis = (int64_t)st->visible;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vis; i += stride) {
-    const uint32_t rec = (uint32_t)dsorted[i];
-    const int v = (int)(rec / (uint32_t)sc.n);
-    const int64_t g = (int64_t)rec - (int64_t)v * sc.n;
-    const uint32_t nt = ntiles[rec];
-    // slot sums: mean x/y, conic 0/1/2, opacity, colour r/g/b
-    float gs[9] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-    const uint32_t off = offrec[rec];
-    const float4* src = pairgrad + 2 * (size_t)off;
-    const float* src1 = pairgrad1 + off;
-#pragma unroll 2
-    for (uint32_t t = 0; t < nt; ++t) {
-      const float4 u = src[2 * (size_t)t], w = src[2 * (size_t)t + 1];
-      gs[0] += u.x;
-      gs[1] += u.y;
-      gs[2] += u.z;
-      gs[3] += u.w;
-      gs[4] += w.x;
-      gs[6] += w.y;
-      gs[7] += w.z;
-      gs[8] += w.w;
-      gs[5] += src1[t];
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = warp * 32; base < vis; base += nwarps * 32) {
+    const int64_t i = base + lane;
+    const int cnt = (int)min((int64_t)32, vis - base);
+    uint32_t rec = 0, off = 0, nt = 0;
+    if (i < vis) {
+      rec = (uint32_t)dsorted[i];
+      off = offrec[rec];
+      nt = nemit[rec];
     }
-    const float p[3] = {sc.pos[3 * g], sc.pos[3 * g + 1], sc.pos[3 * g + 2]};
-    const uint32_t isr = sc.g2sr[g], ish = sc.g2sh[g];
-    const ViewInfo& cam = views[v];
-    const float* W = cam.w2c;
-    float dp[3] = {0.0f, 0.0f, 0.0f}, dsg[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-    const float o = geo[2 * (size_t)rec + 1].y;
-    const float dl = gs[5] * (o * (1.0f - o));
-    // colour -> clamp mask -> SH direction
-    const uint32_t mask = (uint32_t)rgbm[rec].w;
-    float dc[3];
+    sOff[wid][lane] = off;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) dc[c] = (mask >> c & 1u) ? 0.0f : gs[6 + c];
-    drgb[3 * (size_t)rec] = dc[0];
-    drgb[3 * (size_t)rec + 1] = dc[1];
-    drgb[3 * (size_t)rec + 2] = dc[2];
-    const float dv[3] = {p[0] - cam.campos[0], p[1] - cam.campos[1], p[2] - cam.campos[2]};
-    const float dist = sqrtf(fmaf(dv[0], dv[0], fmaf(dv[1], dv[1], dv[2] * dv[2])));
-    const float inv = 1.0f / dist;
-    const float dir[3] = {dv[0] * inv, dv[1] * inv, dv[2] * inv};
-    float Y[kMaxBasis], Dx[kMaxBasis], Dy[kMaxBasis], Dz[kMaxBasis];
-    sh_basis_grad<NB>(dir[0], dir[1], dir[2], Y, Dx, Dy, Dz);
-    float dd[3] = {0.0f, 0.0f, 0.0f};
-    const size_t rb = (size_t)ish * NB * 3;
+    for (int e = 0; e < 9; ++e) sAcc[wid][lane][e] = 0.0f;
+    const uint32_t s0 = __shfl_sync(0xffffffffu, off, 0);
+    const uint32_t s1 = __shfl_sync(0xffffffffu, off + nt, cnt - 1);
+    __syncwarp();
+    for (uint32_t c0 = s0; c0 < s1; c0 += 32) {
+      const uint32_t slot = c0 + lane;
+      const bool valid = slot < s1;
+      // owner: the last record of the warp whose offset is <= slot
+      int own = 0;
 #pragma unroll
-    for (int k = 0; k < NB; ++k) {
-      const float dyk = fmaf(dc[0], load_row(sc.sh_rows, sc.dtype, rb + 3 * k),
-                             fmaf(dc[1], load_row(sc.sh_rows, sc.dtype, rb + 3 * k + 1),
-                                  dc[2] * load_row(sc.sh_rows, sc.dtype, rb + 3 * k + 2)));
-      dd[0] = fmaf(dyk, Dx[k], dd[0]);
-      dd[1] = fmaf(dyk, Dy[k], dd[1]);
-      dd[2] = fmaf(dyk, Dz[k], dd[2]);
+      for (int stp = 16; stp > 0; stp >>= 1)
+        if (own + stp < cnt && sOff[wid][own + stp] <= slot) own += stp;
+      float v[9];
+      if (valid) {
+        const float4 u = pairgrad[2 * (size_t)slot], w = pairgrad[2 * (size_t)slot + 1];
+        v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w; v[4] = w.x;
+        v[5] = pairgrad1[slot];
+        v[6] = w.y; v[7] = w.z; v[8] = w.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 9; ++e) v[e] = 0.0f;
+        own = 32;
+      }
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int own_up = __shfl_up_sync(0xffffffffu, own, d);
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+          const float up = __shfl_up_sync(0xffffffffu, v[e], d);
+          if (lane >= d && own_up == own) v[e] += up;
+        }
+      }
+      const int own_next = __shfl_down_sync(0xffffffffu, own, 1);
+      if (valid && (lane == 31 || own_next != own)) {
+#pragma unroll
+        for (int e = 0; e < 9; ++e) sAcc[wid][own][e] += v[e];
+      }
+      __syncwarp();
     }
-    const float ddot = fmaf(dd[0], dir[0], fmaf(dd[1], dir[1], dd[2] * dir[2]));
+    if (i < vis) {
+      float gs[9];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) dp[a] = fmaf(dd[a] - dir[a] * ddot, inv, dp[a]);
-    // projection
-    float t[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) t[a] = fmaf(W[4 * a], p[0], fmaf(W[4 * a + 1], p[1], fmaf(W[4 * a + 2], p[2], W[4 * a + 3])));
-    const float iz = 1.0f / t[2];
-    const float fx = cam.fx, fy = cam.fy;
-    const float J00 = fx * iz, J02 = -fx * t[0] * iz * iz, J11 = fy * iz, J12 = -fy * t[1] * iz * iz;
-    float T[6];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      T[j] = fmaf(J00, W[j], J02 * W[8 + j]);
-      T[3 + j] = fmaf(J11, W[4 + j], J12 * W[8 + j]);
+      for (int e = 0; e < 9; ++e) gs[e] = sAcc[wid][lane][e];
+      record_chain<NB>(sc, views, sig3, geo, rgbm, rec, gs, rg, drgb);
     }
-    const float* sgp = sig3 + (size_t)isr * 6;
-    const float S[9] = {sgp[0], sgp[1], sgp[2], sgp[1], sgp[3], sgp[4], sgp[2], sgp[4], sgp[5]};
-    float ST0[3], ST1[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      ST0[q] = fmaf(S[3 * q], T[0], fmaf(S[3 * q + 1], T[1], S[3 * q + 2] * T[2]));
-      ST1[q] = fmaf(S[3 * q], T[3], fmaf(S[3 * q + 1], T[4], S[3 * q + 2] * T[5]));
-    }
-    const float A = fmaf(T[0], ST0[0], fmaf(T[1], ST0[1], T[2] * ST0[2])) + kDilation;
-    const float B = fmaf(T[3], ST0[0], fmaf(T[4], ST0[1], T[5] * ST0[2]));
-    const float C = fmaf(T[3], ST1[0], fmaf(T[4], ST1[1], T[5] * ST1[2])) + kDilation;
-    const float det = fmaf(A, C, -(B * B));
-    const float id2 = 1.0f / (det * det);
-    const float g0 = gs[2], g1 = gs[3], g2 = gs[4];
-    const float da = (-g0 * C * C + g1 * B * C - g2 * B * B) * id2;
-    const float db = (2.0f * g0 * B * C - g1 * (A * C + B * B) + 2.0f * g2 * A * B) * id2;
-    const float dcc = (-g0 * B * B + g1 * A * B - g2 * A * A) * id2;
-    float dT[6];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      dT[j] = fmaf(2.0f * da, ST0[j], db * ST1[j]);
-      dT[3 + j] = fmaf(db, ST0[j], 2.0f * dcc * ST1[j]);
-    }
-    const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-    for (int e = 0; e < 6; ++e) {
-      const int q = ia[e], j = ib[e];
-      float f = fmaf(da * T[q], T[j], fmaf(db * T[q], T[3 + j], dcc * T[3 + q] * T[3 + j]));
-      if (q != j) f += fmaf(da * T[j], T[q], fmaf(db * T[j], T[3 + q], dcc * T[3 + j] * T[3 + q]));
-      dsg[e] = f;
-    }
-    float dJ[6];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        dJ[3 * a + k] = fmaf(dT[3 * a], W[4 * k], fmaf(dT[3 * a + 1], W[4 * k + 1], dT[3 * a + 2] * W[4 * k + 2]));
-    const float gmx = gs[0], gmy = gs[1];
-    const float iz2 = iz * iz;
-    float dt[3];
-    dt[0] = fmaf(-fx * iz2, dJ[2], fx * iz * gmx);
-    dt[1] = fmaf(-fy * iz2, dJ[5], fy * iz * gmy);
-    dt[2] = -fx * iz2 * dJ[0] + 2.0f * fx * t[0] * iz2 * iz * dJ[2] - fy * iz2 * dJ[4] +
-            2.0f * fy * t[1] * iz2 * iz * dJ[5] - fx * t[0] * iz2 * gmx - fy * t[1] * iz2 * gmy;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) dp[k] += fmaf(W[k], dt[0], fmaf(W[4 + k], dt[1], W[8 + k] * dt[2]));
-    float* out = rg + 10 * (size_t)rec;
-    out[0] = dp[0];
-    out[1] = dp[1];
-    out[2] = dp[2];
-    out[3] = dl;
-#pragma unroll
-    for (int e = 0; e < 6; ++e) out[4 + e] = dsg[e];
+    __syncwarp();
   }
 }
 
@@ -247,7 +300,7 @@ cudaError_t launch_gaussian_bwd(const SceneArgs& sc, const Layout& L, void* ws, 
   float* drgb = ws_ptr<float>(ws, L.drgb);
   const uint64_t* dsorted = depth_sorted(ws, L);
   const int grid_r = (int)std::max<int64_t>(1, std::min<int64_t>((L.R + 255) / 256, 152 * 16));
-#define CG_RB(NBV) count_launch(), k_record_bwd<NBV><<<grid_r, 256, 0, s>>>(sc, views, sig, geo, rgbm, nt, off, pg, pg1, dsorted, &hdr->st, rg, drgb)
+#define CG_RB(NBV) count_launch(), k_record_bwd<NBV><<<grid_r, 256, 0, s>>>(sc, views, sig, geo, rgbm, ws_ptr<const uint32_t>(ws, L.nemit), off, pg, pg1, dsorted, &hdr->st, rg, drgb)
   switch (sc.nb) {
     case 1: CG_RB(1); break;
     case 4: CG_RB(4); break;
@@ -475,20 +528,31 @@ __global__ void __launch_bounds__(256) k_sr_rows(const uint32_t* __restrict__ st
   for (int i = 0; i < 8; ++i) d_sr[(size_t)r * 8 + i] = drow[i];
 }
 
-// Warp per SH row: lane e sums component e over the row's chunks in order.
+// Warp per SH row: lanes take the row's chunks in a fixed stride and
+// accumulate all W = 3 (d+1)^2 components; a fixed butterfly adds the lanes.
+template <int W>
 __global__ void __launch_bounds__(256) k_sh_rows(const uint32_t* __restrict__ start, const uint32_t* __restrict__ end,
-                                                 const uint32_t* __restrict__ chunk_base, int k_sh, int width,
+                                                 const uint32_t* __restrict__ chunk_base, int k_sh,
                                                  const float* __restrict__ part, float* __restrict__ d_sh) {
   const int lane = threadIdx.x & 31;
   const int r = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (r >= k_sh) return;
   const uint32_t nch = (end[r] - start[r] + kChunk - 1) / kChunk, cb = chunk_base[r];
-  for (int e = lane; e < width; e += 32) {
-    float s = 0.0f;
-#pragma unroll 4
-    for (uint32_t c = 0; c < nch; ++c) s += part[(size_t)width * (cb + c) + e];
-    d_sh[(size_t)r * width + e] = s;
+  float acc[W];
+#pragma unroll
+  for (int e = 0; e < W; ++e) acc[e] = 0.0f;
+  for (uint32_t c = lane; c < nch; c += 32) {
+    const float* p = part + (size_t)W * (cb + c);
+#pragma unroll
+    for (int e = 0; e < W; ++e) acc[e] += p[e];
   }
+#pragma unroll
+  for (int e = 0; e < W; ++e)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+#pragma unroll
+  for (int e = 0; e < W; ++e)
+    if (e % 32 == lane) d_sh[(size_t)r * W + e] = acc[e];
 }
 
 // CSR of one index array: member ids (by row, then Gaussian), row bounds,
@@ -547,9 +611,16 @@ cudaError_t launch_codebook_reduce(const SceneArgs& sc, const Layout& L, void* w
     default: return cudaErrorInvalidValue;
   }
 #undef CG_SHP
-  const int width = sc.nb * 3;
-  count_launch(), k_sh_rows<<<(sc.k_sh + 7) / 8, 256, 0, s>>>(csr_sh, csr_sh + sc.k_sh, csr_sh + 2 * (int64_t)sc.k_sh,
-                                                              sc.k_sh, width, part, d_sh);
+  const unsigned gr = (unsigned)((sc.k_sh + 7) / 8);
+  const uint32_t* e_sh = csr_sh + sc.k_sh;
+  const uint32_t* cb_sh = csr_sh + 2 * (int64_t)sc.k_sh;
+  switch (sc.nb) {
+    case 1: count_launch(), k_sh_rows<3><<<gr, 256, 0, s>>>(csr_sh, e_sh, cb_sh, sc.k_sh, part, d_sh); break;
+    case 4: count_launch(), k_sh_rows<12><<<gr, 256, 0, s>>>(csr_sh, e_sh, cb_sh, sc.k_sh, part, d_sh); break;
+    case 9: count_launch(), k_sh_rows<27><<<gr, 256, 0, s>>>(csr_sh, e_sh, cb_sh, sc.k_sh, part, d_sh); break;
+    case 16: count_launch(), k_sh_rows<48><<<gr, 256, 0, s>>>(csr_sh, e_sh, cb_sh, sc.k_sh, part, d_sh); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -7,7 +7,8 @@
 // Instead of one 64-bit sort of all pairs, the records are sorted by depth
 // once (N keys, 4 passes) and the pairs emitted in that order are then
 // sorted stably on the tile bits only (2-3 passes): the same order, with
-// far fewer bytes moved per pair.
+// far fewer bytes moved per pair.  Only the tiles that pass the exact tile
+// test (tile_keep) are listed.
 //
 // Sort passes use reduce-then-scan (per-block digit histograms, a scan of
 // them, a stable scatter).  No CTA ever waits for another one.
@@ -38,11 +39,15 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_upsweep(const uint64_t* _
     h[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = b * kSortTile;
-#pragma unroll 4
-    for (int i = threadIdx.x; i < kSortTile; i += kSortThreads) {
-      const int64_t idx = base + i;
-      if (idx < count) atomicAdd(&h[(uint32_t)(keys[idx] >> shift) & 255u], 1u);
+    uint64_t k[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+      const int64_t idx = base + r * kSortThreads + threadIdx.x;
+      k[r] = idx < count ? __ldcs(keys + idx) : ~0ull;
     }
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r)
+      if (base + r * kSortThreads + threadIdx.x < count) atomicAdd(&h[(uint32_t)(k[r] >> shift) & 255u], 1u);
     __syncthreads();
     hist[(int64_t)threadIdx.x * nb_cap + b] = h[threadIdx.x];
     __syncthreads();
@@ -125,13 +130,26 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_downsweep(const uint64
     const int64_t base = b * kSortTile + (int64_t)wid * (32 * kSortItems);
     uint64_t key[kSortItems];
     uint32_t rank[kSortItems];
+    // all loads first, so they are in flight together
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+      const int64_t idx = base + r * 32 + lane;
+      key[r] = idx < count ? __ldcs(in + idx) : 0ull;
+    }
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
       const int64_t idx = base + r * 32 + lane;
       const bool valid = idx < count;
-      key[r] = valid ? in[idx] : 0ull;
       const uint32_t d = valid ? ((uint32_t)(key[r] >> shift) & 255u) : 256u;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      // lanes holding the same 9-bit value (digit, or 256 for no key): one
+      // ballot per bit
+      uint32_t peers = 0xffffffffu;
+#pragma unroll
+      for (int bit = 0; bit < 9; ++bit) {
+        const uint32_t on = (d >> bit) & 1u;
+        const uint32_t m = __ballot_sync(0xffffffffu, on != 0u);
+        peers &= on ? m : ~m;
+      }
       const uint32_t before = __popc(peers & lt_mask);
       uint32_t old = 0;
       if (valid) old = wcnt[wid][d];
@@ -322,12 +340,92 @@ __global__ void k_compact_depth(const uint32_t* __restrict__ ntiles, const uint3
     if (ntiles[i] > 0) dkeys[pos[i]] = ((uint64_t)depth[i] << 32) | (uint64_t)i;
 }
 
-__global__ void k_gather_ntiles(const uint64_t* __restrict__ dkeys, const uint32_t* __restrict__ ntiles,
-                                uint32_t* __restrict__ out, const uint64_t* visible_dev) {
-  const int64_t vis = (int64_t)*visible_dev;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < vis; i += stride)
-    out[i] = ntiles[(uint32_t)dkeys[i]];
+// Per-record data of the tile test, staged in shared memory for the warp
+// that walks the record's rectangle.
+struct TileRec {
+  float4 a;       // mean x, mean y, h0, h1
+  float4 b;       // h2, opacity, 1 / (2 h0), 1 / (2 h2)
+  float lthr;     // -log(255 o), approximate (see tile_decide)
+  float rw;       // 1 / rectangle width
+  uint32_t r01;   // x0 | y0 << 16
+  uint32_t r23;   // x1 | y1 << 16
+};
+
+__device__ __forceinline__ void stage_record(TileRec& t, const float4* __restrict__ geo,
+                                             const ushort4* __restrict__ rect, uint32_t rec) {
+  const ushort4 r = rect[rec];
+  t.a = geo[2 * (size_t)rec];
+  const float4 gb = geo[2 * (size_t)rec + 1];
+  t.b = make_float4(gb.x, gb.y, 1.0f / (2.0f * t.a.z), 1.0f / (2.0f * gb.x));
+  t.lthr = -logf(255.0f * gb.y);
+  t.rw = 1.0f / (float)max(1, (int)r.z - (int)r.x);
+  t.r01 = (uint32_t)r.x | ((uint32_t)r.y << 16);
+  t.r23 = (uint32_t)r.z | ((uint32_t)r.w << 16);
+}
+
+// tile_keep's decision, o * exp32(pmax + 0.01) >= 1/255, taken without exp32
+// when pmax + 0.01 is more than 1e-3 from log(1/(255 o)): exp32 is within
+// 4e-7 of exp and logf within a few ulp of log, so outside that band the
+// exact comparison cannot come out differently.
+__device__ __forceinline__ bool tile_decide(const TileRec& t, float pmax) {
+  const float x = pmax + 0.01f;
+  if (x < t.lthr - 1e-3f) return false;
+  if (x > t.lthr + 1e-3f) return true;
+  return t.b.y * exp32(x) >= kAlphaMin;
+}
+
+// Kept tiles of each depth-ordered record (tile_keep over the record's
+// rectangle).  A warp takes 32 records and counts each one's tiles with all
+// lanes.  Writes the count per record and, in depth order, the input of the
+// offset scan.
+__global__ void __launch_bounds__(256) k_count_emit(const uint64_t* __restrict__ dkeys,
+                                                    const float4* __restrict__ geo,
+                                                    const ushort4* __restrict__ rect, int64_t R, int tile,
+                                                    uint32_t* __restrict__ nemit, uint32_t* __restrict__ counts,
+                                                    uint64_t* __restrict__ kmask, const uint64_t* visible_dev) {
+  __shared__ TileRec st[8][32];
+  const int64_t vis = min((int64_t)*visible_dev, R);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = warp * 32; base < vis; base += nwarps * 32) {
+    const int64_t i = base + lane;
+    uint32_t rec = 0;
+    if (i < vis) {
+      rec = (uint32_t)dkeys[i];
+      stage_record(st[wid][lane], geo, rect, rec);
+    }
+    __syncwarp();
+    const int cnt = (int)min((int64_t)32, vis - base);
+    uint32_t mine = 0;
+    for (int q = 0; q < cnt; ++q) {
+      const TileRec& t = st[wid][q];
+      const int x0 = (int)(t.r01 & 0xffffu), y0 = (int)(t.r01 >> 16);
+      const int w = (int)(t.r23 & 0xffffu) - x0, total = w * ((int)(t.r23 >> 16) - y0);
+      uint32_t c = 0;
+      uint64_t bits = 0;
+      for (int t0 = 0; t0 < total; t0 += 32) {
+        const int k = t0 + lane;
+        bool keep = false;
+        if (k < total) {
+          const int yy = (int)(((float)k + 0.5f) * t.rw), xx = k - yy * w;
+          keep = tile_decide(t, tile_pmax(t.a.x, t.a.y, t.a.z, t.a.w, t.b.x, t.b.z, t.b.w, x0 + xx, y0 + yy, tile));
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, keep);
+        if (t0 < 64) bits |= (uint64_t)m << t0;
+        c += __popc(m);
+      }
+      if (lane == q) {
+        mine = c;
+        if (total <= 64) kmask[rec] = bits;  // the emit pass reuses the decisions
+      }
+    }
+    __syncwarp();
+    if (i < vis) {
+      nemit[rec] = mine;
+      counts[i] = mine;
+    }
+  }
 }
 
 __global__ void k_capacity(DeviceState* st, int64_t cap) {
@@ -339,50 +437,70 @@ __global__ void k_capacity(DeviceState* st, int64_t cap) {
   if (!ok) set_status(st, CG_ERR_CAPACITY, 0);
 }
 
-// Pairs of one record: (global tile << 32) | record, tiles of its rectangle
-// in row-major order starting at its offset.  A warp takes 32 consecutive
-// records (depth order) and writes their pairs one record at a time with all
-// lanes, so the stores of a record are contiguous.
+// Pairs of one record in depth order: its kept tiles (tile_keep) in
+// row-major order of its rectangle, each as pair_key(global tile, rank among
+// the kept tiles, record) at offset + rank.  A warp takes 32 consecutive
+// records and writes each one's pairs with all lanes, so the stores of a
+// record are contiguous.
 __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__ dkeys,
                                                     const uint32_t* __restrict__ off_sorted,
+                                                    const float4* __restrict__ geo,
                                                     const ushort4* __restrict__ rect,
-                                                    const ViewInfo* __restrict__ views, int64_t n,
+                                                    const ViewInfo* __restrict__ views, int64_t n, int tile,
+                                                    const uint64_t* __restrict__ kmask,
                                                     uint32_t* __restrict__ offrec, uint64_t* __restrict__ pairs,
-                                                    const DeviceState* st) {
-  const int64_t vis = (int64_t)st->visible;
-  const bool ok = st->pairs_ok != 0;
-  const int lane = threadIdx.x & 31;
+                                                    const DeviceState* state) {
+  __shared__ TileRec st[8][32];
+  __shared__ uint2 sro[8][32];  // record, offset
+  const int64_t vis = (int64_t)state->visible;
+  const bool ok = state->pairs_ok != 0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t base = warp * 32; base < vis; base += nwarps * 32) {
     const int64_t i = base + lane;
-    uint32_t rec = 0, off = 0, r01 = 0, r23 = 0;
     if (i < vis) {
-      rec = (uint32_t)dkeys[i];
-      off = off_sorted[i];
+      const uint32_t rec = (uint32_t)dkeys[i];
+      const uint32_t off = off_sorted[i];
       offrec[rec] = off;
-      const ushort4 r = rect[rec];
-      r01 = (uint32_t)r.x | ((uint32_t)r.y << 16);
-      r23 = (uint32_t)r.z | ((uint32_t)r.w << 16);
+      stage_record(st[wid][lane], geo, rect, rec);
+      sro[wid][lane] = make_uint2(rec, off);
     }
-    if (!ok) continue;
-    const int cnt = (int)min((int64_t)32, vis - base);
-    for (int q = 0; q < cnt; ++q) {
-      const uint32_t qrec = __shfl_sync(0xffffffffu, rec, q);
-      const uint32_t qoff = __shfl_sync(0xffffffffu, off, q);
-      const uint32_t q01 = __shfl_sync(0xffffffffu, r01, q);
-      const uint32_t q23 = __shfl_sync(0xffffffffu, r23, q);
-      const int x0 = (int)(q01 & 0xffffu), y0 = (int)(q01 >> 16);
-      const int w = (int)(q23 & 0xffffu) - x0, h = (int)(q23 >> 16) - y0;
-      const ViewInfo& cam = views[qrec / (uint64_t)n];
-      const int64_t tb = cam.tile_base;
-      const int tx = cam.tiles_x;
-      const int total = w * h;
-      for (int t = lane; t < total; t += 32) {
-        const int yy = t / w, xx = t - yy * w;
-        pairs[qoff + t] = ((uint64_t)(tb + (int64_t)(y0 + yy) * tx + (x0 + xx)) << 32) | qrec;
+    __syncwarp();
+    if (ok) {
+      const int cnt = (int)min((int64_t)32, vis - base);
+      for (int q = 0; q < cnt; ++q) {
+        const TileRec& t = st[wid][q];
+        const uint2 ro = sro[wid][q];
+        const int x0 = (int)(t.r01 & 0xffffu), y0 = (int)(t.r01 >> 16);
+        const int w = (int)(t.r23 & 0xffffu) - x0, total = w * ((int)(t.r23 >> 16) - y0);
+        const ViewInfo& cam = views[ro.x / (uint32_t)n];
+        const int64_t tb = cam.tile_base;
+        const int tx = cam.tiles_x;
+        uint32_t rank0 = 0;
+        const uint64_t bits = total <= 64 ? kmask[ro.x] : 0ull;
+        for (int t0 = 0; t0 < total; t0 += 32) {
+          const int k = t0 + lane;
+          bool keep = false;
+          int xx = 0, yy = 0;
+          if (k < total) {
+            yy = (int)(((float)k + 0.5f) * t.rw);
+            xx = k - yy * w;
+            keep = total <= 64 ? ((bits >> k) & 1ull) != 0ull
+                               : tile_decide(t, tile_pmax(t.a.x, t.a.y, t.a.z, t.a.w, t.b.x, t.b.z, t.b.w, x0 + xx,
+                                                          y0 + yy, tile));
+          }
+          const uint32_t m = __ballot_sync(0xffffffffu, keep);
+          if (keep) {
+            const uint32_t rank = rank0 + __popc(m & lt_mask);
+            pairs[ro.y + rank] = pair_key((uint64_t)(tb + (int64_t)(y0 + yy) * tx + (x0 + xx)), rank, ro.x);
+          }
+          rank0 += __popc(m);
+        }
       }
     }
+    __syncwarp();
   }
 }
 
@@ -395,9 +513,9 @@ __global__ void k_ranges(const uint64_t* __restrict__ pairs, uint2* __restrict__
   const int64_t k = st->pairs_ok ? (int64_t)st->pairs : 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
-    const uint32_t t = (uint32_t)(pairs[i] >> 32);
-    if (i == 0 || (uint32_t)(pairs[i - 1] >> 32) != t) ranges[t].x = (uint32_t)i;
-    if (i == k - 1 || (uint32_t)(pairs[i + 1] >> 32) != t) ranges[t].y = (uint32_t)(i + 1);
+    const uint32_t t = key_tile(pairs[i]);
+    if (i == 0 || key_tile(pairs[i - 1]) != t) ranges[t].x = (uint32_t)i;
+    if (i == k - 1 || key_tile(pairs[i + 1]) != t) ranges[t].y = (uint32_t)(i + 1);
   }
 }
 
@@ -422,21 +540,27 @@ cudaError_t launch_build_pairs(const Layout& L, void* ws, int tile_bits, cudaStr
   if (e != cudaSuccess) return e;
   const uint64_t* dsorted = in_b ? dk1 : dk0;
   if (dsorted != depth_sorted(ws, L)) return cudaErrorInvalidValue;
-  // 3. pair offsets in depth order, total pair count and capacity check
-  count_launch(), k_gather_ntiles<<<g, 256, 0, s>>>(dsorted, ntiles, scan, &st->visible);
+  // 3. kept tiles per record, pair offsets in depth order, total pair count
+  //    and capacity check
+  count_launch(), k_count_emit<<<g, 256, 0, s>>>(dsorted, ws_ptr<const float4>(ws, L.geo),
+                                                 ws_ptr<const ushort4>(ws, L.rect), R, L.tile,
+                                                 ws_ptr<uint32_t>(ws, L.nemit), scan, ws_ptr<uint64_t>(ws, L.kmask),
+                                                 &st->visible);
   e = scan_u32(ws, L, scan, scan, &st->visible, R, &st->scan_total, s);
   if (e != cudaSuccess) return e;
   count_launch(), k_capacity<<<1, 1, 0, s>>>(st, L.Kc);
   // 4. emit pairs in depth order
   uint64_t* p0 = ws_ptr<uint64_t>(ws, L.pairs0);
   uint64_t* p1 = ws_ptr<uint64_t>(ws, L.pairs1);
-  count_launch(), k_emit_pairs<<<g, 256, 0, s>>>(dsorted, scan, ws_ptr<const ushort4>(ws, L.rect), ws_ptr<ViewInfo>(ws, L.views),
-                                 L.n, ws_ptr<uint32_t>(ws, L.offrec), p0, st);
+  count_launch(), k_emit_pairs<<<g, 256, 0, s>>>(dsorted, scan, ws_ptr<const float4>(ws, L.geo),
+                                                 ws_ptr<const ushort4>(ws, L.rect), ws_ptr<ViewInfo>(ws, L.views),
+                                                 L.n, L.tile, ws_ptr<const uint64_t>(ws, L.kmask),
+                                                 ws_ptr<uint32_t>(ws, L.offrec), p0, st);
   // 5. stable sort on the tile bits
-  const int passes = (tile_bits + 7) / 8;
-  e = sort_u64(ws, L, p0, p1, &st->pairs, L.Kc, 32, passes, &in_b, s);
+  e = sort_u64(ws, L, p0, p1, &st->pairs, L.Kc, kKeyTileShift, tile_passes(L), &in_b, s);
   if (e != cudaSuccess) return e;
   const uint64_t* psorted = in_b ? p1 : p0;
+  if (psorted != sorted_pairs(ws, L)) return cudaErrorInvalidValue;
   // 6. per-tile ranges
   uint2* ranges = ws_ptr<uint2>(ws, L.ranges);
   const int gt = (int)std::max<int64_t>(1, std::min<int64_t>((2 * L.T + 255) / 256, kGrid));

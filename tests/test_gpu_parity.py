@@ -85,8 +85,17 @@ def _compare(ref, gpu, check_grads=True):
     # sorted pairs and ranges
     pairs = gpu["pairs"]
     assert pairs.size == ref.k_pairs
-    assert np.array_equal(pairs >> np.uint64(32), ref.keys >> np.uint64(32))
-    assert np.array_equal((pairs & np.uint64(0xffffffff)).astype(np.uint32), ref.list)
+    tiles = pairs >> np.uint64(43)
+    recs = (pairs & np.uint64((1 << 26) - 1)).astype(np.int64)
+    ranks = ((pairs >> np.uint64(26)) & np.uint64((1 << 17) - 1)).astype(np.int64)
+    assert np.array_equal(tiles, ref.keys >> np.uint64(32))
+    assert np.array_equal(recs, ref.list.astype(np.int64))
+    # rank = position of the tile among the record's listed tiles (row-major)
+    order = np.lexsort((tiles, recs))
+    r_sorted, k_sorted = recs[order], ranks[order]
+    first = np.concatenate([[0], np.nonzero(np.diff(r_sorted))[0] + 1])
+    expect = np.arange(r_sorted.size) - np.repeat(first, np.diff(np.concatenate([first, [r_sorted.size]])))
+    assert np.array_equal(k_sorted, expect)
     assert np.array_equal(gpu["ranges"], ref.ranges)
     # per-pixel outputs
     assert np.array_equal(gpu["ncontrib"], ref.n_contrib.astype(np.uint32))

@@ -84,3 +84,30 @@ def test_workspace_bytes_and_argument_checks(lib):
     assert lib.cg_render_fwd(ctypes.byref(sc), camarr, 1, ctypes.byref(o), ws, 16, img, None) == cg.CG_ERR_ARG
     sc.pos = 0
     assert lib.cg_render_fwd(ctypes.byref(sc), camarr, 1, ctypes.byref(o), ws, n2, img, None) == cg.CG_ERR_ARG
+
+
+def test_host_tile_keep_matches_oracle(lib):
+    """The tile test decides an integer outcome (which tiles list a
+    Gaussian): the kernels' and the oracle's FP32 arithmetic must agree on
+    every input, including means on tile edges and near-threshold cases."""
+    from paper_2509_03775_gb300 import scenes
+    sc, cams = scenes.config_single(n=4000, k=64, width=256, height=192)
+    r = oracle.Render(sc, cams, tile=16, cull=False)
+    q = r.rec32[r.rec32["visible"] == 1]
+    n_checked = 0
+    for t in q:
+        geo = np.float32([t["mx"], t["my"], t["h0"], t["h1"], t["h2"], t["o"]])
+        for ty in range(t["y0"], t["y1"]):
+            for tx in range(t["x0"], t["x1"]):
+                mine = lib.cg_host_tile_keep(geo.ctypes.data_as(ctypes.c_void_p), tx, ty, 16)
+                ref = oracle.tile_keep32(*[float(v) for v in geo], tx, ty, 16)
+                assert bool(mine) == ref
+                n_checked += 1
+    rng = np.random.default_rng(4)
+    for _ in range(20000):
+        geo = np.float32([rng.uniform(-40, 80), rng.uniform(-40, 80), -rng.uniform(1e-3, 0.5),
+                          rng.normal(0, 0.1), -rng.uniform(1e-3, 0.5), rng.uniform(0, 1)])
+        tx, ty = int(rng.integers(0, 4)), int(rng.integers(0, 4))
+        mine = lib.cg_host_tile_keep(geo.ctypes.data_as(ctypes.c_void_p), tx, ty, 16)
+        assert bool(mine) == oracle.tile_keep32(*[float(v) for v in geo], tx, ty, 16)
+    assert n_checked > 10000

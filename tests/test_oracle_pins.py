@@ -357,12 +357,15 @@ def test_lists_sorted_and_ranges_consistent():
         assert np.all(tiles[b:e] == gt)
     assert int((r.ranges[:, 1] - r.ranges[:, 0]).sum()) == r.k_pairs
     # pairs of a tile are exactly the visible records whose rectangle holds it
+    # and that pass the tile test
     q = r.rec32
     for gt in [0, 17, 35, 63]:
         ty, tx = divmod(gt, r.tiles_x[0])
-        want = np.nonzero(q["visible"].astype(bool) & (q["x0"] <= tx) & (q["x1"] > tx) &
+        cand = np.nonzero(q["visible"].astype(bool) & (q["x0"] <= tx) & (q["x1"] > tx) &
                           (q["y0"] <= ty) & (q["y1"] > ty))[0]
-        assert sorted(r.tile_list(gt).tolist()) == want.tolist()
+        want = [int(i) for i in cand if oracle.tile_keep32(*[float(q[f][i]) for f in ("mx", "my", "h0", "h1", "h2", "o")],
+                                                              tx, ty, 16)]
+        assert sorted(r.tile_list(gt).tolist()) == want
 
 
 def test_fp32_rects_agree_with_fp64_rects():
@@ -496,3 +499,20 @@ def test_codebook_reduce_identity_total_and_general():
     one.sh_rows = sc.sh_rows[:1]
     _, d_sh_1 = oracle.codebook_reduce(one, r.rec64, g["dsigma"], g["drgb"], 1)
     assert np.allclose(d_sh_1[0], (Y[:, :, None] * g["drgb"][:, None, :]).sum(0), rtol=1e-12, atol=1e-14)
+
+
+def test_tile_test_drops_only_pairs_every_pixel_skips():
+    """Listing a Gaussian only in the tiles where alpha >= 1/255 is reachable
+    leaves the image, the final transmittance and every gradient unchanged,
+    bit for bit (each dropped pair was skipped by every pixel of its tile),
+    while dropping a good share of the pairs."""
+    sc, cams = scenes.config_single(n=20_000, k=512, width=240, height=160)
+    a = oracle.Render(sc, cams, bg=(0.2, 0.3, 0.4), cull=True)
+    b = oracle.Render(sc, cams, bg=(0.2, 0.3, 0.4), cull=False)
+    assert a.k_pairs < 0.9 * b.k_pairs
+    assert np.array_equal(a.image, b.image)
+    assert np.array_equal(a.t_final, b.t_final)
+    w = np.random.default_rng(12).normal(size=a.image.shape)
+    ga, gb = a.backward(w), b.backward(w)
+    for k in ("dpos", "dlogit", "d_sr", "d_sh"):
+        assert np.allclose(ga[k], gb[k], rtol=1e-13, atol=1e-18), k
