@@ -85,6 +85,14 @@ def make_workload(name: str):
     elif name == "tiny":
         scene, cams, _ = scenes.config_tiny()
         desc = "tiny: 1024 Gaussians, SH degree 1, 64+64 rows, 128x128"
+    elif name == "batched":
+        scene, cams = scenes.config_batched()
+        desc = ("batched: the truck-shaped scene (1.5M Gaussians) from 8 cameras at radius 4 in one launch: "
+                "4 x 1957x1091, 2 x 1280x720, 2 x 800x800")
+    elif name == "large":
+        scene, cams = scenes.config_large()
+        desc = ("large: 4M Gaussians (128-cluster mixture), SH degree 3, 16384 + 16384 rows (Zipf 1.1), "
+                "16 cameras at 1957x1091 in one launch")
     else:
         raise ValueError(name)
     target = scene.copy()
@@ -222,6 +230,38 @@ def oracle_sample(scene, cams, target_image_cpu, n_tiles_sample: int, seed: int 
     return est, wall, threads, desc, tm
 
 
+def scenes_bf16(a):
+    from paper_2509_03775_gb300 import scenes
+    return scenes.bf16_round(a)
+
+
+def oracle_views_estimate(scene, cams, n_sample: int = 2, seed: int = 3):
+    """Seconds per rendered view of the FP64 oracle on a multi-view workload:
+    for n_sample views, a random tile-aligned window of 1/16 of the view
+    (forward + backward), per-Gaussian steps in full, per-pixel and per-pair
+    steps scaled by the view / window area; averaged over the sampled views."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(len(cams), size=min(n_sample, len(cams)), replace=False)
+    per, walls = [], []
+    for v in idx:
+        cam = cams[int(v)]
+        crop = crop_camera(cam, 4, rng)
+        t0 = time.perf_counter()
+        r = oracle.Render(scene, [crop])
+        r.backward(np.full(r.image.shape, 1.0 / r.image.size))
+        walls.append(time.perf_counter() - t0)
+        tm = r.timing
+        scale = (cam.width * cam.height) / (crop.width * crop.height)
+        per.append(tm["shadow"] + tm["preprocess"] + tm["gaussian_bwd_reduce"] +
+                   scale * (tm["lists"] + tm["blend_fwd"] + tm["blend_bwd"] + tm["pair_sum"]))
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = (f"FP64 oracle on {len(idx)} of the {len(cams)} views: one random tile-aligned window of 1/16 of each "
+            f"sampled view (forward + backward), per-Gaussian steps in full, per-pixel and per-pair steps scaled "
+            f"by the area ratio; {sum(walls):.1f} s of wall time")
+    return float(np.mean(per)), threads, desc
+
+
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
@@ -238,10 +278,12 @@ def run_cg(args):
     dev = torch.device("cuda", local)
 
     scene, cams, target_scene, desc = make_workload(args.workload)
-    cams = rank_camera(cams, rank)
+    cams = rank_camera(cams, rank) if len(cams) == 1 else cams
+    bf16 = args.bf16 or args.workload == "large"
+    cbt = torch.bfloat16 if bf16 else torch.float32
     r = cg.Renderer(cams, tile=args.tile, batch=args.batch, pair_capacity=1 << 26, device=dev)
-    st = cg.SceneTensors.from_scene(scene, device=dev)
-    tst = cg.SceneTensors.from_scene(target_scene, device=dev)
+    st = cg.SceneTensors.from_scene(scene, device=dev, codebook_dtype=cbt)
+    tst = cg.SceneTensors.from_scene(target_scene, device=dev, codebook_dtype=cbt)
     target = r.forward(tst).clone()            # resident target image
     images = r.forward(st)                     # sizes the pair capacity
     pairs = r.last_pairs
@@ -267,27 +309,57 @@ def run_cg(args):
     if status != cg.CG_OK:
         raise cg.CgError("warm-up", status)
 
+    graph = None
+    launches_per_step = None
+    if args.graph:
+        # capture one step (stage events become event-record nodes); a replay
+        # launches the same kernels
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        cg.timing_enable(True)
+        graph = torch.cuda.CUDAGraph()
+        c0 = cg.launch_count()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                step()
+        launches_per_step = cg.launch_count() - c0
+        stream.wait_stream(side)
+        for _ in range(3):
+            graph.replay()
+        torch.cuda.synchronize(dev)
+
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     launches0 = cg.launch_count()
-    cg.timing_enable(True)
+    if graph is None:
+        cg.timing_enable(True)
     barrier()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        step()
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
     e1.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
     ms_total = e0.elapsed_time(e1)
     stage = cg.timing_read()
     cg.timing_enable(False)
-    launches = cg.launch_count() - launches0
+    launches = cg.launch_count() - launches0 if graph is None else launches_per_step * args.steps
+    if graph is not None:
+        # stages as recorded by the last replay
+        stage = {k: (v[0] * args.steps, v[1] * args.steps) for k, v in stage.items()}
+        status, _ = r.status()
+        if status != cg.CG_OK:
+            raise cg.CgError("graph replay", status)
     clk = clocks.stop()
     seconds = max_over_ranks(ms_total / 1000.0, dev)
-    value = whole_job_value(args.steps, world, seconds)
+    n_views = len(cams)
+    value = whole_job_value(args.steps * n_views, world, seconds)
     ms_per_step = 1000.0 * seconds / args.steps
 
     # stage breakdown and the dominant kernel's roofline
@@ -298,8 +370,9 @@ def run_cg(args):
     hbm_src = "of measured" if hbm_peak else "of fallback"
     hbm_peak = hbm_peak or HBM_PEAK_FALLBACK
     n, P = scene.n, sum(c.width * c.height for c in cams)
-    cb_bytes = scene.k_sr * 32 + scene.k_sh * 4 * 3 * nb
-    step_bytes = 200 * n + 44 * pairs + 40 * P + 3 * cb_bytes
+    R = n * n_views
+    cb_bytes = (scene.k_sr * 32 + scene.k_sh * 4 * 3 * nb) // (2 if bf16 else 1)
+    step_bytes = 200 * R + 44 * pairs + 40 * P + 3 * cb_bytes
     dominant = max((k for k in stages if stages[k]["ms_per_launch"]), key=lambda k: stages[k]["ms_per_launch"])
     dom_ms = stages[dominant]["ms_per_launch"]
     traffic = None
@@ -315,8 +388,8 @@ def run_cg(args):
                     "peak_source": "FP32 lanes 152 x 128 x 2 x 2070 MHz (nominal max clock)",
                     "work": f"{FLOPS_PER_EVAL[dominant]} FP32 ops x {ncontrib} (pixel, Gaussian) evaluations"}
     else:
-        algo = {"sort": 48 * pairs + 64 * n, "preprocess": 84 * n + cb_bytes,
-                "reduce": 68 * n + 2 * cb_bytes, "gauss_bwd": 36 * pairs + 60 * n}[dominant]
+        algo = {"sort": 48 * pairs + 64 * R, "preprocess": 84 * R + cb_bytes,
+                "reduce": 68 * R + 2 * cb_bytes, "gauss_bwd": 36 * pairs + 60 * R}[dominant]
         achieved = algo / (dom_ms / 1000.0) / 1e9
         roofline = {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1), "peak": hbm_peak,
                     "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
@@ -326,17 +399,19 @@ def run_cg(args):
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, r, scene, target, dev)
+        e2e = run_e2e(args, r, scene, target, dev, bf16)
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "renders/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "description": desc, "gaussians": n, "pixels": P,
-                   "pairs": pairs, "tile": args.tile, "sh_degree": scene.sh_degree,
-                   "codebook_rows": [scene.k_sr, scene.k_sh],
-                   "l2": "working set per step > 129 MB L2 (pair buffers alone 0.9 GB); no flush",
-                   "parallelism": f"{world} independent view(s), one per GPU"},
+        "config": {"workload": args.workload, "description": desc, "gaussians": n, "views": n_views,
+                   "pixels": P, "pairs": pairs, "tile": args.tile, "sh_degree": scene.sh_degree,
+                   "codebook_rows": [scene.k_sr, scene.k_sh], "codebook_storage": "bf16" if bf16 else "f32",
+                   "launch": "one CUDA graph replay per step" if graph is not None else "eager calls",
+                   "l2": f"working set per step > 129 MB L2 ({16 * pairs / 1e9:.2f} GB of pair keys alone); no flush",
+                   "parallelism": (f"{world} rank(s), each rendering its own view(s) of the scene"
+                                   if world > 1 else f"{n_views} view(s) in one launch on one GPU")},
         "hbm_roofline_step": {"algorithmic_bytes": step_bytes, "achieved_gbs": round(step_gbs, 1),
                               "peak_gbs": hbm_peak, "frac": round(step_gbs / hbm_peak, 4),
                               "model": "200 N + 44 K + 40 P + codebooks (read twice, gradients once)",
@@ -349,9 +424,18 @@ def run_cg(args):
         "e2e": e2e,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, wall, threads, sdesc, _ = oracle_sample(scene, cams, target.cpu().numpy().astype(np.float64),
-                                                     args.cpu_tiles)
-        out["cpu_baseline"] = {"value": round(1.0 / est, 5), "unit": "renders/s", "cores": threads,
+        osc = scene
+        if bf16:
+            osc = scene.copy()
+            osc.sr_rows = scenes_bf16(scene.sr_rows)
+            osc.sh_rows = scenes_bf16(scene.sh_rows)
+        if n_views == 1:
+            est, wall, threads, sdesc, _ = oracle_sample(osc, cams, target.cpu().numpy().astype(np.float64),
+                                                         args.cpu_tiles)
+            per_render = est
+        else:
+            per_render, threads, sdesc = oracle_views_estimate(osc, cams)
+        out["cpu_baseline"] = {"value": round(1.0 / per_render, 5), "unit": "renders/s", "cores": threads,
                                "kind": "oracle", "sample": sdesc}
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -359,7 +443,15 @@ def run_cg(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, r, scene, target, dev):
+def _host_rows(rows, bf16):
+    import torch
+    if not bf16:
+        return torch.from_numpy(rows).pin_memory()
+    from paper_2509_03775_gb300 import scenes
+    return torch.from_numpy(scenes.bf16_bits(rows).view(np.int16)).view(torch.bfloat16).pin_memory()
+
+
+def run_e2e(args, r, scene, target, dev, bf16=False):
     """Same step through the public API with the inputs in pinned host
     memory and the results read back every step."""
     import torch
@@ -369,8 +461,8 @@ def run_e2e(args, r, scene, target, dev):
         "logit": torch.from_numpy(scene.opacity_logit).pin_memory(),
         "g2sr": torch.from_numpy(scene.g2sr.view(np.int16)).pin_memory(),
         "g2sh": torch.from_numpy(scene.g2sh.view(np.int16)).pin_memory(),
-        "sr": torch.from_numpy(scene.sr_rows).pin_memory(),
-        "sh": torch.from_numpy(scene.sh_rows).pin_memory(),
+        "sr": _host_rows(scene.sr_rows, bf16),
+        "sh": _host_rows(scene.sh_rows, bf16),
         "target": target.cpu().pin_memory(),
     }
     dvc = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
@@ -477,7 +569,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["cg", "reference"], default="cg")
-    ap.add_argument("--workload", choices=["truck", "single", "tiny"], default="truck")
+    ap.add_argument("--workload", choices=["truck", "single", "tiny", "batched", "large"], default="truck")
+    ap.add_argument("--graph", action="store_true", help="replay the step as one captured CUDA graph")
+    ap.add_argument("--bf16", action="store_true", help="BF16 codebook storage (default for --workload large)")
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--cpu-tiles", type=int, default=96, help="tiles in the CPU-baseline sample")

@@ -218,8 +218,9 @@ int cg_host_tile_keep(const float geo[6], int tx, int ty, int tile);
  * of CUDA events on the caller's stream around every launch of each stage
  * below (up to 4096 launches per stage between reads).  cg_timing_read
  * waits for those events, writes the summed milliseconds and launch counts
- * per stage (host arrays of CG_STAGE_COUNT entries) and clears them.  Do not
- * enable it while capturing a CUDA graph. */
+ * per stage (host arrays of CG_STAGE_COUNT entries) and clears them.  Calls
+ * captured in a CUDA graph record their events as event-record nodes: after
+ * replays, cg_timing_read reports the last replay of each captured stage. */
 typedef enum {
   CG_STAGE_PREPROCESS = 0, /* Eq. 2 rows + projection records */
   CG_STAGE_SORT,           /* compaction, depth sort, pair emission, tile sort, ranges */

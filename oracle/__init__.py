@@ -88,10 +88,10 @@ def lib():
             L.or_sr_sigma_backward.argtypes = [_P, _P, _P]
             L.or_shadow32.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P]
             L.or_preprocess64.argtypes = [_P, _P, ctypes.c_int, _P, _P]
-            L.or_count_pairs.argtypes = [_P, ctypes.c_int64, ctypes.c_int, ctypes.c_int]
+            L.or_count_pairs.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int, _P]
             L.or_count_pairs.restype = ctypes.c_int64
             L.or_build_lists.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int64,
-                                         ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P, _P, _P]
+                                         ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]
             L.or_tile_keep32.argtypes = [ctypes.c_float] * 6 + [ctypes.c_int] * 3
             L.or_tile_keep32.restype = ctypes.c_int
             L.or_blend_forward.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P,
@@ -222,10 +222,12 @@ class Render:
     FP32 tile test (or_tile_keep32); without it, in every tile of it.  The
     default culls under the rasterizer rules (mode 0) and not for Eq. 3 as
     printed (mode 1), where every listed Gaussian contributes.
+    ``lists_in_mask`` also restricts the tile lists to the masked tiles (the
+    other tiles' lists stay empty), which bounds the work on large scenes.
     """
 
     def __init__(self, scene, cams, tile: int = 16, bg=(0.0, 0.0, 0.0), mode: int = 0,
-                 tile_mask: np.ndarray | None = None, cull: bool | None = None):
+                 tile_mask: np.ndarray | None = None, cull: bool | None = None, lists_in_mask: bool = False):
         if len(cams) > 64:
             raise ValueError("the oracle handles at most 64 views")
         L = lib()
@@ -257,15 +259,17 @@ class Render:
         t1 = time.perf_counter()
         self.timing["shadow"] = t1 - t0
         self.cull = (self.mode == 0) if cull is None else bool(cull)
-        self.k_pairs = int(L.or_count_pairs(_ptr(self.rec32), self.V * n, self.tile, int(self.cull)))
+        lmask = _ptr(self.tile_mask) if (lists_in_mask and self.tile_mask is not None) else None
+        self.k_pairs = int(L.or_count_pairs(_ptr(self.rec32), n, self.V, _ptr(self.tiles_x), _ptr(self.tile_base),
+                                            self.tile, int(self.cull), lmask))
         if self.k_pairs >= 2 ** 32:
             raise ValueError("pair count exceeds 32-bit indexing")
         self.list = np.zeros(max(self.k_pairs, 1), dtype=np.uint32)
         self.keys = np.zeros(max(self.k_pairs, 1), dtype=np.uint64)
         self.ranges = np.zeros((self.n_tiles, 2), dtype=np.uint32)
         L.or_build_lists(_ptr(self.rec32), n, self.V, _ptr(self.tiles_x), _ptr(self.tile_base),
-                         self.n_tiles, self.k_pairs, self.tile, int(self.cull), _ptr(self.list), _ptr(self.keys),
-                         _ptr(self.ranges))
+                         self.n_tiles, self.k_pairs, self.tile, int(self.cull), lmask, _ptr(self.list),
+                         _ptr(self.keys), _ptr(self.ranges))
         self.list = self.list[:self.k_pairs]
         self.keys = self.keys[:self.k_pairs]
         t2 = time.perf_counter()

@@ -538,14 +538,21 @@ static int pair_cmp(const void *a, const void *b) {
 
 /* Count of listed (tile, record) pairs: tiles of each visible record's
  * rectangle, with cull != 0 only those that pass or_tile_keep32. */
-int64_t or_count_pairs(const or_rec32 *rec32, int64_t n_rec, int tile, int cull) {
+/* list_mask (may be NULL): only tiles with a non-zero byte are listed (the
+ * lists of the other tiles are left empty); record i belongs to view i / n. */
+int64_t or_count_pairs(const or_rec32 *rec32, int n, int n_views, const int *tiles_x, const int64_t *tile_base,
+                       int tile, int cull, const uint8_t *list_mask) {
   int64_t k = 0;
-  for (int64_t i = 0; i < n_rec; ++i) {
-    const or_rec32 *r = &rec32[i];
-    if (!r->visible) continue;
-    for (int y = r->y0; y < r->y1; ++y)
-      for (int x = r->x0; x < r->x1; ++x) k += keep_tile(r, x, y, tile, cull);
-  }
+  for (int v = 0; v < n_views; ++v)
+    for (int g = 0; g < n; ++g) {
+      const or_rec32 *r = &rec32[(size_t)v * n + g];
+      if (!r->visible) continue;
+      for (int y = r->y0; y < r->y1; ++y)
+        for (int x = r->x0; x < r->x1; ++x) {
+          if (list_mask && !list_mask[tile_base[v] + (int64_t)y * tiles_x[v] + x]) continue;
+          k += keep_tile(r, x, y, tile, cull);
+        }
+    }
   return k;
 }
 
@@ -553,8 +560,8 @@ int64_t or_count_pairs(const or_rec32 *rec32, int64_t n_rec, int tile, int cull)
  * Writes list[k_pairs] (record indices v*n+g), keys[k_pairs] and
  * ranges[n_tiles][2]. */
 void or_build_lists(const or_rec32 *rec32, int n, int n_views, const int *tiles_x, const int64_t *tile_base,
-                    int64_t n_tiles, int64_t k_pairs, int tile, int cull, uint32_t *list, uint64_t *keys,
-                    uint32_t *ranges) {
+                    int64_t n_tiles, int64_t k_pairs, int tile, int cull, const uint8_t *list_mask,
+                    uint32_t *list, uint64_t *keys, uint32_t *ranges) {
   or_pair *pairs = (or_pair *)malloc(sizeof(or_pair) * (size_t)(k_pairs > 0 ? k_pairs : 1));
   int64_t k = 0;
   for (int v = 0; v < n_views; ++v)
@@ -563,8 +570,9 @@ void or_build_lists(const or_rec32 *rec32, int n, int n_views, const int *tiles_
       if (!r->visible) continue;
       for (int y = r->y0; y < r->y1; ++y)
         for (int x = r->x0; x < r->x1; ++x) {
-          if (!keep_tile(r, x, y, tile, cull)) continue;
           const uint64_t gt = (uint64_t)(tile_base[v] + (int64_t)y * tiles_x[v] + x);
+          if (list_mask && !list_mask[gt]) continue;
+          if (!keep_tile(r, x, y, tile, cull)) continue;
           pairs[k].key = (gt << 32) | r->depth_bits;
           pairs[k].rec = (uint32_t)((size_t)v * n + g);
           ++k;

@@ -42,7 +42,7 @@ struct StageTimer {
       if (cudaEventCreate(&e) != cudaSuccess) return;
       v.push_back(e);
     }
-    if (cudaEventRecord(v[2 * i], stream) != cudaSuccess) return;
+    if (record(v[2 * i], stream) != cudaSuccess) return;
     stage = st;
     s = stream;
   }
@@ -50,7 +50,15 @@ struct StageTimer {
     if (stage < 0) return;
     std::lock_guard<std::mutex> lk(g_timing.m);
     const int i = g_timing.used[stage];
-    if (cudaEventRecord(g_timing.ev[stage][2 * i + 1], s) == cudaSuccess) g_timing.used[stage] = i + 1;
+    if (record(g_timing.ev[stage][2 * i + 1], s) == cudaSuccess) g_timing.used[stage] = i + 1;
+  }
+  // Inside a stream capture the event becomes an event-record node of the
+  // graph, so each replay records it.
+  static cudaError_t record(cudaEvent_t e, cudaStream_t stream) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+      return cudaEventRecordWithFlags(e, stream, cudaEventRecordExternal);
+    return cudaEventRecord(e, stream);
   }
 };
 
@@ -125,6 +133,7 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
     return at;
   };
   L->hdr = take(sizeof(WsHeader));
+  L->l1 = take(sizeof(double) * 1024);  // fixed offset: cg_l1_loss needs no layout
   L->views = take(sizeof(ViewInfo) * CG_MAX_VIEWS);
   L->sigma3 = take(sizeof(float) * 6 * s->k_sr);
   L->geo = take(sizeof(float4) * 2 * R);
@@ -158,7 +167,6 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
   L->partials = take(sizeof(float) * std::max(6, 3 * nb) * L->chunks_cap);
   L->hist = take(sizeof(uint32_t) * (256 * L->sort_blocks_cap + 256));
   L->blocksums = take(sizeof(uint64_t) * L->scan_blocks_cap);
-  L->l1 = take(sizeof(double) * 1024);
   L->total = off;
   return CG_OK;
 }
@@ -290,16 +298,15 @@ cg_status cg_last_device_status(void* workspace, size_t ws_bytes, cg_stream_t st
 
 cg_status cg_l1_loss(const float* image, const float* target, int64_t count, float* d_image, double* loss_out,
                      void* workspace, size_t ws_bytes, cg_stream_t stream) {
+  const uint64_t l1_off = align_up(sizeof(WsHeader));
   if (!image || !target || !d_image || !loss_out || count < 1 || !workspace || !aligned(workspace, kAlign) ||
-      ws_bytes < sizeof(WsHeader))
+      ws_bytes < l1_off + 1024 * sizeof(double))
     return CG_ERR_ARG;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  WsHeader h;
-  cudaError_t e = cudaMemcpyAsync(&h, workspace, sizeof(WsHeader), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return CG_ERR_CUDA;
-  if (h.magic != kMagic || h.layout.l1 + 1024 * sizeof(double) > ws_bytes) return CG_ERR_ARG;
-  return cuda_status(launch_l1(image, target, count, d_image, loss_out, h.layout, workspace, s));
+  Layout L;
+  memset(&L, 0, sizeof(L));
+  L.l1 = l1_off;
+  return cuda_status(launch_l1(image, target, count, d_image, loss_out, L, workspace,
+                               reinterpret_cast<cudaStream_t>(stream)));
 }
 
 cg_status cg_workspace_array(void* workspace, size_t ws_bytes, cg_ws_array which, void** ptr_out,

@@ -1,0 +1,91 @@
+"""The CUDA path through torch.autograd.Function on the single-view workload
+(200k Gaussians, SH degree 3, 4096 + 4096 Zipf rows, 800x800): gradients of
+a linear loss for positions, opacity logits and both codebooks against the
+FP64 oracle's exact backward, and against central finite differences of the
+oracle's FP64 forward (under fixed decisions) on 32 sampled parameters:
+8 positions, 8 logits, 8 SR entries and 8 SH entries."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_03775_gb300 import cg, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _touched_tiles(ref, recs, pair_tile):
+    mask = np.zeros(ref.n_tiles, dtype=np.uint8)
+    mask[np.unique(pair_tile[np.isin(ref.list, np.asarray(recs, dtype=np.uint32))])] = 1
+    return mask
+
+
+def test_autograd_single_view_against_oracle_and_finite_differences():
+    scene, cams = scenes.config_single()
+    rng = np.random.default_rng(21)
+    ref = oracle.Render(scene, cams)
+    w = rng.normal(size=ref.image.shape) / ref.image.size
+    g_ref = ref.backward(w)
+
+    # GPU through the autograd Function
+    r = cg.Renderer(cams, pair_capacity=1 << 24)
+    dev = "cuda"
+    pos = torch.from_numpy(scene.pos).to(dev).requires_grad_(True)
+    logit = torch.from_numpy(scene.opacity_logit).to(dev).requires_grad_(True)
+    sr = torch.from_numpy(scene.sr_rows).to(dev).requires_grad_(True)
+    sh = torch.from_numpy(scene.sh_rows).to(dev).requires_grad_(True)
+    g2sr = torch.from_numpy(scene.g2sr.view(np.int16)).to(dev)
+    g2sh = torch.from_numpy(scene.g2sh.view(np.int16)).to(dev)
+    img = cg.render(r, pos, logit, sr, sh, g2sr, g2sh, scene.sh_degree)
+    loss = (img.double() * torch.from_numpy(w).to(dev)).sum()
+    loss.backward()
+    got = {"dpos": pos.grad.double().cpu().numpy(), "dlogit": logit.grad.double().cpu().numpy(),
+           "d_sr": sr.grad.double().cpu().numpy(), "d_sh": sh.grad.double().cpu().numpy()}
+    assert np.abs(img.detach().double().cpu().numpy() - ref.image).max() < 1e-4
+    for k in got:
+        want = g_ref[k][..., :7] if k == "d_sr" else g_ref[k]
+        have = got[k][..., :7] if k == "d_sr" else got[k]
+        floor = 1e-6 * np.abs(want).max()
+        assert np.all(np.abs(have - want) <= 1e-3 * np.abs(want) + floor), k
+
+    # finite differences of the oracle's FP64 forward, on the tiles a
+    # parameter touches, under the unperturbed decisions
+    vis = np.nonzero(ref.rec32["visible"])[0]
+    pair_tile = (ref.keys >> np.uint64(32)).astype(np.int64)
+    h = 1e-5
+    sc64 = scene.copy()
+    sc64.pos = scene.pos.astype(np.float64)
+    sc64.opacity_logit = scene.opacity_logit.astype(np.float64)
+    sc64.sr_rows = scene.sr_rows.astype(np.float64)
+    sc64.sh_rows = scene.sh_rows.astype(np.float64)
+    members_sr = np.bincount(scene.g2sr, minlength=scene.k_sr)
+    members_sh = np.bincount(scene.g2sh, minlength=scene.k_sh)
+    rows_sr = rng.choice(np.nonzero((members_sr > 0) & (members_sr < 40))[0], 8, replace=False)
+    rows_sh = rng.choice(np.nonzero((members_sh > 0) & (members_sh < 40))[0], 8, replace=False)
+    params = [("pos", (int(g), int(rng.integers(0, 3)))) for g in rng.choice(vis, 8, replace=False)]
+    params += [("logit", int(g)) for g in rng.choice(vis, 8, replace=False)]
+    params += [("sr", (int(k), int(rng.integers(0, 7)))) for k in rows_sr]
+    params += [("sh", (int(k), int(rng.integers(0, 16)), int(rng.integers(0, 3)))) for k in rows_sh]
+    assert len(params) == 32
+    for kind, idx in params:
+        if kind in ("pos", "logit"):
+            g = idx[0] if kind == "pos" else idx
+            recs = [g]
+        else:
+            row = idx[0]
+            recs = np.nonzero((scene.g2sr if kind == "sr" else scene.g2sh) == row)[0]
+        ref.tile_mask = _touched_tiles(ref, recs, pair_tile)
+
+        def L(sign):
+            s = sc64.copy()
+            arr = {"pos": s.pos, "logit": s.opacity_logit, "sr": s.sr_rows, "sh": s.sh_rows}[kind]
+            arr[idx] += sign * h
+            return float(w @ ref.replay(s))
+
+        fd = (L(+1) - L(-1)) / (2 * h)
+        key = {"pos": "dpos", "logit": "dlogit", "sr": "d_sr", "sh": "d_sh"}[kind]
+        an, gpu = g_ref[key][idx], got[key][idx]
+        noise = 64 * np.finfo(np.float64).eps * float(np.abs(w) @ np.abs(ref.image)) / (2 * h)
+        assert abs(fd - an) <= 1e-5 * abs(an) + noise, (kind, idx, fd, an)
+        assert abs(gpu - fd) <= 1e-3 * abs(fd) + noise + 1e-6 * np.abs(g_ref[key]).max(), (kind, idx, fd, gpu)
+    ref.tile_mask = None

@@ -1,0 +1,170 @@
+"""Parity at the full sizes of the benchmark workloads, in the launch
+configuration bench.py times, on outputs the oracle can compute: the oracle
+takes every Gaussian's FP32 decisions but lists, composites and
+back-propagates only a few compact blocks of tiles.
+
+Checked: every record's tile rectangle, depth key and blend record (bit
+exact); the sorted pairs and contributor counts of the sampled tiles (bit
+exact); image and final transmittance there (1e-4 / 1e-5); and the position
+and opacity gradients of the Gaussians whose rectangles lie inside the
+sampled blocks in every view (their gradients are complete)."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2509_03775_gb300 import cg, scenes
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _block_mask(tiles_x, tile_base, n_tiles, blocks):
+    """blocks: (view, tile x0, tile y0, width, height)."""
+    m = np.zeros(n_tiles, dtype=np.uint8)
+    for v, x0, y0, w, h in blocks:
+        tx = int(tiles_x[v])
+        for ty in range(y0, y0 + h):
+            m[tile_base[v] + ty * tx + x0: tile_base[v] + ty * tx + x0 + w] = 1
+    return m
+
+
+def _central_blocks(cams, size=10):
+    """Two blocks of tiles per view: one at the centre, a smaller one off it."""
+    out = []
+    for v, c in enumerate(cams):
+        tx, ty = -(-c.width // 16), -(-c.height // 16)
+        out.append((v, max(0, tx // 2 - size // 2), max(0, ty // 2 - size // 2), min(size, tx), min(size, ty)))
+        out.append((v, max(0, tx // 4 - size // 4), max(0, ty // 3 - size // 4), min(size // 2, tx), min(size // 2, ty)))
+    return out
+
+
+def _run(scene, cams, blocks, bf16=False, errors_key=None, check_grads=True):
+    osc = scene
+    if bf16:
+        osc = scene.copy()
+        osc.sr_rows = scenes.bf16_round(scene.sr_rows)
+        osc.sh_rows = scenes.bf16_round(scene.sh_rows)
+    tiles_x = np.array([-(-c.width // 16) for c in cams])
+    tiles_y = np.array([-(-c.height // 16) for c in cams])
+    tile_base = np.concatenate([[0], np.cumsum(tiles_x * tiles_y)[:-1]]).astype(np.int64)
+    mask = _block_mask(tiles_x, tile_base, int((tiles_x * tiles_y).sum()), blocks)
+    ref = oracle.Render(osc, cams, tile_mask=mask, lists_in_mask=True)
+    rng = np.random.default_rng(31)
+    d_image = rng.normal(size=ref.image.shape) / ref.image.size
+    g = ref.backward(d_image)
+
+    r = cg.Renderer(cams, pair_capacity=1 << 26)
+    st = cg.SceneTensors.from_scene(scene, codebook_dtype=torch.bfloat16 if bf16 else torch.float32)
+    img = r.forward(st)
+    d_pos, d_logit = r.backward(torch.from_numpy(d_image.astype(np.float32)).cuda())
+    r.codebook_reduce()
+    torch.cuda.synchronize()
+    q = ref.rec32
+    vis = q["visible"].astype(bool)
+    rect = r.array(cg.WS_RECT, torch.int16, 4).cpu().numpy().view(np.uint16).reshape(-1, 4)
+    assert np.array_equal(rect, np.stack([q["x0"], q["y0"], q["x1"], q["y1"]], 1).astype(np.uint16))
+    depth = r.array(cg.WS_DEPTH, torch.int32).cpu().numpy().view(np.uint32)
+    assert np.array_equal(depth[vis], q["depth_bits"][vis])
+    geo = r.array(cg.WS_GEO, torch.float32, 8).cpu().numpy().reshape(-1, 8)
+    for j, f in enumerate(["mx", "my", "h0", "h1", "h2", "o"]):
+        assert np.array_equal(geo[vis, j].view(np.uint32), q[f][vis].view(np.uint32)), f
+    # pairs and ranges of the sampled tiles
+    pairs = r.array(cg.WS_PAIRS, torch.int64).cpu().numpy().view(np.uint64)
+    ranges = r.array(cg.WS_RANGES, torch.int32, 2).cpu().numpy().view(np.uint32).reshape(-1, 2)
+    sel = np.nonzero(mask)[0]
+    for gt in sel:
+        b, e = ranges[gt]
+        ob, oe = ref.ranges[gt]
+        assert e - b == oe - ob, gt
+        assert np.array_equal((pairs[b:e] & np.uint64((1 << 26) - 1)).astype(np.uint32), ref.list[ob:oe]), gt
+    # pixels of the sampled tiles
+    img_g = img.cpu().numpy().astype(np.float64)
+    nc_g = r.array(cg.WS_NCONTRIB, torch.int32).cpu().numpy().view(np.uint32)
+    tf_g = r.array(cg.WS_TFINAL, torch.float32).cpu().numpy()
+    pix = []
+    for v, c in enumerate(cams):
+        txv = int(tiles_x[v])
+        ys, xs = np.mgrid[0:c.height, 0:c.width]
+        gt = tile_base[v] + (ys // 16) * txv + xs // 16
+        sel_pix = np.nonzero(mask[gt.ravel()])[0]
+        pix.append(ref.pix_base[v] + sel_pix)
+    pix = np.concatenate(pix)
+    assert np.array_equal(nc_g[pix], ref.n_contrib[pix].astype(np.uint32))
+    assert np.abs(tf_g[pix] - ref.t_final[pix]).max() < 1e-5
+    hw_err = []
+    for v, c in enumerate(cams):
+        base, hw = 3 * ref.pix_base[v], c.width * c.height
+        local = pix[(pix >= ref.pix_base[v]) & (pix < ref.pix_base[v] + hw)] - ref.pix_base[v]
+        for ch in range(3):
+            hw_err.append(np.abs(img_g[base + ch * hw + local] - ref.image[base + ch * hw + local]).max(initial=0))
+    img_err = float(max(hw_err))
+    assert img_err < 1e-4
+    errs = {"image_max_abs": img_err, "sampled_tiles": int(mask.sum())}
+    if not check_grads:
+        _dump(errs, errors_key)
+        return errs
+    # complete Gaussians: rectangle inside the sampled tiles in every view
+    n = scene.n
+    complete = np.ones(n, dtype=bool)
+    any_vis = np.zeros(n, dtype=bool)
+    for v in range(len(cams)):
+        qv = q[v * n:(v + 1) * n]
+        ok_v = qv["visible"].astype(bool)
+        tx, ty = int(tiles_x[v]), int(tiles_y[v])
+        grid = mask[tile_base[v]:tile_base[v] + tx * ty].reshape(ty, tx).astype(np.int64)
+        integ = np.zeros((ty + 1, tx + 1), dtype=np.int64)
+        integ[1:, 1:] = grid.cumsum(0).cumsum(1)
+        x0, y0 = qv["x0"].astype(np.int64), qv["y0"].astype(np.int64)
+        x1, y1 = qv["x1"].astype(np.int64), qv["y1"].astype(np.int64)
+        covered = integ[y1, x1] - integ[y0, x1] - integ[y1, x0] + integ[y0, x0]
+        inside = covered == (x1 - x0) * (y1 - y0)
+        complete &= ~ok_v | inside
+        any_vis |= ok_v
+    complete &= any_vis
+    assert complete.sum() > 100
+    dp = d_pos.cpu().numpy().astype(np.float64)[complete]
+    dl = d_logit.cpu().numpy().astype(np.float64)[complete]
+    for name, have, want in (("d_pos", dp, g["dpos"][complete]), ("d_logit", dl, g["dlogit"][complete])):
+        floor = 1e-6 * np.abs(want).max()
+        err = np.abs(have - want)
+        assert np.all(err <= 1e-3 * np.abs(want) + floor), name
+        errs[name + "_max_rel"] = float((err / (np.abs(want) + floor)).max())
+    errs["complete_gaussians"] = int(complete.sum())
+    _dump(errs, errors_key)
+    return errs
+
+
+def _dump(errs, key):
+    if key:
+        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+        with open(os.path.join(ROOT, "gpurun_out", f"fullsize_{key}.json"), "w") as f:
+            json.dump(errs, f)
+
+
+def test_truck_full_size_sampled():
+    scene, cams = scenes.config_truck()
+    _run(scene, cams, _central_blocks(cams), errors_key="truck")
+
+
+def test_batched_full_size_sampled():
+    """All eight views in one launch (images, discrete outputs); gradients
+    of one 1280x720 view rendered alone (a Gaussian is complete only in the
+    views whose sampled blocks contain its rectangle)."""
+    scene, cams = scenes.config_batched()
+    blocks = [b for b in _central_blocks(cams) if b[0] in (0, 4, 6)]
+    _run(scene, cams, blocks, errors_key="batched", check_grads=False)
+    _run(scene, [cams[4]], _central_blocks([cams[4]]), errors_key="batched_view4")
+
+
+def test_large_bf16_four_view_subset_sampled():
+    """The 4M-Gaussian BF16-codebook scene: views 0, 4, 8 and 12 in one
+    launch (images, discrete outputs), and view 0 alone with gradients."""
+    scene, cams = scenes.config_large()
+    sub = [cams[i] for i in (0, 4, 8, 12)]
+    _run(scene, sub, _central_blocks(sub), bf16=True, errors_key="large_bf16_4views", check_grads=False)
+    _run(scene, sub[:1], _central_blocks(sub[:1]), bf16=True, errors_key="large_bf16_view0")

@@ -1,0 +1,99 @@
+"""The whole training-step path captured once in a CUDA graph and replayed:
+bitwise equal to the eager calls, follows in-place scene updates, and
+reports a pair-capacity overflow through the status word."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2509_03775_gb300 import cg, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(scene, cams, target_scene, **kw):
+    r = cg.Renderer(cams, **kw)
+    st = cg.SceneTensors.from_scene(scene)
+    target = r.forward(cg.SceneTensors.from_scene(target_scene)).clone()
+    images = r.forward(st)        # sizes the workspace outside the capture
+    bufs = {
+        "images": images, "d_images": torch.empty_like(images),
+        "loss": torch.empty((1,), dtype=torch.float64, device="cuda"),
+        "d_pos": torch.empty((scene.n, 3), device="cuda"), "d_logit": torch.empty((scene.n,), device="cuda"),
+        "d_sr": torch.empty((scene.k_sr, 8), device="cuda"),
+        "d_sh": torch.empty((scene.k_sh, (scene.sh_degree + 1) ** 2, 3), device="cuda"),
+    }
+
+    def step():
+        r.forward(st, images=bufs["images"], check=False)
+        r.l1_loss(bufs["images"], target, d_images=bufs["d_images"], loss=bufs["loss"])
+        r.backward(bufs["d_images"], d_pos=bufs["d_pos"], d_logit=bufs["d_logit"])
+        r.codebook_reduce(d_sr=bufs["d_sr"], d_sh=bufs["d_sh"])
+
+    return r, st, bufs, step
+
+
+def _snapshot(bufs):
+    return {k: v.detach().cpu().clone() for k, v in bufs.items()}
+
+
+def test_graph_replay_matches_eager_and_follows_updates():
+    scene, _ = scenes.config_single(n=30_000, k=512, width=8, height=8)
+    rng = np.random.default_rng(5)
+    dirs = scenes.fibonacci_dirs(3, rng)
+    cams = [scenes.look_at(3.0 * d, w, h) for d, (w, h) in zip(dirs, [(200, 120), (96, 96), (64, 40)])]
+    target = scene.copy()
+    target.pos = (scene.pos + rng.normal(0, 0.01, scene.pos.shape)).astype(np.float32)
+    r, st, bufs, step = _setup(scene, cams, target, pair_capacity=1 << 22)
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step()                   # eager reference
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    eager = _snapshot(bufs)
+
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    for k in bufs:
+        bufs[k].zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert r.status()[0] == cg.CG_OK
+    replay = _snapshot(bufs)
+    for k in eager:
+        assert torch.equal(eager[k], replay[k]), k
+
+    # an in-place update of the scene (as an optimizer step would do) is seen
+    # by the next replay, and equals the eager result for the new scene
+    with torch.no_grad():
+        st.pos.add_(torch.from_numpy(rng.normal(0, 1e-3, scene.pos.shape).astype(np.float32)).cuda())
+        st.opacity_logit.mul_(0.9)
+    g.replay()
+    torch.cuda.synchronize()
+    after = _snapshot(bufs)
+    with torch.cuda.stream(s):
+        step()
+    torch.cuda.synchronize()
+    eager2 = _snapshot(bufs)
+    assert not torch.equal(after["images"], replay["images"])
+    for k in eager2:
+        assert torch.equal(eager2[k], after[k]), k
+
+
+def test_graph_reports_capacity_overflow():
+    scene, cams, target = scenes.config_tiny()
+    r, st, bufs, step = _setup(scene, cams, target, pair_capacity=8000)
+    _, pairs = r.status()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    g.replay()
+    assert r.status()[0] == cg.CG_OK
+    # make every Gaussian ten times larger: more pairs than the capacity
+    with torch.no_grad():
+        st.sr_rows[:, :3].add_(2.3)
+    g.replay()
+    status, need = r.status()
+    assert status == cg.CG_ERR_CAPACITY and need > 8000 > pairs
