@@ -281,9 +281,16 @@ def run_cg(args):
     cams = rank_camera(cams, rank) if len(cams) == 1 else cams
     bf16 = args.bf16 or args.workload == "large"
     cbt = torch.bfloat16 if bf16 else torch.float32
-    r = cg.Renderer(cams, tile=args.tile, batch=args.batch, pair_capacity=1 << 26, device=dev)
     st = cg.SceneTensors.from_scene(scene, device=dev, codebook_dtype=cbt)
     tst = cg.SceneTensors.from_scene(target_scene, device=dev, codebook_dtype=cbt)
+    shape = {"tile": args.tile, "batch": args.batch}
+    tuned = None
+    if args.autotune or args.autotune_tiles:
+        from paper_2509_03775_gb300 import autotune
+        tiles = (8, 16, 32) if args.autotune_tiles else (args.tile,)
+        shape = autotune.tune(st, cams, tiles=tiles, pair_capacity=1 << 26)
+        tuned = dict(shape)
+    r = cg.Renderer(cams, pair_capacity=1 << 26, device=dev, **shape)
     target = r.forward(tst).clone()            # resident target image
     images = r.forward(st)                     # sizes the pair capacity
     pairs = r.last_pairs
@@ -406,7 +413,9 @@ def run_cg(args):
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "description": desc, "gaussians": n, "views": n_views,
-                   "pixels": P, "pairs": pairs, "tile": args.tile, "sh_degree": scene.sh_degree,
+                   "pixels": P, "pairs": pairs, "tile": r.tile, "sh_degree": scene.sh_degree,
+                   "launch_shape": {"batch": r.batch, "batch_bwd": r.batch_bwd, "ppt_fwd": r.ppt_fwd,
+                                    "ppt_bwd": r.ppt_bwd, "autotuned": tuned is not None},
                    "codebook_rows": [scene.k_sr, scene.k_sh], "codebook_storage": "bf16" if bf16 else "f32",
                    "launch": "one CUDA graph replay per step" if graph is not None else "eager calls",
                    "l2": f"working set per step > 129 MB L2 ({16 * pairs / 1e9:.2f} GB of pair keys alone); no flush",
@@ -572,6 +581,9 @@ def main():
     ap.add_argument("--workload", choices=["truck", "single", "tiny", "batched", "large"], default="truck")
     ap.add_argument("--graph", action="store_true", help="replay the step as one captured CUDA graph")
     ap.add_argument("--bf16", action="store_true", help="BF16 codebook storage (default for --workload large)")
+    ap.add_argument("--autotune", action="store_true", help="tune the blend launch shapes first (cached)")
+    ap.add_argument("--autotune-tiles", action="store_true",
+                    help="also tune the tile size (8/16/32; it changes which tiles list a Gaussian)")
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--batch", type=int, default=0)
     ap.add_argument("--cpu-tiles", type=int, default=96, help="tiles in the CPU-baseline sample")

@@ -1,0 +1,113 @@
+"""Autotuner for the blend kernels' launch shapes (and optionally the tile
+size) of one workload, with results cached in a JSON file.
+
+The shared-memory batch and the pixels per thread of the forward and
+backward blend kernels change speed only, never results.  The tile size (8,
+16 or 32 pixels) is part of the image definition (it decides which tiles
+list a Gaussian), so it is searched only when the caller allows it.
+
+For each tile size the tuner renders the workload with every forward shape
+and every backward shape (the two kernels are timed in the same steps by the
+library's stage events), keeps the fastest of each, then times whole steps
+with the winners; the tile size with the fastest step wins.  The cache key
+is the GPU name, the scene size and the camera resolutions.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import torch
+
+from . import cg
+
+FWD_BATCH = (64, 128, 256)
+BWD_BATCH = (32, 64, 128)
+PPT = {8: (1, 2), 16: (1, 2, 4), 32: (4,)}
+
+
+def default_cache() -> str:
+    base = os.environ.get("XDG_CACHE_HOME", os.path.join(os.path.expanduser("~"), ".cache"))
+    return os.path.join(base, "cg_autotune.json")
+
+
+def cache_key(scene: cg.SceneTensors, cams, tiles) -> str:
+    name = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    res = ",".join(f"{c.width}x{c.height}" for c in cams)
+    dt = "bf16" if scene.sr_rows.dtype == torch.bfloat16 else "f32"
+    return (f"{name}|n={scene.n}|d={scene.sh_degree}|k={scene.sr_rows.shape[0]},{scene.sh_rows.shape[0]}|{dt}"
+            f"|{res}|tiles={','.join(str(t) for t in tiles)}")
+
+
+def _step(r: cg.Renderer, scene, d_images):
+    r.forward(scene, check=False)
+    r.backward(d_images)
+    r.codebook_reduce()
+
+
+def _time_steps(r, scene, d_images, reps):
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _step(r, scene, d_images)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        _step(r, scene, d_images)
+    ev1.record()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / reps
+
+
+def tune(scene: cg.SceneTensors, cams, tiles=(16,), reps: int = 3, cache_path: str | None = None,
+         pair_capacity: int = 1 << 24, verbose: bool = False) -> dict:
+    """Returns Renderer keyword arguments (tile, batch, batch_bwd, ppt_fwd,
+    ppt_bwd) for the fastest step, from the cache when present."""
+    path = cache_path or default_cache()
+    key = cache_key(scene, cams, tiles)
+    cache = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    if key in cache:
+        return dict(cache[key]["config"])
+    best = None
+    for tile in tiles:
+        r = cg.Renderer(cams, tile=tile, pair_capacity=pair_capacity)
+        img = r.forward(scene)
+        d_images = torch.full_like(img, 1.0 / img.numel())
+        fwd_c = [(b, p) for b in FWD_BATCH for p in PPT[tile]]
+        bwd_c = [(b, p) for b in BWD_BATCH for p in PPT[tile]]
+        fwd_t, bwd_t = {}, {}
+        for i in range(max(len(fwd_c), len(bwd_c))):
+            f, b = fwd_c[i % len(fwd_c)], bwd_c[i % len(bwd_c)]
+            r.batch, r.ppt_fwd = f
+            r.batch_bwd, r.ppt_bwd = b
+            _step(r, scene, d_images)
+            torch.cuda.synchronize()
+            cg.timing_enable(True)
+            for _ in range(reps):
+                _step(r, scene, d_images)
+            st = cg.timing_read()
+            cg.timing_enable(False)
+            fwd_t.setdefault(f, st["blend_fwd"][0] / max(1, st["blend_fwd"][1]))
+            bwd_t.setdefault(b, st["blend_bwd"][0] / max(1, st["blend_bwd"][1]))
+        f_best = min(fwd_t, key=fwd_t.get)
+        b_best = min(bwd_t, key=bwd_t.get)
+        r.batch, r.ppt_fwd = f_best
+        r.batch_bwd, r.ppt_bwd = b_best
+        step_ms = _time_steps(r, scene, d_images, reps)
+        cfg = {"tile": tile, "batch": f_best[0], "ppt_fwd": f_best[1], "batch_bwd": b_best[0], "ppt_bwd": b_best[1]}
+        if verbose:
+            print(f"tile {tile}: fwd {fwd_t} bwd {bwd_t} -> {cfg} step {step_ms:.3f} ms")
+        if best is None or step_ms < best[0]:
+            best = (step_ms, cfg)
+        del r
+    cache[key] = {"config": best[1], "step_ms": round(best[0], 4)}
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+    return dict(best[1])

@@ -1,0 +1,28 @@
+"""The autotuner returns a valid launch configuration, caches it, and the
+tuned configuration renders the oracle's image."""
+import json
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_03775_gb300 import autotune, cg, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def test_autotune_valid_cached_and_exact(tmp_path):
+    scene, cams, _ = scenes.config_tiny()
+    st = cg.SceneTensors.from_scene(scene)
+    path = str(tmp_path / "tune.json")
+    cfg = autotune.tune(st, cams, tiles=(8, 16), reps=1, cache_path=path)
+    assert cfg["tile"] in (8, 16)
+    assert cfg["ppt_fwd"] in autotune.PPT[cfg["tile"]] and cfg["ppt_bwd"] in autotune.PPT[cfg["tile"]]
+    assert cfg["batch"] in autotune.FWD_BATCH and cfg["batch_bwd"] in autotune.BWD_BATCH
+    with open(path) as f:
+        assert autotune.cache_key(st, cams, (8, 16)) in json.load(f)
+    assert autotune.tune(st, cams, tiles=(8, 16), reps=1, cache_path=path) == cfg
+    r = cg.Renderer(cams, **cfg)
+    img = r.forward(st).cpu().numpy()
+    ref = oracle.Render(scene, cams, tile=cfg["tile"])
+    assert np.abs(img - ref.image).max() < 1e-4
