@@ -38,10 +38,11 @@ FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
 
 # Algorithmic FP32 operations per (pixel, listed Gaussian) evaluation of the
-# blend kernels (an FMA counts 2): the quadratic form of Eq. 1 (10), exp (19),
-# alpha and the Eq. 3 update (10) in the forward; the same recomputation (30)
-# plus the Eq. 3 derivatives (55) in the backward.
-FLOPS_PER_EVAL = {"blend_fwd": 39, "blend_bwd": 85}
+# blend kernels (an FMA counts 2, an exponential 1): the quadratic form of
+# Eq. 1 (10), exp (1), alpha and the Eq. 3 update with three colour FMAs (10)
+# in the forward; the same recomputation with alpha (12) plus the derivatives
+# of Eq. 3 and of the quadratic form (56) in the backward.
+FLOPS_PER_EVAL = {"blend_fwd": 21, "blend_bwd": 68}
 
 # DRAM bytes per launch measured by ncu for a kernel, keyed by the SHA-256 of
 # the kernel's source file at capture time (summaries under profiles/).  A
@@ -423,7 +424,7 @@ def run_cg(args):
                                    if world > 1 else f"{n_views} view(s) in one launch on one GPU")},
         "hbm_roofline_step": {"algorithmic_bytes": step_bytes, "achieved_gbs": round(step_gbs, 1),
                               "peak_gbs": hbm_peak, "frac": round(step_gbs / hbm_peak, 4),
-                              "model": "200 N + 44 K + 40 P + codebooks (read twice, gradients once)",
+                              "model": "200 R + 44 K + 40 P + codebooks (read twice, gradients once); R = views x Gaussians",
                               "note": hbm_src},
         "roofline": roofline,
         "stages_ms": {k: (round(v["ms_per_launch"], 4) if v["ms_per_launch"] else None) for k, v in stages.items()},
