@@ -4,15 +4,15 @@
  * CUDA kernels of that library.
  *
  * The method (ContraGS, arXiv 2509.03775):
- *   State S = {G, C} (Sec. 3.1).  A Gaussian g_i = {p_i, o_i, g2sr_i, g2sh_i}
+ *   State S = {G, C} (Sec. 4.1).  A Gaussian g_i = {p_i, o_i, g2sr_i, g2sh_i}
  *   holds a position, an opacity and two integer indices; its scale and
  *   rotation come from row g2sr_i of the SR codebook (its scales followed by
  *   its quaternion, Fig. 4) and its SH colour coefficients from row g2sh_i of
  *   the SH codebook.  The image I_P(G, C) of camera P (the posterior of
- *   Sec. 3.2 is a function of it) is Eq. 3 over Gaussians whose density is
+ *   Sec. 4.2 is a function of it) is Eq. 3 over Gaussians whose density is
  *   Eq. 1 with the covariance of Eq. 2, projected onto the image plane.
  *   Training updates p, o, SH and SR with the gradient of the loss
- *   (the differentiable set S_diff of Sec. 3.4, and the SGLD steps of Appendix A.1); a codebook
+ *   (the differentiable set S_diff of Sec. 4.4, and the SGLD steps of Appendix A.1); a codebook
  *   row's gradient is the sum over the Gaussians that index it.
  *
  * Conventions shared by every call:
@@ -73,7 +73,7 @@ typedef struct {
   float near_z;
 } cg_camera;
 
-/* The state S = {G, C} of Sec. 3.1.  Device pointers:
+/* The state S = {G, C} of Sec. 4.1.  Device pointers:
  *   pos            [n][3] float
  *   opacity_logit  [n] float          o_i = sigmoid(logit_i)
  *   g2sr, g2sh     [n] uint16
@@ -118,7 +118,7 @@ typedef struct {
  * with these options.  Returns 0 for invalid arguments. */
 size_t cg_workspace_bytes(const cg_scene *scene, const cg_camera *cams, int n_views, const cg_opts *opts);
 
-/* Forward render I_P(G, C) of every view (Eqs. 1-3, Sec. 3.1 indirection):
+/* Forward render I_P(G, C) of every view (Eqs. 1-3, Sec. 4.1 indirection):
  * codebook gather, Eq. 2, EWA projection, SH colour, tile/depth keys (a
  * Gaussian is listed in the tiles of its 3-sigma rectangle where alpha can
  * reach 1/255), radix sort, per-tile front-to-back compositing.

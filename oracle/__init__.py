@@ -12,7 +12,7 @@ with ctypes and strings the steps together in the order of the method:
   Eq. 2 per SR row -> EWA projection and SH colour per (view, Gaussian)
   -> tile lists ordered by FP32 depth -> Eq. 3 per pixel
   -> exact backward of Eq. 3 -> backward of projection / colour / opacity
-  -> codebook rows as sums over the Gaussians that index them (Sec. 3.1).
+  -> codebook rows as sums over the Gaussians that index them (Sec. 4.1).
 
 Integer outcomes (culling, tile rectangles, depth keys, skip / clamp /
 termination of an evaluation, colour clamp) are decided in FP32 with the
@@ -32,6 +32,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "mcmc32.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -41,10 +42,11 @@ CFLAGS = ["-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-s
 
 
 def build(force: bool = False) -> str:
-    """Compile ``oracle.c`` into ``liboracle.so`` (gcc, no CUDA)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile ``oracle.c`` and ``mcmc32.c`` into ``liboracle.so`` (gcc, no CUDA)."""
+    stale = not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(f) for f in _SRCS)
+    if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
+        subprocess.check_call(["gcc", *CFLAGS, *_SRCS, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -81,6 +83,10 @@ def lib():
             L = ctypes.CDLL(_LIB)
             L.or_e32.argtypes = [ctypes.c_float]
             L.or_e32.restype = ctypes.c_float
+            L.or_normals32.argtypes = [ctypes.c_int64, _P, _P]
+            L.or_log32_batch.argtypes = [ctypes.c_int64, _P, _P]
+            L.or_sincos2pi32_batch.argtypes = [ctypes.c_int64, _P, _P, _P]
+            L.or_e32_batch.argtypes = [ctypes.c_int64, _P, _P]
             L.or_sh_consts32.argtypes = [_P]
             L.or_sh_basis.argtypes = [ctypes.c_int, _P, _P, _P]
             L.or_sr_sigma.argtypes = [_P, _P]

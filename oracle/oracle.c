@@ -7,7 +7,7 @@
  *
  * What it computes (ContraGS, arXiv 2509.03775):
  *   - state S = {G, C}, g_i = {p_i, o_i, g2sr_i, g2sh_i}, C = {SH, SR}
- *     (Sec. 3.1): every Gaussian reads its scale+rotation from SR[g2sr_i]
+ *     (Sec. 4.1): every Gaussian reads its scale+rotation from SR[g2sr_i]
  *     and its SH colour coefficients from SH[g2sh_i];
  *   - Eq. 2: Sigma = R(q) S S^T R(q)^T;
  *   - Eq. 1 projected onto the image plane (Sec. 2.1 defines alpha_i as that
@@ -88,7 +88,7 @@ typedef struct {
 
 /* ------------------------------------------------------------------------ */
 /* Real spherical harmonics, degree <= 3 (the colour c_i of Sec. 2.1 and the  */
-/* SH codebook rows of Sec. 3.1).  Constants from their closed forms.         */
+/* SH codebook rows of Sec. 4.1).  Constants from their closed forms.         */
 /* ------------------------------------------------------------------------ */
 
 static double sh_c0(void) { return 0.5 * sqrt(1.0 / M_PI); }
@@ -901,7 +901,7 @@ void or_preprocess_backward(const or_scene *s, const or_camera *cams, int n_view
 
 /* ------------------------------------------------------------------------ */
 /* Codebook gradients: a row's gradient is the sum over the Gaussians that   */
-/* index it (g2sr / g2sh, Sec. 3.1), pushed through Eq. 2 for SR rows and    */
+/* index it (g2sr / g2sh, Sec. 4.1), pushed through Eq. 2 for SR rows and    */
 /* through the SH basis for SH rows.                                         */
 /* ------------------------------------------------------------------------ */
 

@@ -347,7 +347,7 @@ class Renderer:
 
 class CodebookRender(torch.autograd.Function):
     """images = I_P(G, C) with gradients for positions, opacity logits and
-    both codebooks (the differentiable set S_diff of Sec. 3.4)."""
+    both codebooks (the differentiable set S_diff of Sec. 4.4)."""
 
     @staticmethod
     def forward(ctx, renderer: Renderer, pos, opacity_logit, sr_rows, sh_rows, g2sr, g2sh, sh_degree: int):

@@ -1,7 +1,7 @@
 // k_grad.cu -- per-Gaussian backward (pair slots -> projection, colour and
 // opacity chain rule) and the deterministic codebook reduction: a row's
 // gradient is the sum over the Gaussians that index it (g2sr / g2sh of
-// Sec. 3.1), pushed through Eq. 2 for SR rows and through the SH basis for
+// Sec. 4.1), pushed through Eq. 2 for SR rows and through the SH basis for
 // SH rows.  Every sum runs in a fixed order; no floating-point atomics.
 #include <algorithm>
 

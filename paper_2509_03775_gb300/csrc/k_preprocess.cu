@@ -1,6 +1,6 @@
 // k_preprocess.cu -- workspace setup, Eq. 2 per SR row, and the per (view,
 // Gaussian) projection record: gather of the Gaussian's codebook rows
-// (Sec. 3.1), EWA projection of Eq. 1 onto the image plane, SH colour,
+// (Sec. 4.1), EWA projection of Eq. 1 onto the image plane, SH colour,
 // 3-sigma tile rectangle and FP32 depth key.
 #include <algorithm>
 

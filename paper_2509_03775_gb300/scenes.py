@@ -2,11 +2,11 @@
 
 This module only draws inputs: Gaussian records g_i = {p_i, o_i, g2sr_i, g2sh_i}
 and the two codebooks C = {SR, SH} of the codebook-compressed state S = {G, C}
-(ContraGS, Sec. 3.1), plus pinhole cameras.  It holds none of the rendering
+(ContraGS, Sec. 4.1), plus pinhole cameras.  It holds none of the rendering
 arithmetic, so the CPU oracle and the CUDA path can both consume it.
 
 The paper trains on Tanks&Temples, MipNeRF360, Deep Blending and Blender
-(Sec. 4.1).  Those datasets are not used; these scenes stand in for them with
+(Sec. 5.1).  Those datasets are not used; these scenes stand in for them with
 the sizes and value distributions of the five workloads listed below.  Every
 array is produced by ``numpy.random.default_rng(1000 + config_index)``.
 

@@ -29,7 +29,7 @@ def test_e32_accuracy_and_range():
 
 
 # ---------------------------------------------------------------------------
-# SH basis (colour of Sec. 2.1, SH codebook rows of Sec. 3.1)
+# SH basis (colour of Sec. 2.1, SH codebook rows of Sec. 4.1)
 # ---------------------------------------------------------------------------
 
 
