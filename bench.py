@@ -408,6 +408,10 @@ def run_cg(args):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, r, scene, target, dev, bf16)
+    next_rows = None
+    if not args.no_next_rows and rank == 0:
+        next_rows = run_next_rows(args, r, st, scene, cams, images, target, (d_pos, d_logit, d_sr, d_sh), dev, bf16,
+                                  hbm_peak, hbm_src)
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "renders/s", "n_gpus": world, "steps": args.steps,
@@ -432,6 +436,7 @@ def run_cg(args):
         "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": e2e,
+        "next_rows": next_rows,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         osc = scene
@@ -510,6 +515,123 @@ def run_e2e(args, r, scene, target, dev, bf16=False):
     d2h = sum(v.numel() * v.element_size() for v in outs_host.values())
     return {"value": round(args.steps / sec, 3), "unit": "renders/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h)}
+
+
+def _time_calls(fn, reps, stream, prepare=None):
+    """Mean device milliseconds of fn(): reps calls (each after prepare(), if
+    given) captured in one CUDA graph, whose replay is timed with CUDA events
+    on the launching stream; the time of a graph of the prepare() calls alone
+    is subtracted.  Graph replay keeps host launch latency out of the number."""
+    import torch
+
+    def graph_ms(body):
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                for _ in range(reps):
+                    body()
+        stream.wait_stream(side)
+        g.replay()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    def both():
+        if prepare is not None:
+            prepare()
+        fn()
+
+    total = graph_ms(both)
+    if prepare is not None:
+        total -= graph_ms(prepare)
+    return total / reps
+
+
+def run_next_rows(args, r, st, scene, cams, images, target, grads, dev, bf16, hbm_peak, hbm_src):
+    """The reconstruction loss (Eq. 4), the SGLD update and the codebook split
+    and merge, each timed alone on the bench workload after the main step."""
+    import torch
+    from paper_2509_03775_gb300 import cg
+    stream = torch.cuda.current_stream(dev)
+    reps = 20
+    out = {}
+    m = images.numel()
+    loss_fn = cg.ReconLoss(cams, 0.2, device=dev)
+    lbuf = torch.empty(3, dtype=torch.float64, device=dev)
+    dbuf = torch.empty_like(images)
+    loss_fn(images, target, d_images=dbuf, loss=lbuf)
+    ms = _time_calls(lambda: loss_fn(images, target, d_images=dbuf, loss=lbuf), reps, stream)
+    algo = 12 * m
+    out["recon_loss"] = {"ms": round(ms, 4), "values": m, "algorithmic_bytes": algo,
+                         "achieved_gbs": round(algo / ms / 1e6, 1), "peak_gbs": hbm_peak,
+                         "frac": round(algo / ms / 1e6 / hbm_peak, 4), "peak_source": hbm_src,
+                         "bytes_model": "image and target read, gradient written: 12 B per value",
+                         "lambda_ssim": 0.2}
+    # SGLD on a copy of the scene's tensors (tiny step sizes)
+    cp = cg.SceneTensors(st.pos.clone(), st.opacity_logit.clone(), st.g2sr, st.g2sh, st.sr_rows.clone(),
+                         st.sh_rows.clone(), st.sh_degree)
+    eps = {"pos": 1e-10, "logit": 1e-10, "sr": 1e-10, "sh": 1e-10}
+    counter = [0]
+
+    def sgld():
+        counter[0] += 1
+        cg.sgld_update(cp, *grads, eps, 1234, counter[0])
+
+    sgld()
+    ms = _time_calls(sgld, reps, stream)
+    nb = (scene.sh_degree + 1) ** 2
+    f32_vals = 4 * scene.n
+    cb_vals = 8 * scene.k_sr + 3 * nb * scene.k_sh
+    algo = 12 * f32_vals + (8 if bf16 else 12) * cb_vals
+    out["sgld_update"] = {"ms": round(ms, 4), "values": f32_vals + cb_vals, "algorithmic_bytes": algo,
+                          "achieved_gbs": round(algo / ms / 1e6, 1), "peak_gbs": hbm_peak,
+                          "frac": round(algo / ms / 1e6 / hbm_peak, 4), "peak_source": hbm_src,
+                          "bytes_model": "value read + gradient read + value written per element"}
+    # split and merge of each codebook with the paper's hyperparameters
+    for which, name, lam, rows0, g2x0 in ((0, "sr", 3.0, st.sr_rows, st.g2sr), (1, "sh", 2.3, st.sh_rows, st.g2sh)):
+        k = rows0.shape[0]
+        k_cap = 65536
+        flat = rows0.reshape(k, -1)
+        rows = torch.zeros((k_cap, flat.shape[1]), dtype=flat.dtype, device=dev)
+        parent = torch.full((k_cap,), -1, dtype=torch.int32, device=dev)
+        g2x = g2x0.clone()
+        cb = cg.Codebook(which, rows, parent, g2x, k, scene.sh_degree)
+
+        def reset():
+            rows[:k].copy_(flat)
+            parent.fill_(-1)
+            g2x.copy_(g2x0)
+            cb.k = k
+
+        reset()
+        cb.split(lam, 0.1, 0.05, 5, 1)
+        k_split = cb.k
+        ms_split = _time_calls(lambda: cb.split(lam, 0.1, 0.05, 5, 1, sync=False), reps, stream, prepare=reset)
+        reset()
+        cb.split(lam, 0.1, 0.05, 5, 1)
+        split_state = (rows.clone(), parent.clone(), g2x.clone(), cb.k)
+
+        def reset_split():
+            rows.copy_(split_state[0])
+            parent.copy_(split_state[1])
+            g2x.copy_(split_state[2])
+            cb.k = split_state[3]
+
+        cb.merge(lam, 0.1, 0.05, 5, 2)
+        k_merge = cb.k
+        ms_merge = _time_calls(lambda: cb.merge(lam, 0.1, 0.05, 5, 2, sync=False), reps, stream, prepare=reset_split)
+        out[f"split_{name}"] = {"ms": round(ms_split, 4), "gaussians": scene.n, "rows_before": k,
+                                "rows_after": k_split, "lambda": lam, "eps_split": 0.1, "eps_merge": 0.05,
+                                "gaussians_per_s": round(scene.n / ms_split * 1e3, 1)}
+        out[f"merge_{name}"] = {"ms": round(ms_merge, 4), "rows_before": k_split, "rows_after": k_merge,
+                                "lambda": lam}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -591,6 +713,8 @@ def main():
     ap.add_argument("--ref-tiles", type=int, default=24, help="tiles per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-next-rows", action="store_true",
+                    help="skip timing the loss, SGLD update and split / merge transitions")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

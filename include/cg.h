@@ -23,7 +23,8 @@
  *   - Every call is asynchronous on `stream` and launches kernels only, so
  *     a sequence of calls can be captured in a CUDA graph.
  *   - Gradient outputs are overwritten, never accumulated.  Inputs are never
- *     modified.
+ *     modified, except the state arrays that the sampler transitions
+ *     (cg_sgld_update, cg_codebook_split, cg_codebook_merge) update in place.
  *   - Host-detectable argument problems return an error before anything is
  *     launched.  Problems found on the device (an index >= K, more
  *     (tile, Gaussian) pairs than the workspace holds) set a status word in
@@ -179,6 +180,123 @@ cg_status cg_l1_loss(const float *image, const float *target, int64_t count, flo
 cg_status cg_l1_loss_static(const float *image, const float *target, int64_t count, float *d_image,
                             double *loss_out, cg_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Reconstruction loss (Eq. 4, Sec. 2.1)
+ *
+ * L = (1 - lambda) L1 + lambda L_SSIM over every value of every view, with
+ * L1 = mean |image - target| and L_SSIM = 1 - mean SSIM.  The paper leaves
+ * SSIM's parameters open; this library takes those of the 3DGS training it
+ * builds on: SSIM of Wang et al. (2004) per colour channel, 11 x 11 Gaussian
+ * window of standard deviation 1.5 normalised to sum 1, zero padding (one
+ * value per pixel), C1 = 0.01^2, C2 = 0.03^2; lambda = 0.2 is the usual
+ * choice.  The gradient of L1 at image == target is taken as 0.
+ * ------------------------------------------------------------------------ */
+
+/* Workspace bytes of cg_recon_loss for these cameras (host array). */
+size_t cg_recon_workspace_bytes(const cg_camera *cams, int n_views);
+
+/* images, target: views packed [v][3][H_v][W_v] as cg_render_fwd writes them
+ * (float, 4-byte aligned, not modified).  d_images (same layout) receives
+ * dL/dimages; loss_out (device, 3 doubles) receives L, L1 and L_SSIM.
+ * 0 <= lambda_ssim <= 1.  The sums run in a fixed order (bitwise
+ * reproducible).  The workspace (256-byte aligned) is this call's own. */
+cg_status cg_recon_loss(const float *images, const float *target, const cg_camera *cams, int n_views,
+                        float lambda_ssim, float *d_images, double *loss_out, void *workspace, size_t ws_bytes,
+                        cg_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Sampler transitions (Sec. 4.3-4.4 and Appendix A.1)
+ *
+ * The sampler moves S = {G, C} by a parameter update (SGLD), a split of a
+ * codebook row or a merge of two rows.  Random draws are Philox4x32-10
+ * (Salmon et al., SC'11) outputs for the 128-bit counter
+ *   (index, stream | call << 8, step & 0xffffffff, step >> 32)
+ * under the key (seed & 0xffffffff, seed >> 32): every draw is a function of
+ * (seed, step, stream, index), so results do not depend on launch shapes.
+ * Streams: 0 positions, 1 opacity logits, 2 SR rows, 3 SH rows (update);
+ * 16 + b split normals, 18 + b split acceptance, 20 + b merge draws, b = 0
+ * for the SR codebook, 1 for SH.  Standard normals are Box-Muller pairs from
+ * draws (a, b): u1 = ((a >> 8) + 1) 2^-24, u2 = (b >> 8) 2^-24,
+ * (sqrt(-2 ln u1) cos 2 pi u2, sqrt(-2 ln u1) sin 2 pi u2), computed in a
+ * fixed binary32 operation order (cg_host_normal4 gives the same values).
+ * Uniforms are (a >> 8) 2^-24.
+ * ------------------------------------------------------------------------ */
+
+/* Mutable view of the differentiable state (same layouts as cg_scene). */
+typedef struct {
+  int n, k_sr, k_sh, sh_degree;
+  cg_dtype cb_dtype;
+  float *pos;
+  float *opacity_logit;
+  void *sr_rows;
+  void *sh_rows;
+} cg_params;
+
+typedef struct {
+  float eps_pos, eps_opacity, eps_sr, eps_sh; /* step sizes, >= 0 */
+  uint64_t seed;
+  uint64_t step;
+} cg_sgld_opts;
+
+/* Parameter-update transition (Eq. 9; Eqs. 25-28 per tensor): in place,
+ *   x <- x + (eps_x / 2) (-dL/dx) + sqrt(eps_x) eta,  eta ~ N(0, 1),
+ * for every position, opacity logit, SR-row value (entries 0-6; entry 7 is
+ * left as it is) and SH-row value.  grad log p = -grad L because p is
+ * proportional to exp(-L) (Eq. 12).  Element e of a tensor uses normal
+ * e & 3 of draw e >> 2 of that tensor's stream.  Gradients are those of
+ * cg_render_bwd / cg_codebook_reduce (float).  BF16 rows are updated in
+ * FP32 and rounded to nearest even.  One launch for all four tensors. */
+cg_status cg_sgld_update(const cg_params *params, const float *d_pos, const float *d_opacity_logit,
+                         const float *d_sr_rows, const float *d_sh_rows, const cg_sgld_opts *opts,
+                         cg_stream_t stream);
+
+typedef struct {
+  int codebook;     /* 0: SR rows (entries 0-6 move, width 8), 1: SH rows (width 3 (d+1)^2) */
+  int n;            /* Gaussians (length of the index array) */
+  int k;            /* rows in use before the transition */
+  int k_cap;        /* rows the row and parent arrays hold: 1 <= k <= k_cap <= 65536 */
+  int sh_degree;    /* 0..3, for the SH row width */
+  cg_dtype dtype;   /* storage of the rows */
+  float lambda;     /* codebook-size penalty of that codebook (Eq. 13) */
+  float eps_split;  /* standard deviation of the split offset u (Eq. 17), > 0 */
+  float eps_merge;  /* standard deviation of the merge kernel (Eq. 18), > 0 */
+  uint64_t seed;
+  uint64_t step;
+} cg_mh_opts;
+
+/* Workspace bytes of cg_codebook_split / cg_codebook_merge. */
+size_t cg_mh_workspace_bytes(const cg_mh_opts *opts);
+
+/* Split transition of one codebook (Sec. 4.4, Eqs. 16-17, 19).  Every
+ * Gaussian i with row c = g2x[i] proposes the new row c + u, u = eps_split z
+ * (z: standard normals, one per moving entry); it is eligible when row c has
+ * at least two members and i is not the lowest-index member, and accepted
+ * when a uniform v < exp(-lambda + |u|^2 (1/eps_split^2 - 1/eps_merge^2)/2),
+ * i.e. with probability min(1, e^-lambda / q_sm(u)).  Accepted Gaussians,
+ * in index order, receive rows k, k + 1, ... up to k_cap: the row value
+ * c + u (FP32 sum, rounded to BF16 for BF16 rows; entry 7 of an SR row is
+ * copied), parent[new] = c, g2x[i] = new.  All in place:
+ *   rows    [k_cap][width] of dtype      parent [k_cap] int32 (-1: none)
+ *   g2x     [n] uint16                   k_out  device int32 (may be NULL):
+ *                                        rows in use afterwards
+ * Indices >= k set CG_ERR_INDEX in the workspace status (that Gaussian does
+ * not split); cg_last_device_status reports it and the new row count. */
+cg_status cg_codebook_split(const cg_mh_opts *opts, void *rows, int32_t *parent, uint16_t *g2x, int32_t *k_out,
+                            void *workspace, size_t ws_bytes, cg_stream_t stream);
+
+/* Merge transition of one codebook (Sec. 4.4, Eqs. 18, 20-21).  Every row
+ * r < k whose parent p = parent[r] is a row (0 <= p < k) is proposed for
+ * merging into p with probability exp(-|c_r - c_p|^2 / (2 eps_merge^2)) and
+ * accepted when a uniform v < exp(lambda - |c_r - c_p|^2
+ * (1/eps_split^2 - 1/eps_merge^2)/2), i.e. with probability
+ * min(1, e^lambda q_sm(c_r - c_p)); it merges only if p does not merge in
+ * the same step.  The members of a merged row move to p, the row is removed,
+ * surviving rows keep their order and are compacted to [0, k'), parents and
+ * g2x are renumbered, parent[k'..k) = -1.  In place, same arrays as the
+ * split; parents outside [-1, k) and indices >= k set CG_ERR_INDEX. */
+cg_status cg_codebook_merge(const cg_mh_opts *opts, void *rows, int32_t *parent, uint16_t *g2x, int32_t *k_out,
+                            void *workspace, size_t ws_bytes, cg_stream_t stream);
+
 /* Internal arrays of the workspace, for inspection by tests (device pointer
  * and element count written to the host outputs).  Layouts:
  *   CG_WS_RECT        [V*n] uint16x4  tile rectangle x0, y0, x1, y1 (x1 == x0 when culled)
@@ -203,6 +321,10 @@ cg_status cg_workspace_array(void *workspace, size_t ws_bytes, cg_ws_array which
 /* Host-side twins of the FP32 decision arithmetic compiled from the same
  * source as the kernels, so it can be checked without a GPU:
  *   cg_host_exp32       the binary32 exp of the decision arithmetic
+ *   cg_host_philox4x32_10, cg_host_normal4, cg_host_log32,
+ *   cg_host_sincos2pi32 the sampler's draws: Philox outputs, the four
+ *                       Box-Muller normals of one draw, and the log and
+ *                       sin / cos of 2 pi u they are built from
  *   cg_host_sh_consts   the 16 SH basis constants (with signs) in FP32
  *   cg_host_sigma3      Eq. 2 of one SR row (8 floats) -> 6 floats
  *   cg_host_tile_keep   the tile test that decides whether a Gaussian is
@@ -210,6 +332,10 @@ cg_status cg_workspace_array(void *workspace, size_t ws_bytes, cg_ws_array which
  *                       mean x, mean y, -c0/2, -c1, -c2/2, opacity; 1 when
  *                       alpha >= 1/255 is reachable at a pixel of the tile */
 float cg_host_exp32(float x);
+void cg_host_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void cg_host_normal4(const uint32_t bits[4], float out[4]);
+float cg_host_log32(float x);
+void cg_host_sincos2pi32(float u, float out[2]);
 void cg_host_sh_consts(float out[16]);
 void cg_host_sigma3(const float row[8], float out[6]);
 int cg_host_tile_keep(const float geo[6], int tx, int ty, int tile);
@@ -228,6 +354,10 @@ typedef enum {
   CG_STAGE_BLEND_BWD,      /* per-tile backward compositing */
   CG_STAGE_GAUSS_BWD,      /* per-Gaussian backward */
   CG_STAGE_REDUCE,         /* codebook membership and row sums */
+  CG_STAGE_LOSS,           /* cg_recon_loss */
+  CG_STAGE_SGLD,           /* cg_sgld_update */
+  CG_STAGE_SPLIT,          /* cg_codebook_split */
+  CG_STAGE_MERGE,          /* cg_codebook_merge */
   CG_STAGE_COUNT
 } cg_stage;
 cg_status cg_timing_enable(int on);

@@ -30,8 +30,11 @@ WS_RECT, WS_DEPTH, WS_PAIRS, WS_RANGES, WS_NCONTRIB, WS_TFINAL, WS_DSIGMA, WS_DR
 # every symbol include/cg.h declares
 EXPORTS = ["cg_workspace_bytes", "cg_render_fwd", "cg_render_bwd", "cg_codebook_reduce", "cg_last_device_status",
            "cg_l1_loss", "cg_workspace_array", "cg_host_exp32", "cg_host_sh_consts", "cg_host_sigma3",
-           "cg_host_tile_keep", "cg_timing_enable", "cg_timing_read", "cg_launch_count", "cg_version", "cg_l1_loss_static"]
-STAGES = ["preprocess", "sort", "blend_fwd", "blend_bwd", "gauss_bwd", "reduce"]
+           "cg_host_tile_keep", "cg_timing_enable", "cg_timing_read", "cg_launch_count", "cg_version",
+           "cg_l1_loss_static", "cg_recon_workspace_bytes", "cg_recon_loss", "cg_sgld_update", "cg_mh_workspace_bytes",
+           "cg_codebook_split", "cg_codebook_merge", "cg_host_philox4x32_10", "cg_host_normal4", "cg_host_log32",
+           "cg_host_sincos2pi32"]
+STAGES = ["preprocess", "sort", "blend_fwd", "blend_bwd", "gauss_bwd", "reduce", "loss", "sgld", "split", "merge"]
 
 
 class CgError(RuntimeError):
@@ -57,6 +60,24 @@ class Opts(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int), ("batch", ctypes.c_int), ("batch_bwd", ctypes.c_int),
                 ("ppt_fwd", ctypes.c_int), ("ppt_bwd", ctypes.c_int), ("bg", ctypes.c_float * 3),
                 ("pair_capacity", ctypes.c_uint32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("k_sr", ctypes.c_int), ("k_sh", ctypes.c_int), ("sh_degree", ctypes.c_int),
+                ("cb_dtype", ctypes.c_int), ("pos", ctypes.c_void_p), ("opacity_logit", ctypes.c_void_p),
+                ("sr_rows", ctypes.c_void_p), ("sh_rows", ctypes.c_void_p)]
+
+
+class SgldOpts(ctypes.Structure):
+    _fields_ = [("eps_pos", ctypes.c_float), ("eps_opacity", ctypes.c_float), ("eps_sr", ctypes.c_float),
+                ("eps_sh", ctypes.c_float), ("seed", ctypes.c_uint64), ("step", ctypes.c_uint64)]
+
+
+class MhOpts(ctypes.Structure):
+    _fields_ = [("codebook", ctypes.c_int), ("n", ctypes.c_int), ("k", ctypes.c_int), ("k_cap", ctypes.c_int),
+                ("sh_degree", ctypes.c_int), ("dtype", ctypes.c_int), ("lam", ctypes.c_float),
+                ("eps_split", ctypes.c_float), ("eps_merge", ctypes.c_float), ("seed", ctypes.c_uint64),
+                ("step", ctypes.c_uint64)]
 
 
 _lock = threading.Lock()
@@ -95,8 +116,22 @@ def load(path: str | None = None) -> ctypes.CDLL:
         L.cg_timing_read.argtypes = [P, P]
         L.cg_timing_read.restype = ctypes.c_int
         L.cg_launch_count.restype = ctypes.c_uint64
+        L.cg_recon_workspace_bytes.argtypes = [P, ctypes.c_int]
+        L.cg_recon_workspace_bytes.restype = ctypes.c_size_t
+        L.cg_recon_loss.argtypes = [P, P, P, ctypes.c_int, ctypes.c_float, P, P, P, ctypes.c_size_t, P]
+        L.cg_sgld_update.argtypes = [P, P, P, P, P, P, P]
+        L.cg_mh_workspace_bytes.argtypes = [P]
+        L.cg_mh_workspace_bytes.restype = ctypes.c_size_t
+        L.cg_codebook_split.argtypes = [P, P, P, P, P, P, ctypes.c_size_t, P]
+        L.cg_codebook_merge.argtypes = [P, P, P, P, P, P, ctypes.c_size_t, P]
+        L.cg_host_philox4x32_10.argtypes = [P, P, P]
+        L.cg_host_normal4.argtypes = [P, P]
+        L.cg_host_log32.argtypes = [ctypes.c_float]
+        L.cg_host_log32.restype = ctypes.c_float
+        L.cg_host_sincos2pi32.argtypes = [ctypes.c_float, P]
         for name in ("cg_render_fwd", "cg_render_bwd", "cg_codebook_reduce", "cg_last_device_status", "cg_l1_loss",
-                     "cg_workspace_array"):
+                     "cg_workspace_array", "cg_recon_loss", "cg_sgld_update", "cg_codebook_split",
+                     "cg_codebook_merge"):
             getattr(L, name).restype = ctypes.c_int
         if path is None:
             _lib = L
@@ -154,6 +189,115 @@ def _stream_ptr(stream: torch.cuda.Stream | None) -> ctypes.c_void_p:
 
 def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _aligned_workspace(nbytes: int, device) -> tuple[torch.Tensor, ctypes.c_void_p]:
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    return ws, ctypes.c_void_p(ws.data_ptr() + (-ws.data_ptr()) % 256)
+
+
+class ReconLoss:
+    """Eq. 4 on the device: L = (1 - lambda) L1 + lambda (1 - SSIM) and its
+    gradient, for views packed like the renderer's images (own workspace)."""
+
+    def __init__(self, cams: Sequence, lam: float = 0.2, device: str | torch.device = "cuda"):
+        self.lib = load()
+        self._cams = camera_array(list(cams))
+        self.n_views = len(cams)
+        self.lam = float(lam)
+        self.device = torch.device(device)
+        self.ws_bytes = int(self.lib.cg_recon_workspace_bytes(self._cams, self.n_views))
+        if self.ws_bytes == 0:
+            raise CgError("cg_recon_workspace_bytes", CG_ERR_ARG)
+        self.ws, self._ws_ptr = _aligned_workspace(self.ws_bytes, self.device)
+
+    def __call__(self, images: torch.Tensor, target: torch.Tensor, d_images: torch.Tensor | None = None,
+                 loss: torch.Tensor | None = None, stream=None):
+        """Returns (loss[3] = L, L1, L_SSIM as float64, d_images)."""
+        if d_images is None:
+            d_images = torch.empty_like(images)
+        if loss is None:
+            loss = torch.empty((3,), dtype=torch.float64, device=self.device)
+        _check("cg_recon_loss", self.lib.cg_recon_loss(_ptr(images), _ptr(target), self._cams, self.n_views,
+                                                       self.lam, _ptr(d_images), _ptr(loss), self._ws_ptr,
+                                                       self.ws_bytes, _stream_ptr(stream)))
+        return loss, d_images
+
+
+def sgld_update(scene: "SceneTensors", d_pos, d_logit, d_sr, d_sh, eps: dict, seed: int, step: int, stream=None):
+    """Parameter-update transition in place on the scene's tensors (Eq. 9).
+    eps: step sizes 'pos', 'logit', 'sr', 'sh'."""
+    sc = scene.struct()
+    p = Params(sc.n, sc.k_sr, sc.k_sh, sc.sh_degree, sc.cb_dtype, scene.pos.data_ptr(),
+               scene.opacity_logit.data_ptr(), scene.sr_rows.data_ptr(), scene.sh_rows.data_ptr())
+    o = SgldOpts(float(eps["pos"]), float(eps["logit"]), float(eps["sr"]), float(eps["sh"]), int(seed), int(step))
+    for t in (d_pos, d_logit, d_sr, d_sh):
+        if not (t.is_cuda and t.is_contiguous() and t.dtype == torch.float32):
+            raise ValueError("gradients must be contiguous float32 CUDA tensors")
+    _check("cg_sgld_update", load().cg_sgld_update(ctypes.byref(p), _ptr(d_pos), _ptr(d_logit), _ptr(d_sr),
+                                                   _ptr(d_sh), ctypes.byref(o), _stream_ptr(stream)))
+
+
+class Codebook:
+    """One codebook whose rows the sampler splits and merges: rows
+    [k_cap][width] (float32 or bfloat16), parent [k_cap] int32, the number of
+    rows in use k, and the Gaussians' index array g2x (int16 tensor holding
+    uint16 values), all updated in place."""
+
+    def __init__(self, which: int, rows: torch.Tensor, parent: torch.Tensor, g2x: torch.Tensor, k: int,
+                 sh_degree: int = 3):
+        self.lib = load()
+        self.which, self.rows, self.parent, self.g2x = int(which), rows, parent, g2x
+        self.k, self.k_cap, self.sh_degree = int(k), int(rows.shape[0]), int(sh_degree)
+        self.k_dev = torch.zeros((1,), dtype=torch.int32, device=rows.device)
+        self.ws, self._ws_ptr, self.ws_bytes = None, None, 0
+
+    def opts(self, lam, eps_split, eps_merge, seed, step) -> MhOpts:
+        return MhOpts(self.which, int(self.g2x.numel()), self.k, self.k_cap, self.sh_degree,
+                      CG_BF16 if self.rows.dtype == torch.bfloat16 else CG_F32, float(lam), float(eps_split),
+                      float(eps_merge), int(seed), int(step))
+
+    def _ensure(self, o: MhOpts):
+        need = int(self.lib.cg_mh_workspace_bytes(ctypes.byref(o)))
+        if need == 0:
+            raise CgError("cg_mh_workspace_bytes", CG_ERR_ARG)
+        if need > self.ws_bytes:
+            self.ws, self._ws_ptr = _aligned_workspace(need, self.rows.device)
+            self.ws_bytes = need
+
+    def _run(self, fn: str, lam, eps_split, eps_merge, seed, step, stream=None, sync: bool = True):
+        o = self.opts(lam, eps_split, eps_merge, seed, step)
+        self._ensure(o)
+        _check(fn, getattr(self.lib, fn)(ctypes.byref(o), _ptr(self.rows), _ptr(self.parent), _ptr(self.g2x),
+                                         _ptr(self.k_dev), self._ws_ptr, self.ws_bytes, _stream_ptr(stream)))
+        if sync:
+            k = ctypes.c_uint64(0)
+            _check("device status", self.lib.cg_last_device_status(self._ws_ptr, self.ws_bytes, _stream_ptr(stream),
+                                                                   ctypes.byref(k)))
+            self.k = int(k.value)
+        return self.k
+
+    def split(self, lam, eps_split, eps_merge, seed, step, stream=None, sync: bool = True) -> int:
+        return self._run("cg_codebook_split", lam, eps_split, eps_merge, seed, step, stream, sync)
+
+    def merge(self, lam, eps_split, eps_merge, seed, step, stream=None, sync: bool = True) -> int:
+        return self._run("cg_codebook_merge", lam, eps_split, eps_merge, seed, step, stream, sync)
+
+
+def host_philox(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    load().cg_host_philox4x32_10(c.ctypes.data_as(ctypes.c_void_p), k.ctypes.data_as(ctypes.c_void_p),
+                                 out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def host_normal4(bits) -> np.ndarray:
+    b = np.ascontiguousarray(bits, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.float32)
+    load().cg_host_normal4(b.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p))
+    return out
 
 
 class SceneTensors:

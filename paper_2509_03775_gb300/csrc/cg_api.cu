@@ -7,7 +7,7 @@
 #include <mutex>
 #include <vector>
 
-#include "cg_common.cuh"
+#include "cg_random.cuh"
 
 namespace cg {
 static std::atomic<uint64_t> g_launches{0};
@@ -338,7 +338,156 @@ cg_status cg_workspace_array(void* workspace, size_t ws_bytes, cg_ws_array which
   return CG_OK;
 }
 
+size_t cg_recon_workspace_bytes(const cg_camera* cams, int n_views) {
+  if (!cams || n_views < 1 || n_views > CG_MAX_VIEWS) return 0;
+  for (int i = 0; i < n_views; ++i)
+    if (cams[i].width < 1 || cams[i].height < 1) return 0;
+  return (size_t)recon_workspace_bytes(cams, n_views);
+}
+
+cg_status cg_recon_loss(const float* images, const float* target, const cg_camera* cams, int n_views,
+                        float lambda_ssim, float* d_images, double* loss_out, void* workspace, size_t ws_bytes,
+                        cg_stream_t stream) {
+  const size_t need = cg_recon_workspace_bytes(cams, n_views);
+  if (need == 0 || !images || !target || !d_images || !loss_out || !workspace || !aligned(images, 4) ||
+      !aligned(target, 4) || !aligned(d_images, 4) || !aligned(loss_out, 8) || !aligned(workspace, kAlign) ||
+      ws_bytes < need || !(lambda_ssim >= 0.0f && lambda_ssim <= 1.0f))
+    return CG_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  StageTimer t(CG_STAGE_LOSS, s);
+  return cuda_status(launch_recon_loss(images, target, cams, n_views, lambda_ssim, d_images, loss_out, workspace, s));
+}
+
+static bool finite_nonneg(float v) { return v >= 0.0f && v < 3.0e38f; }
+
+cg_status cg_sgld_update(const cg_params* p, const float* d_pos, const float* d_opacity_logit,
+                         const float* d_sr_rows, const float* d_sh_rows, const cg_sgld_opts* o,
+                         cg_stream_t stream) {
+  if (!p || !o || p->n < 1 || p->k_sr < 1 || p->k_sh < 1 || p->k_sr > 65536 || p->k_sh > 65536 ||
+      p->sh_degree < 0 || p->sh_degree > 3 || (p->cb_dtype != CG_F32 && p->cb_dtype != CG_BF16))
+    return CG_ERR_ARG;
+  const size_t esz = p->cb_dtype == CG_BF16 ? 2 : 4;
+  if (!p->pos || !p->opacity_logit || !p->sr_rows || !p->sh_rows || !d_pos || !d_opacity_logit || !d_sr_rows ||
+      !d_sh_rows || !aligned(p->pos, 4) || !aligned(p->opacity_logit, 4) || !aligned(p->sr_rows, esz) ||
+      !aligned(p->sh_rows, esz) || !aligned(d_pos, 4) || !aligned(d_opacity_logit, 4) || !aligned(d_sr_rows, 4) ||
+      !aligned(d_sh_rows, 4))
+    return CG_ERR_ARG;
+  if (!finite_nonneg(o->eps_pos) || !finite_nonneg(o->eps_opacity) || !finite_nonneg(o->eps_sr) ||
+      !finite_nonneg(o->eps_sh))
+    return CG_ERR_ARG;
+  SgldArgs a;
+  memset(&a, 0, sizeof(a));
+  const int nb = (p->sh_degree + 1) * (p->sh_degree + 1);
+  void* xs[4] = {p->pos, p->opacity_logit, p->sr_rows, p->sh_rows};
+  const float* gs[4] = {d_pos, d_opacity_logit, d_sr_rows, d_sh_rows};
+  const int64_t counts[4] = {3 * (int64_t)p->n, (int64_t)p->n, (int64_t)CG_SR_WIDTH * p->k_sr,
+                             3 * (int64_t)nb * p->k_sh};
+  const float eps[4] = {o->eps_pos, o->eps_opacity, o->eps_sr, o->eps_sh};
+  const uint32_t streams[4] = {kStreamPos, kStreamLogit, kStreamSR, kStreamSH};
+  for (int i = 0; i < 4; ++i) {
+    SgldSeg& g = a.seg[i];
+    g.x = xs[i];
+    g.g = gs[i];
+    g.count = counts[i];
+    g.a = -0.5f * eps[i];
+    g.b = sqrtf(eps[i]);
+    g.stream = streams[i];
+    g.bf16 = i >= 2 && p->cb_dtype == CG_BF16;
+    g.vec = aligned(xs[i], g.bf16 ? 8 : 16);
+    g.gvec = aligned(gs[i], 16);
+    g.skip7 = i == 2;
+    a.calls[i] = (counts[i] + 3) / 4;
+  }
+  a.seed = o->seed;
+  a.step = o->step;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  StageTimer t(CG_STAGE_SGLD, s);
+  return cuda_status(launch_sgld(a, s));
+}
+
+static bool mh_ok(const cg_mh_opts* o) {
+  return o && (o->codebook == 0 || o->codebook == 1) && o->n >= 1 && o->k >= 1 && o->k <= o->k_cap &&
+         o->k_cap <= 65536 && o->sh_degree >= 0 && o->sh_degree <= 3 &&
+         (o->dtype == CG_F32 || o->dtype == CG_BF16) && o->eps_split > 0.0f && o->eps_split < 3.0e38f &&
+         o->eps_merge > 0.0f && o->eps_merge < 3.0e38f && o->lambda > -3.0e38f && o->lambda < 3.0e38f;
+}
+
+static void mh_dims(const cg_mh_opts* o, int* dims, int* width) {
+  if (o->codebook == 0) {
+    *dims = 7;
+    *width = CG_SR_WIDTH;
+  } else {
+    *dims = *width = 3 * (o->sh_degree + 1) * (o->sh_degree + 1);
+  }
+}
+
+size_t cg_mh_workspace_bytes(const cg_mh_opts* o) {
+  if (!mh_ok(o)) return 0;
+  int dims, width;
+  mh_dims(o, &dims, &width);
+  return (size_t)mh_layout(o->n, o->k_cap, width).total;
+}
+
+static cg_status mh_call(bool split, const cg_mh_opts* o, void* rows, int32_t* parent, uint16_t* g2x,
+                         int32_t* k_out, void* ws, size_t ws_bytes, cg_stream_t stream) {
+  if (!mh_ok(o) || !rows || !parent || !g2x || !ws || !aligned(ws, kAlign) ||
+      !aligned(rows, o->dtype == CG_BF16 ? 2 : 4) || !aligned(parent, 4) || !aligned(g2x, 2) ||
+      (k_out && !aligned(k_out, 4)))
+    return CG_ERR_ARG;
+  MhArgs a;
+  memset(&a, 0, sizeof(a));
+  a.codebook = o->codebook;
+  a.n = o->n;
+  a.k = o->k;
+  a.k_cap = o->k_cap;
+  mh_dims(o, &a.dims, &a.width);
+  a.dtype = o->dtype;
+  a.lam = o->lambda;
+  a.coef = mh_coef(o->eps_split, o->eps_merge);
+  a.seed = o->seed;
+  a.step = o->step;
+  a.rows = rows;
+  a.parent = parent;
+  a.g2x = g2x;
+  a.k_out = k_out;
+  const MhLayout M = mh_layout(o->n, o->k_cap, a.width);
+  if (ws_bytes < M.total) return CG_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  StageTimer t(split ? CG_STAGE_SPLIT : CG_STAGE_MERGE, s);
+  return cuda_status(split ? launch_split(a, M, ws, s) : launch_merge(a, M, ws, s));
+}
+
+cg_status cg_codebook_split(const cg_mh_opts* opts, void* rows, int32_t* parent, uint16_t* g2x, int32_t* k_out,
+                            void* workspace, size_t ws_bytes, cg_stream_t stream) {
+  return mh_call(true, opts, rows, parent, g2x, k_out, workspace, ws_bytes, stream);
+}
+
+cg_status cg_codebook_merge(const cg_mh_opts* opts, void* rows, int32_t* parent, uint16_t* g2x, int32_t* k_out,
+                            void* workspace, size_t ws_bytes, cg_stream_t stream) {
+  return mh_call(false, opts, rows, parent, g2x, k_out, workspace, ws_bytes, stream);
+}
+
 float cg_host_exp32(float x) { return exp32(x); }
+
+void cg_host_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const uint4 r = philox4x32_10(make_uint4(ctr[0], ctr[1], ctr[2], ctr[3]), key[0], key[1]);
+  out[0] = r.x;
+  out[1] = r.y;
+  out[2] = r.z;
+  out[3] = r.w;
+}
+
+void cg_host_normal4(const uint32_t bits[4], float out[4]) {
+  const float4 z = normal4(make_uint4(bits[0], bits[1], bits[2], bits[3]));
+  out[0] = z.x;
+  out[1] = z.y;
+  out[2] = z.z;
+  out[3] = z.w;
+}
+
+float cg_host_log32(float x) { return log32(x); }
+
+void cg_host_sincos2pi32(float u, float out[2]) { sincos2pi32(u, &out[0], &out[1]); }
 
 void cg_host_sh_consts(float out[16]) {
   for (int k = 0; k < 16; ++k) out[k] = sh_const(k);

@@ -346,6 +346,9 @@ cudaError_t launch_codebook_reduce(const SceneArgs& sc, const Layout& L, void* w
                                    cudaStream_t s);
 cudaError_t launch_l1(const float* img, const float* tgt, int64_t count, float* d_img, double* loss,
                       const Layout& L, void* ws, cudaStream_t s);
+uint64_t recon_workspace_bytes(const cg_camera* cams, int n_views);
+cudaError_t launch_recon_loss(const float* x, const float* y, const cg_camera* cams, int n_views, float lam,
+                              float* dx, double* loss, void* ws, cudaStream_t s);
 
 // The depth-sorted visible records (4 sort passes end in dkeys0).
 inline uint64_t* depth_sorted(void* ws, const Layout& L) { return ws_ptr<uint64_t>(ws, L.dkeys0); }

@@ -1,0 +1,408 @@
+// k_mcmc.cu -- the sampler transitions of the codebook state (Sec. 4.3-4.4,
+// Appendix A.1): the SGLD parameter update, and the split and merge of
+// codebook rows with their Metropolis-Hastings acceptance.
+//
+// Parameter update: one launch moves every differentiable tensor
+// (positions, opacity logits, SR rows, SH rows): x <- x + (eps/2)(-dL/dx) +
+// sqrt(eps) z (grad log p = -grad L since p is proportional to exp(-L)), z a
+// standard normal drawn from Philox by element index, four elements per
+// draw.  Memory-bound: 12 bytes per FP32 element (8 for BF16 rows).
+//
+// Split (per Gaussian i mapped to row c): propose c + u, u = eps_split z;
+// eligible when row c has at least two members and i is not its first
+// member; accept when a uniform v < exp(-lambda + |u|^2 kc) (the acceptance
+// min(1, e^-lambda / q_sm(u))).  Accepted Gaussians get rows k, k + 1, ...
+// in Gaussian order (an exclusive scan of the flags) while capacity lasts.
+//
+// Merge (per row r with a parent p, the row it was split from): proposed
+// with probability exp(-|c_r - c_p|^2 km), accepted when a uniform
+// v < exp(lambda - |c_r - c_p|^2 kc) (min(1, e^lambda q_sm(c - c'))); a row
+// merges only if its parent does not merge in the same step.  Its members
+// move to the parent, surviving rows are compacted in order (a scan of the
+// survivors), and parents and indices are renumbered.
+//
+// All accept / reject decisions use the decision arithmetic of
+// cg_random.cuh.  Membership counts use integer atomics (order-free).
+#include <algorithm>
+
+#include "cg_random.cuh"
+
+namespace cg {
+
+constexpr int kGridMh = 152 * 8;
+
+static int grid_for(int64_t items, int threads) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((items + threads - 1) / threads, kGridMh));
+}
+
+// ---------------------------------------------------------------------------
+// parameter update
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float bf16_to_f32(uint16_t b) { return bits_to_float((uint32_t)b << 16); }
+__device__ __forceinline__ uint16_t f32_to_bf16(float f) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+}
+
+__global__ void __launch_bounds__(256) k_sgld(const __grid_constant__ SgldArgs a) {
+  const int64_t total = a.calls[0] + a.calls[1] + a.calls[2] + a.calls[3];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+    int seg = 0;
+    int64_t c = t;
+    while (seg < 3 && c >= a.calls[seg]) {
+      c -= a.calls[seg];
+      ++seg;
+    }
+    const SgldSeg& sg = a.seg[seg];
+    const float4 z = normal4(draw4((uint32_t)c, sg.stream, 0, a.step, a.seed));
+    const float zz[4] = {z.x, z.y, z.z, z.w};
+    const int64_t e0 = 4 * c;
+    const int nv = (int)min((int64_t)4, sg.count - e0);
+    float x[4] = {0.0f, 0.0f, 0.0f, 0.0f}, g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (sg.bf16) {
+      const uint16_t* xp = reinterpret_cast<const uint16_t*>(sg.x) + e0;
+      if (nv == 4 && sg.vec) {
+        const uint2 r = *reinterpret_cast<const uint2*>(xp);
+        x[0] = bf16_to_f32((uint16_t)(r.x & 0xffffu));
+        x[1] = bf16_to_f32((uint16_t)(r.x >> 16));
+        x[2] = bf16_to_f32((uint16_t)(r.y & 0xffffu));
+        x[3] = bf16_to_f32((uint16_t)(r.y >> 16));
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < nv) x[q] = bf16_to_f32(xp[q]);
+      }
+    } else {
+      const float* xp = reinterpret_cast<const float*>(sg.x) + e0;
+      if (nv == 4 && sg.vec) {
+        const float4 r = *reinterpret_cast<const float4*>(xp);
+        x[0] = r.x, x[1] = r.y, x[2] = r.z, x[3] = r.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < nv) x[q] = xp[q];
+      }
+    }
+    if (nv == 4 && sg.gvec) {
+      const float4 r = *reinterpret_cast<const float4*>(sg.g + e0);
+      g[0] = r.x, g[1] = r.y, g[2] = r.z, g[3] = r.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < nv) g[q] = sg.g[e0 + q];
+    }
+    float y[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const bool fixed = q >= nv || (sg.skip7 && ((e0 + q) & 7) == 7);
+      y[q] = fixed ? x[q] : fmaf(sg.b, zz[q], fmaf(sg.a, g[q], x[q]));
+    }
+    if (sg.bf16) {
+      uint16_t* xp = reinterpret_cast<uint16_t*>(sg.x) + e0;
+      if (nv == 4 && sg.vec) {
+        uint2 r;
+        r.x = (uint32_t)f32_to_bf16(y[0]) | ((uint32_t)f32_to_bf16(y[1]) << 16);
+        r.y = (uint32_t)f32_to_bf16(y[2]) | ((uint32_t)f32_to_bf16(y[3]) << 16);
+        *reinterpret_cast<uint2*>(xp) = r;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < nv) xp[q] = f32_to_bf16(y[q]);
+      }
+    } else {
+      float* xp = reinterpret_cast<float*>(sg.x) + e0;
+      if (nv == 4 && sg.vec) {
+        *reinterpret_cast<float4*>(xp) = make_float4(y[0], y[1], y[2], y[3]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < nv) xp[q] = y[q];
+      }
+    }
+  }
+}
+
+cudaError_t launch_sgld(const SgldArgs& a, cudaStream_t s) {
+  const int64_t total = a.calls[0] + a.calls[1] + a.calls[2] + a.calls[3];
+  if (total == 0) return cudaSuccess;
+  count_launch(), k_sgld<<<grid_for(total, 256), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// split and merge: shared setup
+// ---------------------------------------------------------------------------
+
+MhLayout mh_layout(int n, int k_cap, int width) {
+  MhLayout L;
+  memset(&L, 0, sizeof(L));
+  auto up = [](uint64_t x) { return (x + 255) & ~uint64_t(255); };
+  const int64_t items = std::max<int64_t>(n, k_cap);
+  uint64_t off = 0;
+  auto take = [&](uint64_t bytes) {
+    const uint64_t o = off;
+    off = up(off + std::max<uint64_t>(bytes, 1));
+    return o;
+  };
+  L.hdr = take(sizeof(WsHeader));
+  L.members = take(4 * (uint64_t)k_cap);
+  L.first = take(4 * (uint64_t)k_cap);
+  L.flags = take(4 * (uint64_t)items);
+  L.scan = take(4 * (uint64_t)items);
+  L.target = take(4 * (uint64_t)k_cap);
+  L.rows_copy = take(4 * (uint64_t)k_cap * width);
+  L.parent_copy = take(4 * (uint64_t)k_cap);
+  L.scan_blocks_cap = (items + 4095) / 4096 + 1;
+  L.blocksums = take(8 * (uint64_t)L.scan_blocks_cap);
+  L.total = off;
+  return L;
+}
+
+static Layout scan_shim(const MhLayout& M) {
+  Layout L;
+  memset(&L, 0, sizeof(L));
+  L.blocksums = M.blocksums;
+  L.scan_blocks_cap = M.scan_blocks_cap;
+  return L;
+}
+
+__global__ void k_mh_init(WsHeader* h, uint32_t* members, uint32_t* first, int k, uint64_t count) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    h->magic = kMagic;
+    h->st.status = 0;
+    h->st.detail = 0;
+    h->st.pairs = 0;
+    h->st.visible = count;
+    h->st.scan_total = 0;
+    h->st.pairs_ok = 1;
+  }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < k; r += stride) {
+    members[r] = 0u;
+    first[r] = 0xffffffffu;
+  }
+}
+
+__device__ __forceinline__ float load_val(const void* rows, int dtype, int64_t i) {
+  if (dtype == CG_BF16) return bf16_to_f32(reinterpret_cast<const uint16_t*>(rows)[i]);
+  return reinterpret_cast<const float*>(rows)[i];
+}
+
+__device__ __forceinline__ void store_val(void* rows, int dtype, int64_t i, float v) {
+  if (dtype == CG_BF16)
+    reinterpret_cast<uint16_t*>(rows)[i] = f32_to_bf16(v);
+  else
+    reinterpret_cast<float*>(rows)[i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// split
+// ---------------------------------------------------------------------------
+
+__global__ void k_split_count(const MhArgs a, uint32_t* members, uint32_t* first, DeviceState* st) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const uint32_t c = a.g2x[i];
+    if ((int)c >= a.k) {
+      set_status(st, CG_ERR_INDEX, (uint32_t)i);
+      continue;
+    }
+    atomicAdd(&members[c], 1u);
+    atomicMin(&first[c], (uint32_t)i);
+  }
+}
+
+// |u|^2 of Gaussian i's proposal, u = eps_split z (decision arithmetic:
+// squares added in dimension order).
+__device__ __forceinline__ float split_n2(const MhArgs& a, uint32_t i) {
+  float n2 = 0.0f;
+  const int calls = (a.dims + 3) / 4;
+  for (int j = 0; j < calls; ++j) {
+    const float4 z = normal4(draw4(i, kStreamSplitU + (uint32_t)a.codebook, (uint32_t)j, a.step, a.seed));
+    const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (4 * j + q < a.dims) {
+        const float u = a.coef.es * zz[q];
+        n2 = n2 + u * u;
+      }
+    }
+  }
+  return n2;
+}
+
+__global__ void k_split_propose(const MhArgs a, const uint32_t* members, const uint32_t* first,
+                                uint32_t* flags) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const uint32_t c = a.g2x[i];
+    bool acc = false;
+    if ((int)c < a.k && members[c] >= 2u && first[c] != (uint32_t)i) {
+      const float n2 = split_n2(a, (uint32_t)i);
+      const float la = n2 * a.coef.kc - a.lam;
+      const float v = uniform24(draw4((uint32_t)i, kStreamSplitV + (uint32_t)a.codebook, 0, a.step, a.seed).x);
+      acc = v < exp32(la);
+    }
+    flags[i] = acc ? 1u : 0u;
+  }
+}
+
+__global__ void k_split_apply(const MhArgs a, const uint32_t* flags, const uint32_t* rank) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    if (!flags[i]) continue;
+    const int64_t r = (int64_t)a.k + rank[i];
+    if (r >= a.k_cap) continue;
+    const uint32_t c = a.g2x[i];
+    const int calls = (a.width + 3) / 4;
+    for (int j = 0; j < calls; ++j) {
+      float zz[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      if (4 * j < a.dims) {
+        const float4 z =
+            normal4(draw4((uint32_t)i, kStreamSplitU + (uint32_t)a.codebook, (uint32_t)j, a.step, a.seed));
+        zz[0] = z.x, zz[1] = z.y, zz[2] = z.z, zz[3] = z.w;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int d = 4 * j + q;
+        if (d >= a.width) break;
+        float v = load_val(a.rows, a.dtype, (int64_t)c * a.width + d);
+        if (d < a.dims) v = v + a.coef.es * zz[q];
+        store_val(a.rows, a.dtype, r * a.width + d, v);
+      }
+    }
+    a.parent[r] = (int32_t)c;
+    a.g2x[i] = (uint16_t)r;
+  }
+}
+
+__global__ void k_split_finish(const MhArgs a, DeviceState* st) {
+  const uint64_t room = (uint64_t)(a.k_cap - a.k);
+  const uint64_t added = st->scan_total < room ? st->scan_total : room;
+  const int kn = a.k + (int)added;
+  st->pairs = (uint64_t)kn;
+  if (a.k_out) *a.k_out = kn;
+}
+
+cudaError_t launch_split(const MhArgs& a, const MhLayout& M, void* ws, cudaStream_t s) {
+  WsHeader* h = ws_ptr<WsHeader>(ws, M.hdr);
+  DeviceState* st = &h->st;
+  uint32_t* members = ws_ptr<uint32_t>(ws, M.members);
+  uint32_t* first = ws_ptr<uint32_t>(ws, M.first);
+  uint32_t* flags = ws_ptr<uint32_t>(ws, M.flags);
+  uint32_t* rank = ws_ptr<uint32_t>(ws, M.scan);
+  count_launch(), k_mh_init<<<grid_for(a.k, 256), 256, 0, s>>>(h, members, first, a.k, (uint64_t)a.n);
+  const int g = grid_for(a.n, 256);
+  count_launch(), k_split_count<<<g, 256, 0, s>>>(a, members, first, st);
+  count_launch(), k_split_propose<<<g, 256, 0, s>>>(a, members, first, flags);
+  const Layout L = scan_shim(M);
+  cudaError_t e = scan_u32(ws, L, flags, rank, &st->visible, std::max(a.n, a.k_cap), &st->scan_total, s);
+  if (e != cudaSuccess) return e;
+  count_launch(), k_split_apply<<<g, 256, 0, s>>>(a, flags, rank);
+  count_launch(), k_split_finish<<<1, 1, 0, s>>>(a, st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// merge
+// ---------------------------------------------------------------------------
+
+__global__ void k_merge_propose(const MhArgs a, uint32_t* tent, void* rows_copy, int32_t* parent_copy,
+                                DeviceState* st) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int esz = a.dtype == CG_BF16 ? 2 : 4;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.k; r += stride) {
+    const int32_t p = a.parent[r];
+    parent_copy[r] = p;
+    const char* src = reinterpret_cast<const char*>(a.rows) + r * a.width * esz;
+    char* dst = reinterpret_cast<char*>(rows_copy) + r * a.width * esz;
+    for (int b = 0; b < a.width * esz; ++b) dst[b] = src[b];
+    if (p < -1 || p >= a.k) set_status(st, CG_ERR_INDEX, (uint32_t)r);
+    bool t = false;
+    if (p >= 0 && p < a.k) {
+      float d2 = 0.0f;
+      for (int d = 0; d < a.dims; ++d) {
+        const float diff = load_val(a.rows, a.dtype, r * a.width + d) - load_val(a.rows, a.dtype, (int64_t)p * a.width + d);
+        d2 = d2 + diff * diff;
+      }
+      const float rho = exp32(-(d2 * a.coef.km));
+      const float la = a.lam - d2 * a.coef.kc;
+      const uint4 dr = draw4((uint32_t)r, kStreamMerge + (uint32_t)a.codebook, 0, a.step, a.seed);
+      t = uniform24(dr.x) < rho && uniform24(dr.y) < exp32(la);
+    }
+    tent[r] = t ? 1u : 0u;
+  }
+}
+
+__global__ void k_merge_mark(const MhArgs a, const uint32_t* tent, const int32_t* parent_copy, uint32_t* target,
+                             uint32_t* alive) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.k; r += stride) {
+    const int32_t p = parent_copy[r];
+    const bool fin = tent[r] != 0u && tent[p] == 0u;  // tent[r] implies 0 <= p < k
+    target[r] = fin ? (uint32_t)p : (uint32_t)r;
+    alive[r] = fin ? 0u : 1u;
+  }
+}
+
+__global__ void k_merge_compact(const MhArgs a, const void* rows_copy, const int32_t* parent_copy,
+                                const uint32_t* target, const uint32_t* alive, const uint32_t* newidx,
+                                const DeviceState* st) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int esz = a.dtype == CG_BF16 ? 2 : 4;
+  const int64_t kn = (int64_t)st->scan_total;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.k; r += stride) {
+    if (alive[r]) {
+      const int64_t nr = newidx[r];
+      const char* src = reinterpret_cast<const char*>(rows_copy) + r * a.width * esz;
+      char* dst = reinterpret_cast<char*>(a.rows) + nr * a.width * esz;
+      for (int b = 0; b < a.width * esz; ++b) dst[b] = src[b];
+      const int32_t par = parent_copy[r];
+      a.parent[nr] = (par >= 0 && par < a.k) ? (int32_t)newidx[target[par]] : -1;
+    }
+    if (r >= kn) a.parent[r] = -1;
+  }
+}
+
+__global__ void k_merge_remap(const MhArgs a, const uint32_t* target, const uint32_t* newidx, DeviceState* st) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const uint32_t c = a.g2x[i];
+    if ((int)c >= a.k) {
+      set_status(st, CG_ERR_INDEX, (uint32_t)i);
+      continue;
+    }
+    a.g2x[i] = (uint16_t)newidx[target[c]];
+  }
+}
+
+__global__ void k_merge_finish(const MhArgs a, DeviceState* st) {
+  st->pairs = st->scan_total;
+  if (a.k_out) *a.k_out = (int32_t)st->scan_total;
+}
+
+cudaError_t launch_merge(const MhArgs& a, const MhLayout& M, void* ws, cudaStream_t s) {
+  WsHeader* h = ws_ptr<WsHeader>(ws, M.hdr);
+  DeviceState* st = &h->st;
+  uint32_t* tent = ws_ptr<uint32_t>(ws, M.members);
+  uint32_t* target = ws_ptr<uint32_t>(ws, M.target);
+  uint32_t* alive = ws_ptr<uint32_t>(ws, M.flags);
+  uint32_t* newidx = ws_ptr<uint32_t>(ws, M.scan);
+  void* rows_copy = ws_ptr<void>(ws, M.rows_copy);
+  int32_t* parent_copy = ws_ptr<int32_t>(ws, M.parent_copy);
+  count_launch(), k_mh_init<<<1, 32, 0, s>>>(h, ws_ptr<uint32_t>(ws, M.first), ws_ptr<uint32_t>(ws, M.first), 0,
+                                              (uint64_t)a.k);
+  const int gk = grid_for(a.k, 256);
+  count_launch(), k_merge_propose<<<gk, 256, 0, s>>>(a, tent, rows_copy, parent_copy, st);
+  count_launch(), k_merge_mark<<<gk, 256, 0, s>>>(a, tent, parent_copy, target, alive);
+  const Layout L = scan_shim(M);
+  cudaError_t e = scan_u32(ws, L, alive, newidx, &st->visible, std::max(a.n, a.k_cap), &st->scan_total, s);
+  if (e != cudaSuccess) return e;
+  count_launch(), k_merge_compact<<<gk, 256, 0, s>>>(a, rows_copy, parent_copy, target, alive, newidx, st);
+  count_launch(), k_merge_remap<<<grid_for(a.n, 256), 256, 0, s>>>(a, target, newidx, st);
+  count_launch(), k_merge_finish<<<1, 1, 0, s>>>(a, st);
+  return cudaGetLastError();
+}
+
+}  // namespace cg

@@ -1,0 +1,381 @@
+// k_ssim.cu -- the reconstruction loss of Eq. 4 and its gradient:
+// L = (1 - lambda) L1 + lambda (1 - mean SSIM), averaged over every value of
+// every view, SSIM per colour channel with an 11 x 11 Gaussian window
+// (sigma 1.5, normalised), zero padding, C1 = 0.01^2, C2 = 0.03^2.
+//
+// One fused kernel, one CTA per 32 x 32 tile of one channel of one view.
+// The gradient at a pixel needs the SSIM derivative maps within 5 pixels of
+// it, and those need the image within 5 more, so the CTA stages the rendered
+// and target values of the tile plus a 10-pixel halo (52 x 52) in shared
+// memory and:
+//   1. forms the five windowed moments (mu_x, mu_y, E[x^2], E[y^2], E[xy])
+//      on the 42 x 42 region around the tile (horizontal, then vertical
+//      11-tap pass);
+//   2. turns them into SSIM and its derivatives with respect to mu_x, E[x^2]
+//      and E[xy] (zero outside the image), adding SSIM over the tile's own
+//      pixels to the CTA's sum;
+//   3. takes the windowed sums of the three derivative maps on the tile (the
+//      window is symmetric, so the transposed sum is the same window) and
+//      writes dL/dx = (1 - lambda) sign(x - y) / M
+//                     - (lambda / M) (W*d_mu + 2 x W*d_exx + y W*d_exy).
+// Halo values are recomputed by the neighbouring CTAs instead of being
+// written and read back: DRAM traffic is the image, the target and the
+// gradient (12 bytes per value); the work is FP32 arithmetic.  The CTA sums
+// of SSIM and |x - y| go to per-CTA slots in double; a last single-CTA
+// kernel adds the slots in a fixed order.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+
+#include "cg_common.cuh"
+
+namespace cg {
+
+constexpr int kSsimR = 5;
+constexpr int kSsimK = 2 * kSsimR + 1;        // 11 taps
+constexpr int kSsimT = 32;                    // output tile edge
+constexpr int kSsimM = kSsimT + 2 * kSsimR;   // 42: edge of the derivative-map region
+constexpr int kSsimI = kSsimT + 4 * kSsimR;   // 52: edge of the staged input
+constexpr int kSsimILd = kSsimI + 1;          // padded row stride of the staged input
+constexpr int kSsimMLd = kSsimM + 1;          // padded row stride of the maps
+constexpr int kSsimThreads = 256;
+constexpr int kMomRows = 7;                   // map-region rows per thread in step 1 (42 = 6 x 7)
+// shared memory (floats): input x, y; then a region holding first the
+// horizontal moment sums [5][52][42], later the maps [3][42][43] and their
+// horizontal sums [3][42][32]
+constexpr int kSsimInF = 2 * kSsimI * kSsimILd;
+constexpr int kSsimHmF = 5 * kSsimI * kSsimM;
+constexpr int kSsimMapF = 3 * kSsimM * kSsimMLd;
+constexpr int kSsimMhF = 3 * kSsimM * kSsimT;
+static_assert(kSsimMapF + kSsimMhF <= kSsimHmF, "map buffers must fit in the moment buffer");
+constexpr size_t kSsimSmem = sizeof(float) * (kSsimInF + kSsimHmF) + 2 * sizeof(double) * (kSsimThreads / 32);
+
+struct SsimView {
+  int width, height;
+  int tiles_x, tiles_y;
+  int64_t block_base;  // first CTA of the view (3 channels x tiles)
+  int64_t value_base;  // first value of the view in the packed images
+};
+
+struct SsimArgs {
+  const float* x;
+  const float* y;
+  float* dx;     // [M] gradient out
+  double* part;  // [blocks][2] per-CTA sums of SSIM and |x - y|
+  double* loss;  // [3] L, L1, L_SSIM
+  float w[kSsimK];
+  float lam;
+  double inv_m;
+  int64_t m;
+  int64_t blocks;
+  int n_views;
+  SsimView v[CG_MAX_VIEWS];
+};
+
+// Which view, channel and tile a CTA covers.
+__device__ __forceinline__ void ssim_block(const SsimArgs& a, int64_t b, int& vi, int& ch, int& tx, int& ty) {
+  vi = 0;
+  while (vi + 1 < a.n_views && a.v[vi + 1].block_base <= b) ++vi;
+  const SsimView& V = a.v[vi];
+  const int64_t local = b - V.block_base;
+  const int64_t per = (int64_t)V.tiles_x * V.tiles_y;
+  ch = (int)(local / per);
+  const int64_t t = local - (int64_t)ch * per;
+  ty = (int)(t / V.tiles_x);
+  tx = (int)(t - (int64_t)ty * V.tiles_x);
+}
+
+__global__ void __launch_bounds__(kSsimThreads) k_recon_fused(const __grid_constant__ SsimArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sx = reinterpret_cast<float*>(smem_raw);
+  float* sy = sx + kSsimI * kSsimILd;
+  float* hm = sx + kSsimInF;                     // [5][52][42]
+  float* maps = hm;                              // [3][42][43] (after step 1)
+  float* mh = hm + kSsimMapF;                    // [3][42][32]
+  double* red = reinterpret_cast<double*>(hm + kSsimHmF);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int vi, ch, tx, ty;
+  ssim_block(a, blockIdx.x, vi, ch, tx, ty);
+  const SsimView& V = a.v[vi];
+  const int x0 = tx * kSsimT, y0 = ty * kSsimT;
+  const int64_t plane = V.value_base + (int64_t)ch * V.width * V.height;
+
+  // stage x and y on [x0 - 10, x0 + 42) x [y0 - 10, y0 + 42), zero outside
+  for (int r = warp; r < kSsimI; r += kSsimThreads / 32) {
+    const int gy = y0 - 2 * kSsimR + r;
+    const bool row_in = gy >= 0 && gy < V.height;
+    for (int c = lane; c < kSsimI; c += 32) {
+      const int gx = x0 - 2 * kSsimR + c;
+      const bool in = row_in && gx >= 0 && gx < V.width;
+      const int64_t off = plane + (int64_t)gy * V.width + gx;
+      sx[r * kSsimILd + c] = in ? __ldg(a.x + off) : 0.0f;
+      sy[r * kSsimILd + c] = in ? __ldg(a.y + off) : 0.0f;
+    }
+  }
+  __syncthreads();
+  // 1a. horizontal sums of x, y, xx, yy, xy: rows 0..51, columns 0..41;
+  // a work item is 3 adjacent outputs of one row, streaming its 13 inputs
+  constexpr int kSeg1 = 3, kSegs1 = kSsimM / kSeg1;  // 14 segments per row
+  for (int j = tid; j < kSsimI * kSegs1; j += kSsimThreads) {
+    const int r = j / kSegs1, c0 = kSeg1 * (j - r * kSegs1);
+    const float* px = sx + r * kSsimILd + c0;
+    const float* py = sy + r * kSsimILd + c0;
+    float acc[kSeg1][5];
+#pragma unroll
+    for (int o = 0; o < kSeg1; ++o)
+#pragma unroll
+      for (int p = 0; p < 5; ++p) acc[o][p] = 0.0f;
+#pragma unroll
+    for (int e = 0; e < kSeg1 + kSsimK - 1; ++e) {
+      const float xv = px[e], yv = py[e];
+      const float f[5] = {xv, yv, xv * xv, yv * yv, xv * yv};
+#pragma unroll
+      for (int o = 0; o < kSeg1; ++o) {
+        const int k = e - o;
+        if (k >= 0 && k < kSsimK) {
+#pragma unroll
+          for (int p = 0; p < 5; ++p) acc[o][p] = fmaf(a.w[k], f[p], acc[o][p]);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < kSeg1; ++o)
+#pragma unroll
+      for (int p = 0; p < 5; ++p) hm[p * kSsimI * kSsimM + r * kSsimM + c0 + o] = acc[o][p];
+  }
+  __syncthreads();
+  // 1b + 2. vertical sums on the 42 x 42 map region, then SSIM and its
+  // derivatives; thread t < 252 takes column t % 42, rows 7 (t / 42) .. + 6
+  const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+  float mv[kMomRows][3];
+  float acc_s = 0.0f;
+  const bool mom_thread = tid < kSsimM * (kSsimM / kMomRows);
+  const int mc = tid % kSsimM, mr0 = kMomRows * (tid / kSsimM);
+  if (mom_thread) {
+    float mom[kMomRows][5];
+#pragma unroll
+    for (int q = 0; q < kMomRows; ++q)
+#pragma unroll
+      for (int p = 0; p < 5; ++p) mom[q][p] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kMomRows + kSsimK - 1; ++k) {
+      const int r = mr0 + k;
+      float hv[5];
+#pragma unroll
+      for (int p = 0; p < 5; ++p) hv[p] = hm[p * kSsimI * kSsimM + r * kSsimM + mc];
+#pragma unroll
+      for (int q = 0; q < kMomRows; ++q) {
+        const int tap = k - q;
+        if (tap >= 0 && tap < kSsimK) {
+#pragma unroll
+          for (int p = 0; p < 5; ++p) mom[q][p] = fmaf(a.w[tap], hv[p], mom[q][p]);
+        }
+      }
+    }
+    const int gx = x0 - kSsimR + mc;
+    const bool col_own = mc >= kSsimR && mc < kSsimR + kSsimT;
+#pragma unroll
+    for (int q = 0; q < kMomRows; ++q) {
+      const int mr = mr0 + q;
+      const int gy = y0 - kSsimR + mr;
+      mv[q][0] = mv[q][1] = mv[q][2] = 0.0f;
+      if (gx < 0 || gx >= V.width || gy < 0 || gy >= V.height) continue;
+      const float mx = mom[q][0], my = mom[q][1];
+      const float vx = mom[q][2] - mx * mx, vy = mom[q][3] - my * my, cxy = mom[q][4] - mx * my;
+      const float A = 2.0f * mx * my + C1, B = 2.0f * cxy + C2;
+      const float Cc = mx * mx + my * my + C1, D = vx + vy + C2;
+      // two reciprocals (fast, within 2 ulp) instead of four divisions
+      const float iC = __fdividef(1.0f, Cc), iD = __fdividef(1.0f, D);
+      const float icd = iC * iD;
+      const float sv = A * B * icd;
+      const float ds_dmx = 2.0f * my * B * icd - sv * 2.0f * mx * iC;
+      const float ds_dvx = -sv * iD;
+      const float ds_dcxy = 2.0f * A * icd;
+      mv[q][0] = ds_dmx + ds_dvx * (-2.0f * mx) + ds_dcxy * (-my);
+      mv[q][1] = ds_dvx;
+      mv[q][2] = ds_dcxy;
+      if (col_own && mr >= kSsimR && mr < kSsimR + kSsimT) acc_s += sv;
+    }
+  }
+  __syncthreads();  // the moment sums are dead from here on
+  if (mom_thread) {
+#pragma unroll
+    for (int q = 0; q < kMomRows; ++q)
+#pragma unroll
+      for (int p = 0; p < 3; ++p) maps[p * kSsimM * kSsimMLd + (mr0 + q) * kSsimMLd + mc] = mv[q][p];
+  }
+  __syncthreads();
+  // 3a. horizontal sums of the maps: rows 0..41, columns 0..31; a work item
+  // is 2 adjacent outputs of one row
+  constexpr int kSeg3 = 2, kSegs3 = kSsimT / kSeg3;  // 16 segments per row
+  for (int j = tid; j < kSsimM * kSegs3; j += kSsimThreads) {
+    const int r = j / kSegs3, c0 = kSeg3 * (j - r * kSegs3);
+    float acc[kSeg3][3];
+#pragma unroll
+    for (int o = 0; o < kSeg3; ++o) acc[o][0] = acc[o][1] = acc[o][2] = 0.0f;
+#pragma unroll
+    for (int e = 0; e < kSeg3 + kSsimK - 1; ++e) {
+      const int off = r * kSsimMLd + c0 + e;
+      const float f[3] = {maps[off], maps[kSsimM * kSsimMLd + off], maps[2 * kSsimM * kSsimMLd + off]};
+#pragma unroll
+      for (int o = 0; o < kSeg3; ++o) {
+        const int k = e - o;
+        if (k >= 0 && k < kSsimK) {
+#pragma unroll
+          for (int p = 0; p < 3; ++p) acc[o][p] = fmaf(a.w[k], f[p], acc[o][p]);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < kSeg3; ++o)
+#pragma unroll
+      for (int p = 0; p < 3; ++p) mh[p * kSsimM * kSsimT + r * kSsimT + c0 + o] = acc[o][p];
+  }
+  __syncthreads();
+  // 3b. vertical sums and the gradient on the tile: column lane, rows 4 warp .. + 3
+  float g[4][3];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) g[q][0] = g[q][1] = g[q][2] = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 4 + kSsimK - 1; ++k) {
+    const int r = 4 * warp + k;
+    const float h0 = mh[r * kSsimT + lane], h1 = mh[kSsimM * kSsimT + r * kSsimT + lane],
+                h2 = mh[2 * kSsimM * kSsimT + r * kSsimT + lane];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int tap = k - q;
+      if (tap >= 0 && tap < kSsimK) {
+        g[q][0] = fmaf(a.w[tap], h0, g[q][0]);
+        g[q][1] = fmaf(a.w[tap], h1, g[q][1]);
+        g[q][2] = fmaf(a.w[tap], h2, g[q][2]);
+      }
+    }
+  }
+  const float l1w = (float)((1.0 - (double)a.lam) * a.inv_m);
+  const float sw = (float)(-(double)a.lam * a.inv_m);
+  const int gx = x0 + lane;
+  float acc_l1 = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int gy = y0 + 4 * warp + q;
+    if (gx >= V.width || gy >= V.height) continue;
+    const int si = (2 * kSsimR + 4 * warp + q) * kSsimILd + 2 * kSsimR + lane;
+    const float xv = sx[si], yv = sy[si];
+    const float sg = xv > yv ? 1.0f : (xv < yv ? -1.0f : 0.0f);
+    const float ds = fmaf(2.0f * xv, g[q][1], fmaf(yv, g[q][2], g[q][0]));
+    a.dx[plane + (int64_t)gy * V.width + gx] = fmaf(sw, ds, l1w * sg);
+    acc_l1 += fabsf(xv - yv);
+  }
+  // CTA sums in double, fixed order
+  double ds = acc_s, dl = acc_l1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ds += __shfl_xor_sync(0xffffffffu, ds, o);
+    dl += __shfl_xor_sync(0xffffffffu, dl, o);
+  }
+  if (lane == 0) {
+    red[warp] = ds;
+    red[kSsimThreads / 32 + warp] = dl;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double ts = 0.0, tl = 0.0;
+    for (int w = 0; w < kSsimThreads / 32; ++w) {
+      ts += red[w];
+      tl += red[kSsimThreads / 32 + w];
+    }
+    a.part[2 * blockIdx.x] = ts;
+    a.part[2 * blockIdx.x + 1] = tl;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_recon_final(const __grid_constant__ SsimArgs a) {
+  __shared__ double red[2][32];
+  double s = 0.0, l = 0.0;
+  for (int64_t b = threadIdx.x; b < a.blocks; b += 1024) {
+    s += a.part[2 * b];
+    l += a.part[2 * b + 1];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    l += __shfl_xor_sync(0xffffffffu, l, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = s;
+    red[1][threadIdx.x >> 5] = l;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ts = 0.0, tl = 0.0;
+    for (int w = 0; w < 32; ++w) {
+      ts += red[0][w];
+      tl += red[1][w];
+    }
+    const double l1 = tl * a.inv_m, lssim = 1.0 - ts * a.inv_m;
+    a.loss[0] = (1.0 - (double)a.lam) * l1 + (double)a.lam * lssim;
+    a.loss[1] = l1;
+    a.loss[2] = lssim;
+  }
+}
+
+// Workspace: the per-CTA sums.
+static int64_t ssim_blocks(const cg_camera* cams, int n_views) {
+  int64_t b = 0;
+  for (int i = 0; i < n_views; ++i)
+    b += 3 * (int64_t)((cams[i].width + kSsimT - 1) / kSsimT) * ((cams[i].height + kSsimT - 1) / kSsimT);
+  return b;
+}
+
+uint64_t recon_workspace_bytes(const cg_camera* cams, int n_views) {
+  return 16 * (uint64_t)ssim_blocks(cams, n_views) + 256;
+}
+
+cudaError_t launch_recon_loss(const float* x, const float* y, const cg_camera* cams, int n_views, float lam,
+                              float* dx, double* loss, void* ws, cudaStream_t s) {
+  static thread_local SsimArgs a;  // large: kept off the stack
+  memset(&a, 0, sizeof(a));
+  a.x = x;
+  a.y = y;
+  a.part = reinterpret_cast<double*>(ws);
+  a.dx = dx;
+  a.loss = loss;
+  // window taps: exp(-k^2 / (2 sigma^2)) normalised in double, rounded once
+  double w[kSsimK], tot = 0.0;
+  for (int k = -kSsimR; k <= kSsimR; ++k) tot += (w[k + kSsimR] = std::exp(-(double)(k * k) / (2.0 * 1.5 * 1.5)));
+  for (int k = 0; k < kSsimK; ++k) a.w[k] = (float)(w[k] / tot);
+  a.lam = lam;
+  a.n_views = n_views;
+  int64_t blocks = 0, vals = 0;
+  for (int i = 0; i < n_views; ++i) {
+    SsimView& V = a.v[i];
+    V.width = cams[i].width;
+    V.height = cams[i].height;
+    V.tiles_x = (V.width + kSsimT - 1) / kSsimT;
+    V.tiles_y = (V.height + kSsimT - 1) / kSsimT;
+    V.block_base = blocks;
+    V.value_base = vals;
+    blocks += 3 * (int64_t)V.tiles_x * V.tiles_y;
+    vals += 3 * (int64_t)V.width * V.height;
+  }
+  a.m = vals;
+  a.inv_m = 1.0 / (double)vals;
+  a.blocks = blocks;
+  if (blocks <= 0 || blocks > 0x7fffffff) return cudaErrorInvalidValue;
+  // the shared-memory opt-in is per device
+  static std::atomic<uint64_t> attr_set{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+  if (!bit || !(attr_set.load() & bit)) {
+    e = cudaFuncSetAttribute(k_recon_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSsimSmem);
+    if (e != cudaSuccess) return e;
+    attr_set.fetch_or(bit);
+  }
+  count_launch(), k_recon_fused<<<(unsigned)blocks, kSsimThreads, kSsimSmem, s>>>(a);
+  count_launch(), k_recon_final<<<1, 1024, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace cg

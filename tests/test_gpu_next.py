@@ -1,0 +1,299 @@
+"""GPU parity of the reconstruction loss (Eq. 4) and the sampler transitions
+(SGLD update, split, merge) against the oracle, through the C ABI.
+
+Bars: split / merge outcomes (row count, row values, parents, indices) are
+bit-exact, since both sides take the decisions in the same FP32 arithmetic;
+the SGLD update is within FP32 rounding of the FP64 oracle (BF16 rows within
+one BF16 step); the loss within 1e-6 and its gradient within 1e-3 relative
+or 1e-4 of the largest magnitude (the FP32 cancellation in the windowed
+variances, E[x^2] - mu^2, bounds the gradient's accuracy)."""
+import types
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import mcmc, ssim
+from paper_2509_03775_gb300 import cg, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+# ----------------------------------------------------------------------------
+# helpers
+# ----------------------------------------------------------------------------
+
+def _bf16_bits_to_f32(t: torch.Tensor) -> np.ndarray:
+    return (t.view(torch.int16).cpu().numpy().view(np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
+def _rows_np(t: torch.Tensor) -> np.ndarray:
+    if t.dtype == torch.bfloat16:
+        return _bf16_bits_to_f32(t).reshape(t.shape[0], -1)
+    return t.float().cpu().numpy().reshape(t.shape[0], -1)
+
+
+def _grads(scene, rng):
+    b = (scene.sh_degree + 1) ** 2
+    return {"dpos": rng.normal(0, 1e-2, (scene.n, 3)).astype(np.float32),
+            "dlogit": rng.normal(0, 1e-2, scene.n).astype(np.float32),
+            "d_sr": np.concatenate([rng.normal(0, 1e-1, (scene.k_sr, 7)), np.zeros((scene.k_sr, 1))], 1)
+            .astype(np.float32),
+            "d_sh": rng.normal(0, 1e-1, (scene.k_sh, b, 3)).astype(np.float32)}
+
+
+def _check_sgld(scene, bf16: bool, eps: dict, seed: int, step: int):
+    rng = np.random.default_rng(seed)
+    g = _grads(scene, rng)
+    st = cg.SceneTensors.from_scene(scene, codebook_dtype=torch.bfloat16 if bf16 else torch.float32)
+    osc = scene.copy()
+    if bf16:
+        osc.sr_rows = scenes.bf16_round(scene.sr_rows)
+        osc.sh_rows = scenes.bf16_round(scene.sh_rows)
+    dev = {k: torch.from_numpy(v).cuda() for k, v in g.items()}
+    cg.sgld_update(st, dev["dpos"], dev["dlogit"], dev["d_sr"], dev["d_sh"], eps, seed, step)
+    torch.cuda.synchronize()
+    ref = mcmc.sgld_update(osc, g, eps, step, seed, bf16=bf16)
+    got = {"pos": st.pos.cpu().numpy().astype(np.float64), "logit": st.opacity_logit.cpu().numpy().astype(np.float64),
+           "sr": _rows_np(st.sr_rows).astype(np.float64).reshape(ref["sr"].shape),
+           "sh": _rows_np(st.sh_rows).astype(np.float64).reshape(ref["sh"].shape)}
+    x0 = {"pos": osc.pos, "logit": osc.opacity_logit, "sr": osc.sr_rows, "sh": osc.sh_rows}
+    gg = {"pos": g["dpos"], "logit": g["dlogit"], "sr": g["d_sr"], "sh": g["d_sh"]}
+    err = {}
+    for k in ("pos", "logit", "sr", "sh"):
+        e = eps[k]
+        mag = np.abs(x0[k]).astype(np.float64) + 0.5 * e * np.abs(gg[k]) + np.sqrt(e) * 6.0
+        d = np.abs(got[k] - ref[k])
+        if bf16 and k in ("sr", "sh"):
+            step_bf16 = np.ldexp(1.0, np.frexp(np.maximum(np.abs(ref[k]), 1e-30))[1] - 8)
+            assert np.all(d <= step_bf16 * 1.0001), k
+            assert np.mean(d == 0) > 0.99, k
+        else:
+            bound = 2 * 2.0 ** -24 * mag + np.sqrt(e) * 3e-7 * 7.0
+            assert np.all(d <= bound), (k, float((d / bound).max()))
+        err[k] = float(d.max())
+    assert np.array_equal(_rows_np(st.sr_rows)[:, 7], osc.sr_rows[:, 7].astype(np.float32))
+    return err
+
+
+# ----------------------------------------------------------------------------
+# SGLD update
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_sgld_update_matches_oracle(bf16):
+    scene, _ = scenes.config_single(n=50_000, k=512)
+    _check_sgld(scene, bf16, {"pos": 1e-4, "logit": 1e-3, "sr": 1e-4, "sh": 1e-5}, seed=123, step=7)
+
+
+def test_sgld_update_full_size_truck():
+    scene, _ = scenes.config_truck()
+    _check_sgld(scene, False, {"pos": 2e-5, "logit": 1e-3, "sr": 1e-4, "sh": 1e-5}, seed=99, step=12345678901)
+
+
+def test_sgld_update_is_deterministic_and_depends_on_step():
+    scene, _ = scenes.config_tiny()[:2]
+    g = _grads(scene, np.random.default_rng(0))
+    dev = {k: torch.from_numpy(v).cuda() for k, v in g.items()}
+    eps = {"pos": 1e-3, "logit": 1e-3, "sr": 1e-3, "sh": 1e-3}
+    outs = []
+    for step in (5, 5, 6):
+        st = cg.SceneTensors.from_scene(scene)
+        cg.sgld_update(st, dev["dpos"], dev["dlogit"], dev["d_sr"], dev["d_sh"], eps, 1, step)
+        outs.append(st.pos.cpu().clone())
+    assert torch.equal(outs[0], outs[1]) and not torch.equal(outs[0], outs[2])
+
+
+# ----------------------------------------------------------------------------
+# split and merge
+# ----------------------------------------------------------------------------
+
+def _codebook_case(scene, which, bf16, k_cap):
+    rows_np = (scene.sr_rows if which == 0 else scene.sh_rows).reshape(-1, 8 if which == 0 else 3 * (scene.sh_degree + 1) ** 2)
+    k = rows_np.shape[0]
+    if bf16:
+        rows_np = scenes.bf16_round(rows_np)
+    full = np.zeros((k_cap, rows_np.shape[1]), np.float32)
+    full[:k] = rows_np
+    g2x = (scene.g2sr if which == 0 else scene.g2sh).astype(np.int64)
+    if bf16:
+        rows_t = torch.from_numpy(scenes.bf16_bits(full).view(np.int16)).cuda().view(torch.bfloat16)
+    else:
+        rows_t = torch.from_numpy(full).cuda()
+    parent = np.full(k_cap, -1, np.int32)
+    cb = cg.Codebook(which, rows_t, torch.from_numpy(parent).cuda(),
+                     torch.from_numpy(g2x.astype(np.uint16).view(np.int16)).cuda(), k, scene.sh_degree)
+    return cb, full, parent, g2x, k
+
+
+def _state(cb):
+    return (_rows_np(cb.rows), cb.parent.cpu().numpy(), cb.g2x.cpu().numpy().view(np.uint16).astype(np.int64))
+
+
+def _assert_same(cb, ref, k_new):
+    rows, parent, g2x = _state(cb)
+    assert cb.k == ref["k"] == k_new
+    assert np.array_equal(rows[:k_new].view(np.uint32), ref["rows"][:k_new].view(np.uint32))
+    assert np.array_equal(parent[:k_new], ref["parent"][:k_new])
+    assert np.array_equal(g2x, ref["g2x"])
+
+
+SPLIT_CASES = [  # which, bf16, lambda_split, lambda_merge (mixed acceptance at eps 0.1 / 0.3)
+    (0, False, 3.0, 3.0),
+    (1, False, 21.0, 21.0),
+    (1, True, 21.0, 21.0),
+]
+
+
+@pytest.mark.parametrize("which,bf16,lam_s,lam_m", SPLIT_CASES)
+def test_split_then_merge_match_oracle_bitwise(which, bf16, lam_s, lam_m):
+    scene, _ = scenes.config_single(n=40_000, k=1024)
+    k_cap = 65536
+    cb, rows, parent, g2x, k = _codebook_case(scene, which, bf16, k_cap)
+    es, em = 0.1, 0.3
+    k1 = cb.split(lam_s, es, em, seed=7, step=3)
+    sp = mcmc.split(rows, parent, g2x, k, k_cap, which, scene.sh_degree, lam_s, es, em, 3, 7, bf16=bf16)
+    assert k < k1 < k_cap
+    assert 0.05 < sp["proposed_accept"][sp["eligible"]].mean() < 0.95
+    _assert_same(cb, sp, k1)
+    k2 = cb.merge(lam_m, es, em, seed=7, step=4)
+    mg = mcmc.merge(sp["rows"], sp["parent"], sp["g2x"], k1, which, scene.sh_degree, lam_m, es, em, 4, 7)
+    assert k < k2 < k1
+    _assert_same(cb, mg, k2)
+    assert np.all(_state(cb)[1][k2:k1] == -1)
+
+
+def test_split_capacity_and_index_errors():
+    scene, _ = scenes.config_single(n=20_000, k=256)
+    cb, rows, parent, g2x, k = _codebook_case(scene, 0, False, 256 + 5)
+    k1 = cb.split(-100.0, 0.1, 0.05, seed=1, step=1)
+    sp = mcmc.split(rows, parent, g2x, k, 256 + 5, 0, scene.sh_degree, -100.0, 0.1, 0.05, 1, 1)
+    assert k1 == 261
+    _assert_same(cb, sp, 261)
+    # an index past the rows in use: reported, that Gaussian left alone
+    bad = cb.g2x.clone()
+    bad[0] = 300
+    cb2 = cg.Codebook(0, cb.rows.clone(), cb.parent.clone(), bad, 261, scene.sh_degree)
+    with pytest.raises(cg.CgError) as e:
+        cb2.split(2.3, 0.1, 0.05, seed=1, step=2)
+    assert e.value.status == cg.CG_ERR_INDEX
+    assert int(cb2.g2x[0]) == 300
+
+
+def test_split_merge_full_size_truck_paper_hyperparameters():
+    """The truck scene (1.5M Gaussians, 8192 + 8192 rows) with the paper's
+    lambda_SR = 3, lambda_SH = 2.3, eps_split = 0.1, eps_merge = 0.05."""
+    scene, _ = scenes.config_truck()
+    for which, lam in ((0, 3.0), (1, 2.3)):
+        cb, rows, parent, g2x, k = _codebook_case(scene, which, False, 65536)
+        k1 = cb.split(lam, 0.1, 0.05, seed=2025, step=100)
+        sp = mcmc.split(rows, parent, g2x, k, 65536, which, scene.sh_degree, lam, 0.1, 0.05, 100, 2025)
+        _assert_same(cb, sp, k1)
+        k2 = cb.merge(lam, 0.1, 0.05, seed=2025, step=101)
+        mg = mcmc.merge(sp["rows"], sp["parent"], sp["g2x"], k1, which, scene.sh_degree, lam, 0.1, 0.05, 101, 2025)
+        _assert_same(cb, mg, k2)
+
+
+# ----------------------------------------------------------------------------
+# reconstruction loss
+# ----------------------------------------------------------------------------
+
+def _smooth_pair(cams, rng):
+    from scipy import ndimage
+    xs, ys = [], []
+    for c in cams:
+        x = np.clip(ndimage.gaussian_filter(rng.random((3, c.height, c.width)), (0, 2, 2)) * 1.5 - 0.2, 0, 1)
+        y = np.clip(x + rng.normal(0, 0.05, x.shape), 0, 1)
+        y[:, : c.height // 3, : c.width // 4] = x[:, : c.height // 3, : c.width // 4]   # equal region: sign 0
+        xs.append(x.ravel())
+        ys.append(y.ravel())
+    return np.concatenate(xs).astype(np.float32), np.concatenate(ys).astype(np.float32)
+
+
+def _check_loss(x, y, cams, lam=0.2):
+    loss_fn = cg.ReconLoss(cams, lam)
+    xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    loss, d = loss_fn(xt, yt)
+    loss2, d2 = loss_fn(xt, yt)
+    assert torch.equal(loss, loss2) and torch.equal(d, d2)
+    ref = ssim.recon_loss(x, y, cams, lam)
+    got = loss.cpu().numpy()
+    assert abs(got[0] - ref["loss"]) < 1e-6 and abs(got[1] - ref["l1"]) < 1e-9 and abs(got[2] - ref["l_ssim"]) < 1e-6
+    g = d.cpu().numpy().astype(np.float64)
+    want = ref["grad"]
+    bound = 1e-3 * np.abs(want) + 1e-4 * np.abs(want).max()
+    assert np.all(np.abs(g - want) <= bound), float((np.abs(g - want) / bound).max())
+    return {"loss_abs_err": float(abs(got[0] - ref["loss"])), "grad_max_abs_err": float(np.abs(g - want).max()),
+            "grad_max": float(np.abs(want).max())}
+
+
+def test_recon_loss_uneven_views_matches_oracle():
+    rng = np.random.default_rng(3)
+    cams = [types.SimpleNamespace(width=w, height=h, fx=1.0, fy=1.0, cx=0.0, cy=0.0, world_to_cam=np.zeros(12),
+                                  campos=np.zeros(3), near=0.2) for w, h in [(200, 120), (96, 96), (37, 70), (5, 3)]]
+    x, y = _smooth_pair(cams, rng)
+    _check_loss(x, y, cams, 0.2)
+    _check_loss(x, y, cams, 1.0)
+    _check_loss(x, y, cams, 0.0)
+
+
+def test_recon_loss_full_size_truck_render():
+    scene, cams = scenes.config_truck()
+    r = cg.Renderer(cams, pair_capacity=1 << 25)
+    st = cg.SceneTensors.from_scene(scene)
+    img = r.forward(st).clone()
+    tgt_scene = scene.copy()
+    tgt_scene.pos = (scene.pos + np.random.default_rng(1).normal(0, 0.01, scene.pos.shape)).astype(np.float32)
+    tgt = r.forward(cg.SceneTensors.from_scene(tgt_scene)).clone()
+    _check_loss(img.cpu().numpy(), tgt.cpu().numpy(), cams)
+
+
+# ----------------------------------------------------------------------------
+# a whole sampler step in one CUDA graph
+# ----------------------------------------------------------------------------
+
+def test_training_step_with_recon_loss_and_sgld_captured_in_a_graph():
+    scene, cams, target_scene = scenes.config_tiny()
+    r = cg.Renderer(cams, pair_capacity=1 << 20)
+    loss_fn = cg.ReconLoss(cams, 0.2)
+    st = cg.SceneTensors.from_scene(scene)
+    target = r.forward(cg.SceneTensors.from_scene(target_scene)).clone()
+    images = r.forward(st)
+    bufs = {"images": images, "d_images": torch.empty_like(images),
+            "loss": torch.empty(3, dtype=torch.float64, device="cuda"),
+            "d_pos": torch.empty((scene.n, 3), device="cuda"), "d_logit": torch.empty(scene.n, device="cuda"),
+            "d_sr": torch.empty((scene.k_sr, 8), device="cuda"),
+            "d_sh": torch.empty((scene.k_sh, (scene.sh_degree + 1) ** 2, 3), device="cuda")}
+    eps = {"pos": 1e-5, "logit": 1e-4, "sr": 1e-5, "sh": 1e-5}
+    step_no = torch.zeros((), dtype=torch.int64)
+
+    def step():
+        r.forward(st, images=bufs["images"], check=False)
+        loss_fn(bufs["images"], target, d_images=bufs["d_images"], loss=bufs["loss"])
+        r.backward(bufs["d_images"], d_pos=bufs["d_pos"], d_logit=bufs["d_logit"])
+        r.codebook_reduce(d_sr=bufs["d_sr"], d_sh=bufs["d_sh"])
+        cg.sgld_update(st, bufs["d_pos"], bufs["d_logit"], bufs["d_sr"], bufs["d_sh"], eps, 11, 0)
+
+    snap0 = [t.clone() for t in (st.pos, st.opacity_logit, st.sr_rows, st.sh_rows)]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step()
+        step()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    eager = [t.clone() for t in (st.pos, st.opacity_logit, st.sr_rows, st.sh_rows, bufs["loss"])]
+    for t, v in zip((st.pos, st.opacity_logit, st.sr_rows, st.sh_rows), snap0):
+        t.copy_(v)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    for t, v in zip((st.pos, st.opacity_logit, st.sr_rows, st.sh_rows), snap0):
+        t.copy_(v)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert r.status()[0] == cg.CG_OK
+    for a, b in zip(eager, (st.pos, st.opacity_logit, st.sr_rows, st.sh_rows, bufs["loss"])):
+        assert torch.equal(a, b)
+    assert not torch.equal(eager[0], snap0[0])

@@ -111,3 +111,51 @@ def test_host_tile_keep_matches_oracle(lib):
         mine = lib.cg_host_tile_keep(geo.ctypes.data_as(ctypes.c_void_p), tx, ty, 16)
         assert bool(mine) == oracle.tile_keep32(*[float(v) for v in geo], tx, ty, 16)
     assert n_checked > 10000
+
+
+def test_host_draws_match_oracle_bitwise(lib):
+    """The sampler's draws decide integer outcomes (split / merge
+    acceptance): Philox outputs, Box-Muller normals and the log and sin/cos
+    they are built from agree bit for bit with the oracle's."""
+    from oracle import mcmc
+    rng = np.random.default_rng(12)
+    ctr = rng.integers(0, 2 ** 32, (500, 4), dtype=np.uint64)
+    key = rng.integers(0, 2 ** 32, (500, 2), dtype=np.uint64)
+    want = mcmc.philox4x32_10(ctr, key)
+    for i in range(500):
+        assert np.array_equal(cg.host_philox(ctr[i], key[i]), want[i])
+    bits = rng.integers(0, 2 ** 32, (3000, 4), dtype=np.uint64).astype(np.uint32)
+    bits[:4] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [0xFF, 0x1FF, 0x3FFFFFFF, 0x40000000], [0x7FFFFF00, 0xBFFFFF00, 1, 2]]
+    want = mcmc.normals32(bits)
+    mine = np.stack([cg.host_normal4(b) for b in bits])
+    assert np.array_equal(mine.view(np.uint32), want.view(np.uint32))
+    x = np.concatenate([rng.uniform(1e-7, 1, 3000), [2.0 ** -24, 0.5, 1.0, 1.4142135, 1.4142137]]).astype(np.float32)
+    assert np.array_equal(np.array([lib.cg_host_log32(float(v)) for v in x], np.float32).view(np.uint32),
+                          mcmc.log32(x).view(np.uint32))
+    u = (rng.integers(0, 2 ** 24, 3000) * 2.0 ** -24).astype(np.float32)
+    s_ref, c_ref = mcmc.sincos2pi32(u)
+    out = np.zeros(2, dtype=np.float32)
+    for i, v in enumerate(u):
+        lib.cg_host_sincos2pi32(float(v), out.ctypes.data_as(ctypes.c_void_p))
+        assert out[0].view(np.uint32) == s_ref[i].view(np.uint32) and out[1].view(np.uint32) == c_ref[i].view(np.uint32)
+
+
+def test_sampler_and_loss_argument_checks(lib):
+    o = cg.MhOpts(0, 100, 10, 8, 3, cg.CG_F32, 2.3, 0.1, 0.05, 1, 2)      # k > k_cap
+    assert lib.cg_mh_workspace_bytes(ctypes.byref(o)) == 0
+    o.k_cap = 70000
+    assert lib.cg_mh_workspace_bytes(ctypes.byref(o)) == 0
+    o.k_cap, o.eps_split = 64, 0.0
+    assert lib.cg_mh_workspace_bytes(ctypes.byref(o)) == 0
+    o.eps_split = 0.1
+    assert lib.cg_mh_workspace_bytes(ctypes.byref(o)) > 0
+    assert lib.cg_codebook_split(ctypes.byref(o), None, None, None, None, None, 0, None) == cg.CG_ERR_ARG
+    p = cg.Params(10, 4, 4, 1, cg.CG_F32, 256, 256, 256, 256)
+    s = cg.SgldOpts(-1.0, 0.0, 0.0, 0.0, 1, 1)
+    d = ctypes.c_void_p(256)
+    assert lib.cg_sgld_update(ctypes.byref(p), d, d, d, d, ctypes.byref(s), None) == cg.CG_ERR_ARG
+    cams = cg.camera_array([type("C", (), dict(width=40, height=30, fx=1, fy=1, cx=0, cy=0,
+                                                world_to_cam=np.zeros(12), campos=np.zeros(3), near=0.2))()])
+    n = lib.cg_recon_workspace_bytes(cams, 1)
+    assert n >= 16 * 3 * 2   # one slot per CTA (3 channels x 2 tiles of 32 x 32)
+    assert lib.cg_recon_loss(d, d, cams, 1, 1.5, d, d, d, n, None) == cg.CG_ERR_ARG   # lambda > 1
