@@ -164,6 +164,10 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
   L->csr_ids_sr = take(sizeof(uint32_t) * n);
   L->csr_ids_sh = take(sizeof(uint32_t) * n);
   L->chunks = take(sizeof(uint4) * L->chunks_cap);
+  L->chunks_sh = take(sizeof(uint4) * L->chunks_cap);
+  L->csr_idx_sr = take(sizeof(uint16_t) * n);
+  L->csr_idx_sh = take(sizeof(uint16_t) * n);
+  L->csr_state = take(2 * sizeof(CsrState));
   L->partials = take(sizeof(float) * std::max(6, 3 * nb) * L->chunks_cap);
   L->hist = take(sizeof(uint32_t) * (256 * L->sort_blocks_cap + 256));
   L->blocksums = take(sizeof(uint64_t) * L->scan_blocks_cap);
@@ -198,6 +202,7 @@ SceneArgs scene_args(const cg_scene* s) {
   a.dtype = (int)s->cb_dtype;
   a.pos = s->pos; a.logit = s->opacity_logit; a.g2sr = s->g2sr; a.g2sh = s->g2sh;
   a.sr_rows = s->sr_rows; a.sh_rows = s->sh_rows;
+  a.sh_vec = aligned(s->sh_rows, 16) ? 1 : 0;
   return a;
 }
 

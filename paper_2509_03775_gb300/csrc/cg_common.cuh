@@ -265,7 +265,8 @@ struct ViewTable {
 struct Layout {
   uint64_t total;
   uint64_t hdr, views, sigma3, geo, rgbm, rect, ntiles, depth, offrec, scan, dkeys0, dkeys1, pairs0, pairs1,
-      ranges, tfinal, ncontrib, pairgrad, pairgrad1, recgrad, nemit, kmask, dsigma, drgb, csr_keys0, csr_keys1, csr_off_sr, csr_off_sh, csr_ids_sr, csr_ids_sh, chunks,
+      ranges, tfinal, ncontrib, pairgrad, pairgrad1, recgrad, nemit, kmask, dsigma, drgb, csr_keys0, csr_keys1, csr_off_sr, csr_off_sh, csr_ids_sr, csr_ids_sh, chunks, chunks_sh,
+      csr_idx_sr, csr_idx_sh, csr_state,
       partials, hist, blocksums, l1;
   // sizes
   int64_t n, R, T, P, Kc;
@@ -274,6 +275,20 @@ struct Layout {
   int64_t scan_blocks_cap;   // capacity of the per-block scan sums
   int64_t chunks_cap;        // capacity of the codebook-reduction chunk table
 };
+
+// Codebook membership (CSR) cache of one codebook: the row index array it
+// was built from is kept (csr_idx_*), and the build is repeated only when
+// the key (array address, n, k) or any index differs.
+struct CsrState {
+  uint64_t magic;
+  uint64_t idx_ptr;
+  uint32_t k;
+  uint32_t n;
+  uint32_t changed;   // set by the check, cleared when the build is done
+  uint32_t pad;
+  uint64_t nchunks;   // chunks of the cached build
+};
+constexpr uint64_t kCsrMagic = 0x43535243'00000001ull;
 
 // Device-written status and counters (in the header).
 struct DeviceState {
@@ -309,6 +324,62 @@ __device__ __forceinline__ float load_row(const void* rows, int dtype, size_t i)
   return reinterpret_cast<const float*>(rows)[i];
 }
 
+// One SH row (3 NB values, [basis][colour]) widened to FP32.  With `vec`
+// (16-byte aligned rows base) rows of a multiple of 8 (BF16) or 4 (FP32)
+// values are read with 16- / 8-byte loads; the values are the same.
+template <int NB>
+__device__ __forceinline__ void load_sh_row(const void* rows, int dtype, int vec, uint32_t row,
+                                            float (&c)[3 * NB]) {
+  constexpr int V = 3 * NB;
+  const size_t base = (size_t)row * V;
+  if (dtype == CG_BF16) {
+    const uint16_t* p = reinterpret_cast<const uint16_t*>(rows) + base;
+    if constexpr (V % 8 == 0) {
+      if (vec) {
+#pragma unroll
+        for (int j = 0; j < V / 8; ++j) {
+          const uint4 u = __ldg(reinterpret_cast<const uint4*>(p) + j);
+          const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            c[8 * j + 2 * h] = bits_to_float(w[h] << 16);
+            c[8 * j + 2 * h + 1] = bits_to_float(w[h] & 0xffff0000u);
+          }
+        }
+        return;
+      }
+    } else if constexpr (V % 4 == 0) {
+      if (vec) {
+#pragma unroll
+        for (int j = 0; j < V / 4; ++j) {
+          const uint2 u = __ldg(reinterpret_cast<const uint2*>(p) + j);
+          c[4 * j] = bits_to_float(u.x << 16);
+          c[4 * j + 1] = bits_to_float(u.x & 0xffff0000u);
+          c[4 * j + 2] = bits_to_float(u.y << 16);
+          c[4 * j + 3] = bits_to_float(u.y & 0xffff0000u);
+        }
+        return;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) c[j] = bits_to_float((uint32_t)__ldg(p + j) << 16);
+  } else {
+    const float* p = reinterpret_cast<const float*>(rows) + base;
+    if constexpr (V % 4 == 0) {
+      if (vec) {
+#pragma unroll
+        for (int j = 0; j < V / 4; ++j) {
+          const float4 u = __ldg(reinterpret_cast<const float4*>(p) + j);
+          c[4 * j] = u.x, c[4 * j + 1] = u.y, c[4 * j + 2] = u.z, c[4 * j + 3] = u.w;
+        }
+        return;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) c[j] = __ldg(p + j);
+  }
+}
+
 __device__ __forceinline__ int find_view(const ViewInfo* views, int n_views, int64_t gtile) {
   int v = 0;
   while (v + 1 < n_views && views[v + 1].tile_base <= gtile) ++v;
@@ -323,6 +394,7 @@ void count_launch();
 // ----------------------------------------------------------------------------
 struct SceneArgs {
   int n, k_sr, k_sh, nb, dtype;
+  int sh_vec;  // sh_rows is 16-byte aligned: whole rows may be read with vector loads
   const float* pos;
   const float* logit;
   const uint16_t* g2sr;

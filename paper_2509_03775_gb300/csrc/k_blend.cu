@@ -269,6 +269,10 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const Bl
     my_max = max(my_max, px.nc[k]);
   }
   atomicMax(&s_maxc, my_max);
+  // list positions at or past the warp's largest contributor count give
+  // this warp's pixels nothing: the warp skips them (their partial sums are
+  // the zeros the butterfly would have produced)
+  const uint32_t warp_max = __reduce_max_sync(0xffffffffu, my_max);
   __syncthreads();
   const uint32_t maxc = s_maxc;
   const uint32_t len = rg.y - rg.x;
@@ -296,7 +300,10 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const Bl
     }
     __syncthreads();
     const uint32_t pos0 = (uint32_t)(b0 - rg.x);
-    for (int j = n_in - 1; j >= 0; j -= 3) {
+    // first batch entry this warp must walk: positions < warp_max
+    const int j_top = (int)max((int64_t)-1, min((int64_t)n_in, (int64_t)warp_max - (int64_t)pos0) - 1);
+    for (int i = lane; i < (n_in - 1 - j_top) * 9; i += 32) part[wid][j_top + 1 + i / 9][i % 9] = 0.0f;
+    for (int j = j_top; j >= 0; j -= 3) {
       float g[32];
 #pragma unroll
       for (int e = 0; e < 32; ++e) g[e] = 0.0f;

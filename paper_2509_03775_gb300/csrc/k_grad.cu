@@ -64,7 +64,7 @@ template <int NB>
 __device__ __forceinline__ void record_chain(const SceneArgs& sc, const ViewInfo* __restrict__ views,
                                            const float* __restrict__ sig3, const float4* __restrict__ geo,
                                            const float4* __restrict__ rgbm, uint32_t rec, const float (&gs)[9],
-                                           float* __restrict__ rg, float* __restrict__ drgb) {
+                                           float (&out)[10], float* __restrict__ drgb) {
   const int v = (int)(rec / (uint32_t)sc.n);
   const int64_t g = (int64_t)rec - (int64_t)v * sc.n;
   const float p[3] = {sc.pos[3 * g], sc.pos[3 * g + 1], sc.pos[3 * g + 2]};
@@ -89,12 +89,11 @@ __device__ __forceinline__ void record_chain(const SceneArgs& sc, const ViewInfo
   float Y[kMaxBasis], Dx[kMaxBasis], Dy[kMaxBasis], Dz[kMaxBasis];
   sh_basis_grad<NB>(dir[0], dir[1], dir[2], Y, Dx, Dy, Dz);
   float dd[3] = {0.0f, 0.0f, 0.0f};
-  const size_t rb = (size_t)ish * NB * 3;
+  float shr[3 * NB];
+  load_sh_row<NB>(sc.sh_rows, sc.dtype, sc.sh_vec, ish, shr);
 #pragma unroll
   for (int k = 0; k < NB; ++k) {
-    const float dyk = fmaf(dc[0], load_row(sc.sh_rows, sc.dtype, rb + 3 * k),
-                           fmaf(dc[1], load_row(sc.sh_rows, sc.dtype, rb + 3 * k + 1),
-                                dc[2] * load_row(sc.sh_rows, sc.dtype, rb + 3 * k + 2)));
+    const float dyk = fmaf(dc[0], shr[3 * k], fmaf(dc[1], shr[3 * k + 1], dc[2] * shr[3 * k + 2]));
     dd[0] = fmaf(dyk, Dx[k], dd[0]);
     dd[1] = fmaf(dyk, Dy[k], dd[1]);
     dd[2] = fmaf(dyk, Dz[k], dd[2]);
@@ -161,7 +160,6 @@ __device__ __forceinline__ void record_chain(const SceneArgs& sc, const ViewInfo
           2.0f * fy * t[1] * iz2 * iz * dJ[5] - fx * t[0] * iz2 * gmx - fy * t[1] * iz2 * gmy;
 #pragma unroll
   for (int k = 0; k < 3; ++k) dp[k] += fmaf(W[k], dt[0], fmaf(W[4 + k], dt[1], W[8 + k] * dt[2]));
-  float* out = rg + 10 * (size_t)rec;
   out[0] = dp[0];
   out[1] = dp[1];
   out[2] = dp[2];
@@ -170,107 +168,99 @@ __device__ __forceinline__ void record_chain(const SceneArgs& sc, const ViewInfo
   for (int e = 0; e < 6; ++e) out[4 + e] = dsg[e];
 }
 
-// Visible (view, Gaussian) records in depth order, 32 per warp.  The slots
-// of a warp's records form one contiguous range (their offsets were scanned
-// in depth order), which the warp reads coalesced, 32 slots at a time; a
-// segmented shuffle scan over each group of 32 slots (segments = records)
-// adds each record's slots in a fixed order.  Then lane l applies the chain
-// rule of the opacity, the colour (clamp mask, SH direction) and the
-// projection for record l and writes its position, logit and Sigma
-// gradients to rg[rec][10] and its masked colour gradient to drgb.
-template <int NB>
-__global__ void __launch_bounds__(256) k_record_bwd(const SceneArgs sc, const ViewInfo* __restrict__ views,
-                                                    const float* __restrict__ sig3, const float4* __restrict__ geo,
-                                                    const float4* __restrict__ rgbm,
-                                                    const uint32_t* __restrict__ nemit,
-                                                    const uint32_t* __restrict__ offrec,
-                                                    const float4* __restrict__ pairgrad,
-                                                    const float* __restrict__ pairgrad1,
-                                                    const uint64_t* __restrict__ dsorted, const DeviceState* st,
-                                                    float* __restrict__ rg, float* __restrict__ drgb) {
-  __shared__ uint32_t sOff[8][32];
-  __shared__ float sAcc[8][32][9];
+// Visible (view, Gaussian) records in depth order; a group of 8 lanes
+// takes one record (a warp takes 4 consecutive records at a time).  The
+// record's slots are contiguous: lane j of the group adds slots j, j + 8,
+// j + 16, ... in order (the group's loads are one contiguous span), then a
+// fixed 3-step butterfly over the group adds the 8 partial sums.  The nine
+// sums of each record go to rg[rec][0..8].
+constexpr int kSlotGroup = 8;
+
+__device__ __forceinline__ void load_slot(const float4* __restrict__ pairgrad, const float* __restrict__ pairgrad1,
+                                          uint32_t slot, float (&v)[9]) {
+  const float4 u = __ldcs(pairgrad + 2 * (size_t)slot), w = __ldcs(pairgrad + 2 * (size_t)slot + 1);
+  v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w; v[4] = w.x;
+  v[5] = __ldcs(pairgrad1 + slot);
+  v[6] = w.y; v[7] = w.z; v[8] = w.w;
+}
+
+__global__ void __launch_bounds__(256) k_slot_sum(const uint32_t* __restrict__ nemit,
+                                                  const uint32_t* __restrict__ offrec,
+                                                  const float4* __restrict__ pairgrad,
+                                                  const float* __restrict__ pairgrad1,
+                                                  const uint64_t* __restrict__ dsorted, const DeviceState* st,
+                                                  float* __restrict__ rg) {
   if (st->pairs_ok == 0) return;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int kPerWarp = 32 / kSlotGroup;
+  const int lane = threadIdx.x & 31, sub = lane & (kSlotGroup - 1), grp = lane / kSlotGroup;
   const int64_t vis = (int64_t)st->visible;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = warp * 32; base < vis; base += nwarps * 32) {
-    const int64_t i = base + lane;
-    const int cnt = (int)min((int64_t)32, vis - base);
+  for (int64_t base = warp * kPerWarp; base < vis; base += nwarps * kPerWarp) {
+    const int64_t i = base + grp;
     uint32_t rec = 0, off = 0, nt = 0;
     if (i < vis) {
       rec = (uint32_t)dsorted[i];
       off = offrec[rec];
       nt = nemit[rec];
     }
-    sOff[wid][lane] = off;
+    float acc[9];
 #pragma unroll
-    for (int e = 0; e < 9; ++e) sAcc[wid][lane][e] = 0.0f;
-    const uint32_t s0 = __shfl_sync(0xffffffffu, off, 0);
-    const uint32_t s1 = __shfl_sync(0xffffffffu, off + nt, cnt - 1);
-    __syncwarp();
-    for (uint32_t c0 = s0; c0 < s1; c0 += 32) {
-      const uint32_t slot = c0 + lane;
-      const bool valid = slot < s1;
-      // owner: the last record of the warp whose offset is <= slot
-      int own = 0;
+    for (int e = 0; e < 9; ++e) acc[e] = 0.0f;
+    uint32_t t = sub;
+    for (; t + kSlotGroup < nt; t += 2 * kSlotGroup) {
+      float v0[9], v1[9];
+      load_slot(pairgrad, pairgrad1, off + t, v0);
+      load_slot(pairgrad, pairgrad1, off + t + kSlotGroup, v1);
 #pragma unroll
-      for (int stp = 16; stp > 0; stp >>= 1)
-        if (own + stp < cnt && sOff[wid][own + stp] <= slot) own += stp;
-      float v[9];
-      if (valid) {
-        const float4 u = pairgrad[2 * (size_t)slot], w = pairgrad[2 * (size_t)slot + 1];
-        v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w; v[4] = w.x;
-        v[5] = pairgrad1[slot];
-        v[6] = w.y; v[7] = w.z; v[8] = w.w;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 9; ++e) v[e] = 0.0f;
-        own = 32;
-      }
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const int own_up = __shfl_up_sync(0xffffffffu, own, d);
-#pragma unroll
-        for (int e = 0; e < 9; ++e) {
-          const float up = __shfl_up_sync(0xffffffffu, v[e], d);
-          if (lane >= d && own_up == own) v[e] += up;
-        }
-      }
-      const int own_next = __shfl_down_sync(0xffffffffu, own, 1);
-      if (valid && (lane == 31 || own_next != own)) {
-#pragma unroll
-        for (int e = 0; e < 9; ++e) sAcc[wid][own][e] += v[e];
-      }
-      __syncwarp();
+      for (int e = 0; e < 9; ++e) acc[e] = (acc[e] + v0[e]) + v1[e];
     }
-    if (i < vis) {
-      float gs[9];
+    if (t < nt) {
+      float v0[9];
+      load_slot(pairgrad, pairgrad1, off + t, v0);
 #pragma unroll
-      for (int e = 0; e < 9; ++e) gs[e] = sAcc[wid][lane][e];
-      record_chain<NB>(sc, views, sig3, geo, rgbm, rec, gs, rg, drgb);
+      for (int e = 0; e < 9; ++e) acc[e] += v0[e];
     }
-    __syncwarp();
+#pragma unroll
+    for (int d = kSlotGroup / 2; d > 0; d >>= 1)
+#pragma unroll
+      for (int e = 0; e < 9; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], d);
+    if (sub == 0 && i < vis) {
+      float* out = rg + 10 * (size_t)rec;
+#pragma unroll
+      for (int e = 0; e < 9; ++e) out[e] = acc[e];
+    }
   }
 }
 
-// Per Gaussian: the sum over views, in view order, of its visible records'
-// gradients; culled records contribute zero (and get a zero colour gradient).
-__global__ void __launch_bounds__(256) k_gauss_sum(int64_t n, int n_views, const uint32_t* __restrict__ ntiles,
-                                                   const float* __restrict__ rg, const DeviceState* st,
-                                                   float* __restrict__ d_pos, float* __restrict__ d_logit,
-                                                   float* __restrict__ dsigma, float* __restrict__ drgb) {
+// Per Gaussian: for each view in order, the chain rule of its record (the
+// opacity, the colour through the clamp mask and the SH direction, the
+// projection) applied to the record's nine sums, and the sum over views of
+// the position, logit and Sigma gradients; culled records contribute zero
+// (and get a zero colour gradient).
+template <int NB>
+__global__ void __launch_bounds__(256, 3) k_chain_sum(const SceneArgs sc, int n_views, const ViewInfo* __restrict__ views,
+                                                   const float* __restrict__ sig3, const float4* __restrict__ geo,
+                                                   const float4* __restrict__ rgbm,
+                                                   const uint32_t* __restrict__ ntiles, const float* __restrict__ rg,
+                                                   const DeviceState* st, float* __restrict__ d_pos,
+                                                   float* __restrict__ d_logit, float* __restrict__ dsigma,
+                                                   float* __restrict__ drgb) {
   const bool ok = st->pairs_ok != 0;
+  const int64_t n = sc.n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += stride) {
     float acc[10] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     for (int v = 0; v < n_views; ++v) {
       const int64_t rec = (int64_t)v * n + g;
       if (ok && ntiles[rec] > 0) {
+        float gs[9], out[10];
         const float* r = rg + 10 * (size_t)rec;
 #pragma unroll
-        for (int e = 0; e < 10; ++e) acc[e] += r[e];
+        for (int e = 0; e < 9; ++e) gs[e] = r[e];
+        record_chain<NB>(sc, views, sig3, geo, rgbm, (uint32_t)rec, gs, out, drgb);
+#pragma unroll
+        for (int e = 0; e < 10; ++e) acc[e] += out[e];
       } else {
         drgb[3 * rec] = drgb[3 * rec + 1] = drgb[3 * rec + 2] = 0.0f;
       }
@@ -300,17 +290,18 @@ cudaError_t launch_gaussian_bwd(const SceneArgs& sc, const Layout& L, void* ws, 
   float* drgb = ws_ptr<float>(ws, L.drgb);
   const uint64_t* dsorted = depth_sorted(ws, L);
   const int grid_r = (int)std::max<int64_t>(1, std::min<int64_t>((L.R + 255) / 256, 152 * 16));
-#define CG_RB(NBV) count_launch(), k_record_bwd<NBV><<<grid_r, 256, 0, s>>>(sc, views, sig, geo, rgbm, ws_ptr<const uint32_t>(ws, L.nemit), off, pg, pg1, dsorted, &hdr->st, rg, drgb)
+  count_launch(), k_slot_sum<<<grid_r, 256, 0, s>>>(ws_ptr<const uint32_t>(ws, L.nemit), off, pg, pg1, dsorted,
+                                                    &hdr->st, rg);
+  const int grid_g = (int)std::max<int64_t>(1, std::min<int64_t>((L.n + 255) / 256, 152 * 16));
+#define CG_CS(NBV) count_launch(), k_chain_sum<NBV><<<grid_g, 256, 0, s>>>(sc, L.n_views, views, sig, geo, rgbm, nt, rg, &hdr->st, d_pos, d_logit, dsig, drgb)
   switch (sc.nb) {
-    case 1: CG_RB(1); break;
-    case 4: CG_RB(4); break;
-    case 9: CG_RB(9); break;
-    case 16: CG_RB(16); break;
+    case 1: CG_CS(1); break;
+    case 4: CG_CS(4); break;
+    case 9: CG_CS(9); break;
+    case 16: CG_CS(16); break;
     default: return cudaErrorInvalidValue;
   }
-#undef CG_RB
-  const int grid_g = (int)std::max<int64_t>(1, std::min<int64_t>((L.n + 255) / 256, 152 * 16));
-  count_launch(), k_gauss_sum<<<grid_g, 256, 0, s>>>(L.n, L.n_views, nt, rg, &hdr->st, d_pos, d_logit, dsig, drgb);
+#undef CG_CS
   return cudaGetLastError();
 }
 
@@ -321,7 +312,11 @@ cudaError_t launch_gaussian_bwd(const SceneArgs& sc, const Layout& L, void* ws, 
 // Keys (row << 32 | g); an index >= k (already reported by the forward) is
 // keyed past the last row.
 __global__ void k_row_keys(const uint16_t* __restrict__ idx, int64_t n, int k, uint64_t* __restrict__ keys,
-                           uint64_t* count_slot) {
+                           uint64_t* count_slot, const CsrState* cs) {
+  if (!cs->changed) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *count_slot = 0;
+    return;
+  }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += stride) {
     const uint32_t r = idx[g];
@@ -330,7 +325,8 @@ __global__ void k_row_keys(const uint16_t* __restrict__ idx, int64_t n, int k, u
   if (blockIdx.x == 0 && threadIdx.x == 0) *count_slot = (uint64_t)n;
 }
 
-__global__ void k_zero_counts(uint32_t* c, int64_t m) {
+__global__ void k_zero_counts(uint32_t* c, int64_t m, const CsrState* cs) {
+  if (cs && !cs->changed) return;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) c[i] = 0u;
 }
@@ -338,7 +334,8 @@ __global__ void k_zero_counts(uint32_t* c, int64_t m) {
 // Member ids and [start, end) of every row from the keys sorted by row
 // (rows without members keep start = end = 0).
 __global__ void k_row_bounds(const uint64_t* __restrict__ keys, int64_t n, int k, uint32_t* __restrict__ start,
-                             uint32_t* __restrict__ end, uint32_t* __restrict__ ids) {
+                             uint32_t* __restrict__ end, uint32_t* __restrict__ ids, const CsrState* cs) {
+  if (!cs->changed) return;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const uint64_t key = keys[i];
@@ -352,7 +349,11 @@ __global__ void k_row_bounds(const uint64_t* __restrict__ keys, int64_t n, int k
 
 // chunks per row: ceil(count / kChunk)
 __global__ void k_chunk_counts(const uint32_t* __restrict__ start, const uint32_t* __restrict__ end, int k,
-                               uint32_t* __restrict__ nch, uint64_t* count_slot) {
+                               uint32_t* __restrict__ nch, uint64_t* count_slot, const CsrState* cs) {
+  if (!cs->changed) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *count_slot = 0;
+    return;
+  }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < k; r += stride)
     nch[r] = (end[r] - start[r] + kChunk - 1) / kChunk;
@@ -361,7 +362,9 @@ __global__ void k_chunk_counts(const uint32_t* __restrict__ start, const uint32_
 
 // chunk c of row r covers member positions [start_r + c*kChunk, min(.., end_r))
 __global__ void k_fill_chunks(const uint32_t* __restrict__ start, const uint32_t* __restrict__ end,
-                              const uint32_t* __restrict__ chunk_base, int k, uint4* __restrict__ chunks) {
+                              const uint32_t* __restrict__ chunk_base, int k, uint4* __restrict__ chunks,
+                              const CsrState* cs) {
+  if (!cs->changed) return;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < k; r += stride) {
     const uint32_t b = start[r], e = end[r], cb = chunk_base[r];
@@ -557,8 +560,40 @@ __global__ void __launch_bounds__(256) k_sh_rows(const uint32_t* __restrict__ st
 
 // CSR of one index array: member ids (by row, then Gaussian), row bounds,
 // chunk bases and the chunk table (chunk count in *chunks_dev).
-static cudaError_t build_csr(void* ws, const Layout& L, const uint16_t* idx, int k, uint32_t* csr, uint32_t* ids,
-                             uint4* chunks, DeviceState* st, cudaStream_t s) {
+// Compares the index array with the copy the cached build was made from
+// (and the cache key); marks the cache stale on any difference and updates
+// the copy.
+__global__ void __launch_bounds__(256) k_csr_check(const uint16_t* __restrict__ idx, uint16_t* __restrict__ copy,
+                                                   int64_t n, int k, CsrState* cs) {
+  bool diff = cs->magic != kCsrMagic || cs->idx_ptr != (uint64_t)(uintptr_t)idx || cs->k != (uint32_t)k ||
+              cs->n != (uint32_t)n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += stride) {
+    const uint16_t v = idx[g];
+    if (copy[g] != v) {
+      diff = true;
+      copy[g] = v;
+    }
+  }
+  if (__syncthreads_or(diff) && threadIdx.x == 0) atomicOr(&cs->changed, 1u);
+}
+
+// Records the chunk count and the key of a new build; clears the flag.
+__global__ void k_csr_done(CsrState* cs, const uint64_t* nchunks_dev, const uint16_t* idx, int64_t n, int k) {
+  if (!cs->changed) return;
+  cs->nchunks = *nchunks_dev;
+  cs->magic = kCsrMagic;
+  cs->idx_ptr = (uint64_t)(uintptr_t)idx;
+  cs->k = (uint32_t)k;
+  cs->n = (uint32_t)n;
+  cs->changed = 0u;
+}
+
+// Membership of one codebook (rows -> members in index order, chunks of
+// kChunk members), rebuilt only when its index array changed since the
+// cached build; every kernel of the build returns at once otherwise.
+static cudaError_t build_csr(void* ws, const Layout& L, const uint16_t* idx, uint16_t* copy, int k, uint32_t* csr,
+                             uint32_t* ids, uint4* chunks, CsrState* cs, DeviceState* st, cudaStream_t s) {
   const int64_t n = L.n;
   uint32_t* start = csr;
   uint32_t* end = csr + k;
@@ -567,16 +602,18 @@ static cudaError_t build_csr(void* ws, const Layout& L, const uint16_t* idx, int
   uint64_t* k1 = ws_ptr<uint64_t>(ws, L.csr_keys1);
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
   const int gk = std::max(1, std::min((2 * k + 255) / 256, 152 * 8));
-  count_launch(), k_zero_counts<<<gk, 256, 0, s>>>(start, 2 * (int64_t)k);
-  count_launch(), k_row_keys<<<g, 256, 0, s>>>(idx, n, k, k0, &st->red_a);
+  count_launch(), k_csr_check<<<g, 256, 0, s>>>(idx, copy, n, k, cs);
+  count_launch(), k_zero_counts<<<gk, 256, 0, s>>>(start, 2 * (int64_t)k, cs);
+  count_launch(), k_row_keys<<<g, 256, 0, s>>>(idx, n, k, k0, &st->red_a, cs);
   bool in_b = false;
   cudaError_t e = sort_u64(ws, L, k0, k1, &st->red_a, n, 32, k >= 65536 ? 3 : 2, &in_b, s);
   if (e != cudaSuccess) return e;
-  count_launch(), k_row_bounds<<<g, 256, 0, s>>>(in_b ? k1 : k0, n, k, start, end, ids);
-  count_launch(), k_chunk_counts<<<gk, 256, 0, s>>>(start, end, k, cbase, &st->red_b);
+  count_launch(), k_row_bounds<<<g, 256, 0, s>>>(in_b ? k1 : k0, n, k, start, end, ids, cs);
+  count_launch(), k_chunk_counts<<<gk, 256, 0, s>>>(start, end, k, cbase, &st->red_b, cs);
   e = scan_u32(ws, L, cbase, cbase, &st->red_b, k, &st->red_a, s);  // red_a <- chunk count
   if (e != cudaSuccess) return e;
-  count_launch(), k_fill_chunks<<<gk, 256, 0, s>>>(start, end, cbase, k, chunks);
+  count_launch(), k_fill_chunks<<<gk, 256, 0, s>>>(start, end, cbase, k, chunks, cs);
+  count_launch(), k_csr_done<<<1, 1, 0, s>>>(cs, &st->red_a, idx, n, k);
   return cudaGetLastError();
 }
 
@@ -585,24 +622,28 @@ cudaError_t launch_codebook_reduce(const SceneArgs& sc, const Layout& L, void* w
   WsHeader* hdr = ws_ptr<WsHeader>(ws, L.hdr);
   DeviceState* st = &hdr->st;
   uint4* chunks = ws_ptr<uint4>(ws, L.chunks);
+  uint4* chunks_sh = ws_ptr<uint4>(ws, L.chunks_sh);
+  CsrState* cs = ws_ptr<CsrState>(ws, L.csr_state);
   float* part = ws_ptr<float>(ws, L.partials);
   const int gw = 152 * 8;
   // SR rows
   uint32_t* csr_sr = ws_ptr<uint32_t>(ws, L.csr_off_sr);
-  cudaError_t e = build_csr(ws, L, sc.g2sr, sc.k_sr, csr_sr, ws_ptr<uint32_t>(ws, L.csr_ids_sr), chunks, st, s);
+  cudaError_t e = build_csr(ws, L, sc.g2sr, ws_ptr<uint16_t>(ws, L.csr_idx_sr), sc.k_sr, csr_sr,
+                            ws_ptr<uint32_t>(ws, L.csr_ids_sr), chunks, &cs[0], st, s);
   if (e != cudaSuccess) return e;
-  count_launch(), k_sr_partials<<<gw, 256, 0, s>>>(chunks, &st->red_a, ws_ptr<uint32_t>(ws, L.csr_ids_sr),
+  count_launch(), k_sr_partials<<<gw, 256, 0, s>>>(chunks, &cs[0].nchunks, ws_ptr<uint32_t>(ws, L.csr_ids_sr),
                                                    ws_ptr<float>(ws, L.dsigma), part);
   count_launch(), k_sr_rows<<<(sc.k_sr + 7) / 8, 256, 0, s>>>(csr_sr, csr_sr + sc.k_sr, csr_sr + 2 * (int64_t)sc.k_sr,
                                                               sc.k_sr, part, sc.sr_rows, sc.dtype, d_sr);
   // SH rows
   uint32_t* csr_sh = ws_ptr<uint32_t>(ws, L.csr_off_sh);
-  e = build_csr(ws, L, sc.g2sh, sc.k_sh, csr_sh, ws_ptr<uint32_t>(ws, L.csr_ids_sh), chunks, st, s);
+  e = build_csr(ws, L, sc.g2sh, ws_ptr<uint16_t>(ws, L.csr_idx_sh), sc.k_sh, csr_sh,
+                ws_ptr<uint32_t>(ws, L.csr_ids_sh), chunks_sh, &cs[1], st, s);
   if (e != cudaSuccess) return e;
   const ViewInfo* views = ws_ptr<ViewInfo>(ws, L.views);
   const uint32_t* ids = ws_ptr<uint32_t>(ws, L.csr_ids_sh);
   const float* drgb = ws_ptr<float>(ws, L.drgb);
-#define CG_SHP(NBV) count_launch(), k_sh_partials<NBV><<<gw, 256, 0, s>>>(chunks, &st->red_a, ids, sc.pos, views, L.n_views, L.n, drgb, part)
+#define CG_SHP(NBV) count_launch(), k_sh_partials<NBV><<<gw, 256, 0, s>>>(chunks_sh, &cs[1].nchunks, ids, sc.pos, views, L.n_views, L.n, drgb, part)
   switch (sc.nb) {
     case 1: CG_SHP(1); break;
     case 4: CG_SHP(4); break;

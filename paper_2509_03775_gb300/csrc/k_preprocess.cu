@@ -118,14 +118,15 @@ __global__ void __launch_bounds__(256) k_preprocess(const SceneArgs sc, const Vi
     const float nrm = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
     float Y[kMaxBasis];
     sh_basis32(NB, dx / nrm, dy / nrm, dz / nrm, Y);
-    const size_t rb = (size_t)ish * NB * 3;
+    float shr[3 * NB];
+    load_sh_row<NB>(sc.sh_rows, sc.dtype, sc.sh_vec, ish, shr);
     float col[3];
     uint32_t mask = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      float acc = load_row(sc.sh_rows, sc.dtype, rb + c) * Y[0];
+      float acc = shr[c] * Y[0];
 #pragma unroll
-      for (int k = 1; k < NB; ++k) acc = fmaf(load_row(sc.sh_rows, sc.dtype, rb + 3 * k + c), Y[k], acc);
+      for (int k = 1; k < NB; ++k) acc = fmaf(shr[3 * k + c], Y[k], acc);
       const float pre = acc + 0.5f;
       if (pre < 0.0f) mask |= 1u << c;
       col[c] = pre < 0.0f ? 0.0f : pre;

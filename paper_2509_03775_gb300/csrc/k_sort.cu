@@ -437,11 +437,31 @@ __global__ void k_capacity(DeviceState* st, int64_t cap) {
   if (!ok) set_status(st, CG_ERR_CAPACITY, 0);
 }
 
+// Position of the r-th (from 0) set bit of x (r < popc(x)).
+__device__ __forceinline__ int select_bit32(uint32_t x, int r) {
+  int pos = 0;
+#pragma unroll
+  for (int width = 16; width > 0; width >>= 1) {
+    const int c = __popc(x & ((1u << width) - 1u));
+    if (r >= c) {
+      r -= c;
+      x >>= width;
+      pos += width;
+    }
+  }
+  return pos;
+}
+
 // Pairs of one record in depth order: its kept tiles (tile_keep) in
 // row-major order of its rectangle, each as pair_key(global tile, rank among
 // the kept tiles, record) at offset + rank.  A warp takes 32 consecutive
-// records and writes each one's pairs with all lanes, so the stores of a
-// record are contiguous.
+// records.  The pairs of its records of at most 64 rectangle tiles (whose
+// kept-tile bits the count pass left in kmask) are spread over the lanes:
+// lane l writes pair p = l, l + 32, ... of the warp's list, finding its
+// record by a search over the warp's prefix of pair counts and its tile as
+// the rank-th set bit of the record's mask, so consecutive lanes write
+// consecutive pairs.  Larger records are then written by the whole warp,
+// one at a time, recomputing the tile test.
 __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__ dkeys,
                                                     const uint32_t* __restrict__ off_sorted,
                                                     const float4* __restrict__ geo,
@@ -451,7 +471,12 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__
                                                     uint32_t* __restrict__ offrec, uint64_t* __restrict__ pairs,
                                                     const DeviceState* state) {
   __shared__ TileRec st[8][32];
-  __shared__ uint2 sro[8][32];  // record, offset
+  __shared__ uint2 sro[8][32];       // record, offset (large records)
+  __shared__ uint64_t sMask[8][32];  // kept-tile bits (small records)
+  __shared__ uint4 sInfo[8][32];     // record, offset, x0 | y0 << 16, rectangle width
+  __shared__ int64_t sTB[8][32];     // first global tile of the record's view
+  __shared__ int sTX[8][32];         // tiles per row of that view
+  __shared__ uint32_t sP[8][32];     // exclusive prefix of the small records' pair counts
   const int64_t vis = (int64_t)state->visible;
   const bool ok = state->pairs_ok != 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -460,17 +485,59 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t base = warp * 32; base < vis; base += nwarps * 32) {
     const int64_t i = base + lane;
+    bool big = false;
+    uint32_t c = 0;
     if (i < vis) {
       const uint32_t rec = (uint32_t)dkeys[i];
       const uint32_t off = off_sorted[i];
       offrec[rec] = off;
-      stage_record(st[wid][lane], geo, rect, rec);
-      sro[wid][lane] = make_uint2(rec, off);
+      const ushort4 r = rect[rec];
+      const int w = (int)r.z - (int)r.x, total = w * ((int)r.w - (int)r.y);
+      big = total > 64;
+      if (big) {
+        stage_record(st[wid][lane], geo, rect, rec);
+        sro[wid][lane] = make_uint2(rec, off);
+      } else {
+        const uint64_t m = kmask[rec];
+        c = (uint32_t)__popcll((long long)m);
+        sMask[wid][lane] = m;
+        sInfo[wid][lane] = make_uint4(rec, off, (uint32_t)r.x | ((uint32_t)r.y << 16), (uint32_t)w);
+        const ViewInfo& cam = views[rec / (uint32_t)n];
+        sTB[wid][lane] = cam.tile_base;
+        sTX[wid][lane] = cam.tiles_x;
+      }
     }
+    // exclusive prefix of the small records' pair counts over the lanes
+    uint32_t incl = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t up = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += up;
+    }
+    sP[wid][lane] = incl - c;
+    const uint32_t tw = __shfl_sync(0xffffffffu, incl, 31);
+    uint32_t bigs = __ballot_sync(0xffffffffu, big);
     __syncwarp();
     if (ok) {
-      const int cnt = (int)min((int64_t)32, vis - base);
-      for (int q = 0; q < cnt; ++q) {
+      for (uint32_t p = lane; p < tw; p += 32) {
+        int q = 0;
+#pragma unroll
+        for (int stp = 16; stp > 0; stp >>= 1)
+          if (sP[wid][q + stp] <= p) q += stp;
+        const uint32_t rank = p - sP[wid][q];
+        const uint64_t m = sMask[wid][q];
+        const uint32_t lo = (uint32_t)m, cl = (uint32_t)__popc(lo);
+        const int k = rank < cl ? select_bit32(lo, (int)rank) : 32 + select_bit32((uint32_t)(m >> 32), (int)(rank - cl));
+        const uint4 inf = sInfo[wid][q];
+        const int w = (int)inf.w;
+        const int yy = (int)(((float)k + 0.5f) * (1.0f / (float)w)), xx = k - yy * w;
+        const int x0 = (int)(inf.z & 0xffffu), y0 = (int)(inf.z >> 16);
+        pairs[inf.y + rank] =
+            pair_key((uint64_t)(sTB[wid][q] + (int64_t)(y0 + yy) * sTX[wid][q] + (x0 + xx)), rank, inf.x);
+      }
+      while (bigs != 0u) {
+        const int q = __ffs(bigs) - 1;
+        bigs &= bigs - 1u;
         const TileRec& t = st[wid][q];
         const uint2 ro = sro[wid][q];
         const int x0 = (int)(t.r01 & 0xffffu), y0 = (int)(t.r01 >> 16);
@@ -479,7 +546,6 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__
         const int64_t tb = cam.tile_base;
         const int tx = cam.tiles_x;
         uint32_t rank0 = 0;
-        const uint64_t bits = total <= 64 ? kmask[ro.x] : 0ull;
         for (int t0 = 0; t0 < total; t0 += 32) {
           const int k = t0 + lane;
           bool keep = false;
@@ -487,16 +553,14 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__
           if (k < total) {
             yy = (int)(((float)k + 0.5f) * t.rw);
             xx = k - yy * w;
-            keep = total <= 64 ? ((bits >> k) & 1ull) != 0ull
-                               : tile_decide(t, tile_pmax(t.a.x, t.a.y, t.a.z, t.a.w, t.b.x, t.b.z, t.b.w, x0 + xx,
-                                                          y0 + yy, tile));
+            keep = tile_decide(t, tile_pmax(t.a.x, t.a.y, t.a.z, t.a.w, t.b.x, t.b.z, t.b.w, x0 + xx, y0 + yy, tile));
           }
-          const uint32_t m = __ballot_sync(0xffffffffu, keep);
+          const uint32_t mk = __ballot_sync(0xffffffffu, keep);
           if (keep) {
-            const uint32_t rank = rank0 + __popc(m & lt_mask);
+            const uint32_t rank = rank0 + __popc(mk & lt_mask);
             pairs[ro.y + rank] = pair_key((uint64_t)(tb + (int64_t)(y0 + yy) * tx + (x0 + xx)), rank, ro.x);
           }
-          rank0 += __popc(m);
+          rank0 += __popc(mk);
         }
       }
     }
@@ -509,13 +573,45 @@ __global__ void k_zero_u32(uint32_t* p, int64_t count) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) p[i] = 0u;
 }
 
-__global__ void k_ranges(const uint64_t* __restrict__ pairs, uint2* __restrict__ ranges, const DeviceState* st) {
+// [start, end) of every tile in the sorted pairs.  Thread t reads keys
+// 4t .. 4t + 3 with two 16-byte loads; the neighbouring keys come from the
+// adjacent lanes (the warp's first and last lanes read them directly).
+__global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ pairs, uint2* __restrict__ ranges,
+                                                const DeviceState* st) {
   const int64_t k = st->pairs_ok ? (int64_t)st->pairs : 0;
+  const int lane = threadIdx.x & 31;
+  const int64_t groups = (k + 3) / 4;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
-    const uint32_t t = key_tile(pairs[i]);
-    if (i == 0 || key_tile(pairs[i - 1]) != t) ranges[t].x = (uint32_t)i;
-    if (i == k - 1 || key_tile(pairs[i + 1]) != t) ranges[t].y = (uint32_t)(i + 1);
+  // the loop runs warp-uniformly so that the shuffles see every lane
+  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x) + (threadIdx.x & ~31); base < groups; base += stride) {
+    const int64_t g = base + lane;
+    const int64_t i0 = 4 * g;
+    uint32_t t[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};
+    if (i0 + 3 < k) {
+      const uint4 a = __ldcs(reinterpret_cast<const uint4*>(pairs + i0));
+      const uint4 b = __ldcs(reinterpret_cast<const uint4*>(pairs + i0 + 2));
+      t[0] = key_tile(((uint64_t)a.y << 32) | a.x);
+      t[1] = key_tile(((uint64_t)a.w << 32) | a.z);
+      t[2] = key_tile(((uint64_t)b.y << 32) | b.x);
+      t[3] = key_tile(((uint64_t)b.w << 32) | b.z);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (i0 + j < k) t[j] = key_tile(pairs[i0 + j]);
+    }
+    uint32_t prev = __shfl_up_sync(0xffffffffu, t[3], 1);
+    uint32_t next = __shfl_down_sync(0xffffffffu, t[0], 1);
+    if (lane == 0) prev = (i0 > 0 && i0 - 1 < k) ? key_tile(pairs[i0 - 1]) : 0xffffffffu;
+    if (lane == 31) next = (i0 + 4 < k) ? key_tile(pairs[i0 + 4]) : 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t i = i0 + j;
+      if (i >= k) break;
+      const uint32_t before = j == 0 ? prev : t[j - 1];
+      const uint32_t after = j == 3 ? next : t[j + 1];
+      if (i == 0 || before != t[j]) ranges[t[j]].x = (uint32_t)i;
+      if (i == k - 1 || after != t[j]) ranges[t[j]].y = (uint32_t)(i + 1);
+    }
   }
 }
 
@@ -565,7 +661,7 @@ cudaError_t launch_build_pairs(const Layout& L, void* ws, int tile_bits, cudaStr
   uint2* ranges = ws_ptr<uint2>(ws, L.ranges);
   const int gt = (int)std::max<int64_t>(1, std::min<int64_t>((2 * L.T + 255) / 256, kGrid));
   count_launch(), k_zero_u32<<<gt, 256, 0, s>>>(reinterpret_cast<uint32_t*>(ranges), 2 * L.T);
-  const int gk = (int)std::max<int64_t>(1, std::min<int64_t>((L.Kc + 255) / 256, kGrid));
+  const int gk = (int)std::max<int64_t>(1, std::min<int64_t>((L.Kc / 4 + 255) / 256, kGrid));
   count_launch(), k_ranges<<<gk, 256, 0, s>>>(psorted, ranges, st);
   return cudaGetLastError();
 }

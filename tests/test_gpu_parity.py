@@ -215,3 +215,31 @@ def test_l1_loss_kernel():
     ref = np.abs(a.astype(np.float64) - b).mean()
     assert abs(loss.item() - ref) < 1e-9 * max(1.0, ref)
     assert np.array_equal(np.sign(d.cpu().numpy()), np.sign(a - b))
+
+
+def test_codebook_membership_cache_follows_index_changes():
+    """The codebook reduction keeps the row membership of the last call and
+    rebuilds it only when an index array changed: after in-place index edits
+    (as a split or merge makes) its gradients equal a fresh workspace's."""
+    scene, cams = scenes.config_single(n=20_000, k=256, width=160, height=128)
+    rng = np.random.default_rng(8)
+
+    def grads(r, st, d_img):
+        r.forward(st)
+        r.backward(d_img)
+        return [t.clone() for t in r.codebook_reduce()]
+
+    r = cg.Renderer(cams, pair_capacity=1 << 22)
+    st = cg.SceneTensors.from_scene(scene)
+    d_img = torch.from_numpy(rng.normal(size=3 * 160 * 128).astype(np.float32)).cuda()
+    g0 = grads(r, st, d_img)
+    assert all(torch.equal(a, b) for a, b in zip(g0, grads(r, st, d_img)))   # cached build, same result
+    for which in ("g2sr", "g2sh"):
+        idx = getattr(st, which)
+        sel = torch.from_numpy(rng.choice(scene.n, 500, replace=False)).cuda()
+        idx[sel] = torch.from_numpy(rng.integers(0, 256, 500).astype(np.int16)).cuda()
+        got = grads(r, st, d_img)
+        fresh = grads(cg.Renderer(cams, pair_capacity=1 << 22), st, d_img)
+        for a, b in zip(got, fresh):
+            assert torch.equal(a, b), which
+    assert not torch.equal(got[0], g0[0]) and not torch.equal(got[1], g0[1])
