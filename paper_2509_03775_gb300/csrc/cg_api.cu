@@ -190,7 +190,7 @@ cg_status check_ws(void* ws, size_t ws_bytes, const Layout& L) {
 }
 
 // Blend launch shape: defaults per tile size (measured on GB300).
-int fwd_batch(const cg_opts* o) { return o->batch ? o->batch : 256; }
+int fwd_batch(const cg_opts* o) { return o->batch ? o->batch : 64; }
 int bwd_batch(const cg_opts* o) { return o->batch_bwd ? o->batch_bwd : 64; }
 int fwd_ppt(const cg_opts* o) { return o->ppt_fwd ? o->ppt_fwd : (o->tile == 32 ? 4 : 1); }
 int bwd_ppt(const cg_opts* o) { return o->ppt_bwd ? o->ppt_bwd : (o->tile == 32 ? 4 : 2); }

@@ -674,14 +674,19 @@ constexpr int kL1Blocks = 1024;
 __global__ void __launch_bounds__(256) k_l1(const float* __restrict__ img, const float* __restrict__ tgt,
                                             int64_t count, float* __restrict__ d_img, double* __restrict__ part) {
   __shared__ double red[8];
-  double acc = 0.0;
+  float s_hi = 0.0f, s_lo = 0.0f;
   const float inv = 1.0f / (float)count;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
     const float d = img[i] - tgt[i];
-    acc += (double)fabsf(d);
+    // float-float (Knuth's TwoSum) accumulation: FP64-class accuracy at
+    // FP32 instruction rates
+    const float v = fabsf(d), t = s_hi + v, bp = t - s_hi;
+    s_lo += (s_hi - (t - bp)) + (v - bp);
+    s_hi = t;
     d_img[i] = d > 0.0f ? inv : (d < 0.0f ? -inv : 0.0f);
   }
+  double acc = (double)s_hi + (double)s_lo;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;

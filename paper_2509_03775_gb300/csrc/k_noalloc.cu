@@ -43,16 +43,21 @@ __global__ void __launch_bounds__(kStaticThreads) k_l1_static(const float* __res
   __shared__ double red[kStaticThreads / 32];
   const float inv = 1.0f / (float)count;
   const int64_t base = (int64_t)blockIdx.x * kStaticPerBlock;
-  double acc = 0.0;
+  float s_hi = 0.0f, s_lo = 0.0f;
 #pragma unroll
   for (int k = 0; k < kStaticItems; ++k) {
     const int64_t i = base + (int64_t)k * kStaticThreads + threadIdx.x;
     if (i < count) {
       const float d = img[i] - tgt[i];
-      acc += (double)fabsf(d);
+      // float-float (Knuth's TwoSum) accumulation: FP64-class accuracy at
+      // FP32 instruction rates
+      const float v = fabsf(d), t = s_hi + v, bp = t - s_hi;
+      s_lo += (s_hi - (t - bp)) + (v - bp);
+      s_hi = t;
       d_img[i] = d > 0.0f ? inv : (d < 0.0f ? -inv : 0.0f);
     }
   }
+  double acc = (double)s_hi + (double)s_lo;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;

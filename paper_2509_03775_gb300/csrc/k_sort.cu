@@ -375,56 +375,83 @@ __device__ __forceinline__ bool tile_decide(const TileRec& t, float pmax) {
 }
 
 // Kept tiles of each depth-ordered record (tile_keep over the record's
-// rectangle).  A warp takes 32 records and counts each one's tiles with all
-// lanes.  Writes the count per record and, in depth order, the input of the
-// offset scan.
+// rectangle).  A warp takes 32 consecutive records and lays their rectangle
+// tiles end to end (an exclusive prefix of the tile counts); its lanes then
+// test 32 consecutive tiles of that list at a time, whatever record they
+// belong to, so every lane has work until the warp's list ends.  Each
+// record's kept tiles of a 32-tile step are counted by the first lane of
+// its run (lanes holding the same record are found with one match); records
+// of at most 64 tiles also collect their kept-tile bits for the emit pass.
+// Writes the count per record and, in depth order, the input of the offset
+// scan.
 __global__ void __launch_bounds__(256) k_count_emit(const uint64_t* __restrict__ dkeys,
                                                     const float4* __restrict__ geo,
                                                     const ushort4* __restrict__ rect, int64_t R, int tile,
                                                     uint32_t* __restrict__ nemit, uint32_t* __restrict__ counts,
                                                     uint64_t* __restrict__ kmask, const uint64_t* visible_dev) {
   __shared__ TileRec st[8][32];
+  __shared__ uint32_t sPre[8][32];
+  __shared__ uint32_t sCnt[8][32];
+  __shared__ uint64_t sMask[8][32];
   const int64_t vis = min((int64_t)*visible_dev, R);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t base = warp * 32; base < vis; base += nwarps * 32) {
     const int64_t i = base + lane;
-    uint32_t rec = 0;
+    uint32_t rec = 0, nt = 0;
     if (i < vis) {
       rec = (uint32_t)dkeys[i];
       stage_record(st[wid][lane], geo, rect, rec);
+      const TileRec& t = st[wid][lane];
+      nt = ((t.r23 & 0xffffu) - (t.r01 & 0xffffu)) * ((t.r23 >> 16) - (t.r01 >> 16));
     }
-    __syncwarp();
-    const int cnt = (int)min((int64_t)32, vis - base);
-    uint32_t mine = 0;
-    for (int q = 0; q < cnt; ++q) {
-      const TileRec& t = st[wid][q];
-      const int x0 = (int)(t.r01 & 0xffffu), y0 = (int)(t.r01 >> 16);
-      const int w = (int)(t.r23 & 0xffffu) - x0, total = w * ((int)(t.r23 >> 16) - y0);
-      uint32_t c = 0;
-      uint64_t bits = 0;
-      for (int t0 = 0; t0 < total; t0 += 32) {
-        const int k = t0 + lane;
-        bool keep = false;
-        if (k < total) {
-          const int yy = (int)(((float)k + 0.5f) * t.rw), xx = k - yy * w;
-          keep = tile_decide(t, tile_pmax(t.a.x, t.a.y, t.a.z, t.a.w, t.b.x, t.b.z, t.b.w, x0 + xx, y0 + yy, tile));
-        }
-        const uint32_t m = __ballot_sync(0xffffffffu, keep);
-        if (t0 < 64) bits |= (uint64_t)m << t0;
-        c += __popc(m);
-      }
-      if (lane == q) {
-        mine = c;
-        if (total <= 64) kmask[rec] = bits;  // the emit pass reuses the decisions
-      }
+    uint32_t incl = nt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t up = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += up;
     }
+    sPre[wid][lane] = incl - nt;
+    sCnt[wid][lane] = 0;
+    sMask[wid][lane] = 0ull;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
     __syncwarp();
+    for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+      const uint32_t p = c0 + lane;
+      const bool valid = p < total;
+      // the record of list position p: the last one whose start is <= p
+      int q = 0;
+#pragma unroll
+      for (int stp = 16; stp > 0; stp >>= 1)
+        if (sPre[wid][q + stp] <= p) q += stp;
+      bool keep = false;
+      int k = 0;
+      if (valid) {
+        const TileRec& t = st[wid][q];
+        k = (int)(p - sPre[wid][q]);
+        const int x0 = (int)(t.r01 & 0xffffu), y0 = (int)(t.r01 >> 16);
+        const int w = (int)(t.r23 & 0xffffu) - x0;
+        const int yy = (int)(((float)k + 0.5f) * t.rw), xx = k - yy * w;
+        keep = tile_decide(t, tile_pmax(t.a.x, t.a.y, t.a.z, t.a.w, t.b.x, t.b.z, t.b.w, x0 + xx, y0 + yy, tile));
+      }
+      const uint32_t m = __ballot_sync(0xffffffffu, keep);
+      const uint32_t peers = __match_any_sync(0xffffffffu, valid ? q : 32);
+      const bool head = valid && (peers & ((1u << lane) - 1u)) == 0u;
+      if (head) {
+        const uint32_t mine = (m & peers) >> lane;  // bit j: list position p + j
+        sCnt[wid][q] += (uint32_t)__popc(mine);
+        if (k < 64) sMask[wid][q] |= (uint64_t)mine << k;
+      }
+      __syncwarp();
+    }
     if (i < vis) {
-      nemit[rec] = mine;
-      counts[i] = mine;
+      const uint32_t c = sCnt[wid][lane];
+      nemit[rec] = c;
+      counts[i] = c;
+      if (nt <= 64u) kmask[rec] = sMask[wid][lane];  // the emit pass reuses the decisions
     }
+    __syncwarp();
   }
 }
 
