@@ -8,6 +8,8 @@ codebook reduction -- every stage in libcg's kernels.
 
 Default workload (N = 1): the truck-shaped scene, 1.5M Gaussians, SH
 degree 3, 8192 rows per codebook, one 1957x1091 camera, FP32 codebooks.
+The step is captured once as a CUDA graph and replayed (--eager launches
+the calls one by one); the e2e figure goes through the public API eagerly.
 With torchrun (N > 1) every rank renders its own view of the same scene
 (weak scaling, no data-path collective; only the timing is reduced).
 
@@ -707,7 +709,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["cg", "reference"], default="cg")
     ap.add_argument("--workload", choices=["truck", "single", "tiny", "batched", "large"], default="truck")
-    ap.add_argument("--graph", action="store_true", help="replay the step as one captured CUDA graph")
+    ap.add_argument("--graph", action="store_true", help="replay the step as one captured CUDA graph (default)")
+    ap.add_argument("--eager", action="store_true", help="launch the step's calls one by one instead of a graph")
     ap.add_argument("--bf16", action="store_true", help="BF16 codebook storage (default for --workload large)")
     ap.add_argument("--autotune", action="store_true", help="tune the blend launch shapes first (cached)")
     ap.add_argument("--autotune-tiles", action="store_true",
@@ -723,6 +726,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    args.graph = not args.eager
     if args.impl == "reference":
         run_reference(args)
     else:
