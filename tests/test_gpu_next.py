@@ -7,6 +7,8 @@ the SGLD update is within FP32 rounding of the FP64 oracle (BF16 rows within
 one BF16 step); the loss within 1e-6 and its gradient within 1e-3 relative
 or 1e-4 of the largest magnitude (the FP32 cancellation in the windowed
 variances, E[x^2] - mu^2, bounds the gradient's accuracy)."""
+import json
+import os
 import types
 
 import numpy as np
@@ -17,6 +19,14 @@ from oracle import mcmc, ssim
 from paper_2509_03775_gb300 import cg, scenes
 
 pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _dump(errs, key):
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    with open(os.path.join(ROOT, "gpurun_out", f"next_{key}.json"), "w") as f:
+        json.dump(errs, f)
 
 
 # ----------------------------------------------------------------------------
@@ -83,12 +93,14 @@ def _check_sgld(scene, bf16: bool, eps: dict, seed: int, step: int):
 @pytest.mark.parametrize("bf16", [False, True])
 def test_sgld_update_matches_oracle(bf16):
     scene, _ = scenes.config_single(n=50_000, k=512)
-    _check_sgld(scene, bf16, {"pos": 1e-4, "logit": 1e-3, "sr": 1e-4, "sh": 1e-5}, seed=123, step=7)
+    _dump(_check_sgld(scene, bf16, {"pos": 1e-4, "logit": 1e-3, "sr": 1e-4, "sh": 1e-5}, seed=123, step=7),
+          f"sgld_single_{'bf16' if bf16 else 'f32'}")
 
 
 def test_sgld_update_full_size_truck():
     scene, _ = scenes.config_truck()
-    _check_sgld(scene, False, {"pos": 2e-5, "logit": 1e-3, "sr": 1e-4, "sh": 1e-5}, seed=99, step=12345678901)
+    _dump(_check_sgld(scene, False, {"pos": 2e-5, "logit": 1e-3, "sr": 1e-4, "sh": 1e-5}, seed=99,
+                      step=12345678901), "sgld_truck")
 
 
 def test_sgld_update_is_deterministic_and_depends_on_step():
@@ -184,6 +196,7 @@ def test_split_merge_full_size_truck_paper_hyperparameters():
     """The truck scene (1.5M Gaussians, 8192 + 8192 rows) with the paper's
     lambda_SR = 3, lambda_SH = 2.3, eps_split = 0.1, eps_merge = 0.05."""
     scene, _ = scenes.config_truck()
+    counts = {}
     for which, lam in ((0, 3.0), (1, 2.3)):
         cb, rows, parent, g2x, k = _codebook_case(scene, which, False, 65536)
         k1 = cb.split(lam, 0.1, 0.05, seed=2025, step=100)
@@ -192,6 +205,8 @@ def test_split_merge_full_size_truck_paper_hyperparameters():
         k2 = cb.merge(lam, 0.1, 0.05, seed=2025, step=101)
         mg = mcmc.merge(sp["rows"], sp["parent"], sp["g2x"], k1, which, scene.sh_degree, lam, 0.1, 0.05, 101, 2025)
         _assert_same(cb, mg, k2)
+        counts["sr" if which == 0 else "sh"] = {"rows": k, "after_split": k1, "after_merge": k2}
+    _dump(counts, "split_merge_truck")
 
 
 # ----------------------------------------------------------------------------
@@ -232,7 +247,7 @@ def test_recon_loss_uneven_views_matches_oracle():
     cams = [types.SimpleNamespace(width=w, height=h, fx=1.0, fy=1.0, cx=0.0, cy=0.0, world_to_cam=np.zeros(12),
                                   campos=np.zeros(3), near=0.2) for w, h in [(200, 120), (96, 96), (37, 70), (5, 3)]]
     x, y = _smooth_pair(cams, rng)
-    _check_loss(x, y, cams, 0.2)
+    _dump(_check_loss(x, y, cams, 0.2), "loss_uneven")
     _check_loss(x, y, cams, 1.0)
     _check_loss(x, y, cams, 0.0)
 
@@ -245,7 +260,7 @@ def test_recon_loss_full_size_truck_render():
     tgt_scene = scene.copy()
     tgt_scene.pos = (scene.pos + np.random.default_rng(1).normal(0, 0.01, scene.pos.shape)).astype(np.float32)
     tgt = r.forward(cg.SceneTensors.from_scene(tgt_scene)).clone()
-    _check_loss(img.cpu().numpy(), tgt.cpu().numpy(), cams)
+    _dump(_check_loss(img.cpu().numpy(), tgt.cpu().numpy(), cams), "loss_truck")
 
 
 # ----------------------------------------------------------------------------
