@@ -312,3 +312,45 @@ def merge(rows, parent, g2x, k: int, codebook: int, sh_degree: int, lam: float, 
     out_g2x = newidx[target[g2x]]
     return {"rows": out_rows, "parent": out_parent, "g2x": out_g2x, "k": k_new, "merged": final,
             "proposed": tent, "d2": d2}
+
+
+# ----------------------------------------------------------------------------
+# growth (Sec. 5.1: +5 % Gaussians every 100 iterations by duplication)
+# ----------------------------------------------------------------------------
+
+STREAM_GROW = 24
+
+
+def sigmoid32(logit) -> np.ndarray:
+    """Opacity in the FP32 decision arithmetic: 1 / (1 + exp32(-l))."""
+    l = np.asarray(logit, dtype=np.float32).ravel()
+    return (np.float32(1.0) / (np.float32(1.0) + exp32(-l))).astype(np.float32)
+
+
+def grow_weights(logit) -> np.ndarray:
+    """Integer sampling weights floor(o 2^24) (exact in FP32, so both sides
+    agree; uniform weights when every weight is 0)."""
+    o = sigmoid32(logit)
+    w = np.floor(o * np.float32(2.0 ** 24)).astype(np.int64)
+    return w if w.sum() > 0 else np.ones_like(w)
+
+
+def grow(pos, logit, g2sr, g2sh, m: int, step: int, seed: int) -> dict:
+    """m new Gaussians, each a copy of an existing one drawn with
+    probability proportional to its opacity: new Gaussian j takes the 64-bit
+    draw x of counter (j, stream 24, step), u = x mod W (W = sum of the
+    weights) and copies the Gaussian whose weight interval holds u.  The
+    copies are appended after the n existing Gaussians."""
+    n = len(logit)
+    w = grow_weights(logit)
+    incl = np.cumsum(w)
+    total = int(incl[-1])
+    d = draws(np.arange(m), STREAM_GROW, 0, step, seed).astype(np.uint64)
+    x = (d[:, 1] << np.uint64(32)) | d[:, 0]
+    u = (x % np.uint64(total)).astype(np.int64)
+    src = np.searchsorted(incl, u, side="right")
+    return {"src": src.astype(np.int64),
+            "pos": np.concatenate([np.asarray(pos, np.float32).reshape(n, 3), np.asarray(pos, np.float32).reshape(n, 3)[src]]),
+            "logit": np.concatenate([np.asarray(logit, np.float32), np.asarray(logit, np.float32)[src]]),
+            "g2sr": np.concatenate([np.asarray(g2sr), np.asarray(g2sr)[src]]),
+            "g2sh": np.concatenate([np.asarray(g2sh), np.asarray(g2sh)[src]])}

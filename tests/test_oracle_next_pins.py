@@ -278,3 +278,36 @@ def test_recon_loss_gradient_by_finite_differences():
         fd = (ssim.recon_loss(xp, y, cams)["loss"] - ssim.recon_loss(xm, y, cams)["loss"]) / (2 * h)
         assert abs(fd - r["grad"][i]) <= 1e-6 * abs(fd) + 1e-9, (i, fd, r["grad"][i])
     assert abs(r["loss"] - (0.8 * np.abs(x - y).mean() + 0.2 * r["l_ssim"])) < 1e-15
+
+
+# ----------------------------------------------------------------------------
+# growth
+# ----------------------------------------------------------------------------
+
+def test_growth_copies_gaussians_in_proportion_to_opacity():
+    rng = np.random.default_rng(12)
+    n = 50
+    logit = rng.normal(0, 2, n).astype(np.float32)
+    pos = rng.normal(size=(n, 3)).astype(np.float32)
+    g2sr = rng.integers(0, 9, n).astype(np.uint16)
+    g2sh = rng.integers(0, 9, n).astype(np.uint16)
+    out = mcmc.grow(pos, logit, g2sr, g2sh, 200_000, step=3, seed=4)
+    src = out["src"]
+    assert src.min() >= 0 and src.max() < n
+    # copies are exact
+    assert np.array_equal(out["pos"][n:], pos[src]) and np.array_equal(out["g2sh"][n:], g2sh[src])
+    assert np.array_equal(out["pos"][:n], pos) and np.array_equal(out["logit"][n:], logit[src])
+    # frequencies follow the opacities (chi-square against o / sum o)
+    o = 1.0 / (1.0 + np.exp(-logit.astype(np.float64)))
+    expected = o / o.sum() * src.size
+    observed = np.bincount(src, minlength=n)
+    assert stats.chisquare(observed, expected).pvalue > 1e-3
+    # the FP32 opacity equals the FP64 sigmoid to a few ulp
+    assert np.abs(mcmc.sigmoid32(logit) - o).max() < 1e-6
+    # deterministic, and another step draws other copies
+    again = mcmc.grow(pos, logit, g2sr, g2sh, 200_000, step=3, seed=4)["src"]
+    other = mcmc.grow(pos, logit, g2sr, g2sh, 200_000, step=4, seed=4)["src"]
+    assert np.array_equal(src, again) and not np.array_equal(src, other)
+    # every weight 0: uniform choice
+    flat = mcmc.grow(pos, np.full(n, -200.0, np.float32), g2sr, g2sh, 100_000, step=1, seed=1)["src"]
+    assert stats.chisquare(np.bincount(flat, minlength=n)).pvalue > 1e-3
