@@ -600,6 +600,39 @@ def run_next_rows(args, r, st, scene, cams, images, target, grads, dev, bf16, hb
                           "achieved_gbs": round(algo / ms / 1e6, 1), "peak_gbs": hbm_peak,
                           "frac": round(algo / ms / 1e6 / hbm_peak, 4), "peak_source": hbm_src,
                           "bytes_model": "value read + gradient read + value written per element"}
+    # growth by 5 % (opacity-weighted copies) and the incremental membership update
+    n, m = scene.n, scene.n // 20
+    gpos = torch.zeros((n + m, 3), device=dev)
+    glogit = torch.zeros(n + m, device=dev)
+    gsr = torch.zeros(n + m, dtype=torch.int16, device=dev)
+    gsh = torch.zeros(n + m, dtype=torch.int16, device=dev)
+    gpos[:n].copy_(st.pos)
+    glogit[:n].copy_(st.opacity_logit)
+    gsr[:n].copy_(st.g2sr)
+    gsh[:n].copy_(st.g2sh)
+    gws = cg.grow_workspace(n, dev)
+    src = torch.empty(m, dtype=torch.int32, device=dev)
+    cg.grow(gpos, glogit, gsr, gsh, n, m, 7, 1, src_out=src, workspace=gws)
+    ms_grow = _time_calls(lambda: cg.grow(gpos, glogit, gsr, gsh, n, m, 7, 1, src_out=src, workspace=gws), reps,
+                          stream)
+    rg = cg.Renderer(cams, pair_capacity=r.pair_capacity, device=dev, n_capacity=n + m)
+    small = cg.SceneTensors(gpos[:n], glogit[:n], gsr[:n], gsh[:n], st.sr_rows, st.sh_rows, st.sh_degree)
+    grown = cg.SceneTensors(gpos, glogit, gsr, gsh, st.sr_rows, st.sh_rows, st.sh_degree)
+    rg.forward(small)
+    rg.backward(torch.zeros_like(images))
+    rg.codebook_reduce()                     # memberships of the first n Gaussians
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    rg.codebook_append(grown, n)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_app = a.elapsed_time(b)
+    state = rg.array(cg.WS_CSR_STATE, torch.int32, 10).cpu().numpy().reshape(2, 10)
+    out["grow"] = {"ms": round(ms_grow, 4), "gaussians": n, "added": m, "bytes_model": "copies of 24 B per new Gaussian"}
+    out["membership_append"] = {"ms": round(ms_app, 4), "appended": m, "incremental": bool((state[:, 7] == 1).all()),
+                                "timing": "one eager call between CUDA events (includes launch gaps)"}
+    del rg
     # split and merge of each codebook with the paper's hyperparameters
     for which, name, lam, rows0, g2x0 in ((0, "sr", 3.0, st.sr_rows, st.g2sr), (1, "sh", 2.3, st.sh_rows, st.g2sh)):
         k = rows0.shape[0]

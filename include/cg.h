@@ -104,7 +104,11 @@ typedef struct {
  * bg: background colour added with the final transmittance.
  * pair_capacity: (tile, Gaussian) pairs the workspace has room for
  * (1 <= pair_capacity < 2^32); every call on a workspace must pass the value
- * it was sized with. */
+ * it was sized with.
+ * n_capacity: Gaussians the workspace has room for (0 = scene->n); a
+ * workspace sized for n_capacity serves any scene->n <= n_capacity, so it
+ * (and the codebook memberships it keeps) outlives growth.  Every call on a
+ * workspace must pass the value it was sized with. */
 typedef struct {
   int tile;
   int batch;
@@ -113,6 +117,7 @@ typedef struct {
   int ppt_bwd;
   float bg[3];
   uint32_t pair_capacity;
+  uint32_t n_capacity;
 } cg_opts;
 
 /* Workspace bytes for rendering `n_views` cameras (host array) of `scene`
@@ -152,6 +157,18 @@ cg_status cg_render_bwd(const cg_scene *scene, const cg_camera *cams, int n_view
 cg_status cg_codebook_reduce(const cg_scene *scene, const cg_camera *cams, int n_views, const cg_opts *opts,
                              void *workspace, size_t ws_bytes, float *d_sr_rows, float *d_sh_rows,
                              cg_stream_t stream);
+
+/* Incremental update of the codebook memberships this workspace keeps (the
+ * rows -> members lists cg_codebook_reduce sums over), after Gaussians
+ * n_old .. scene->n - 1 were appended (cg_grow): each row's list becomes its
+ * old list followed by its new members in index order, without re-sorting
+ * the old members.  If the kept lists are not those of the first n_old
+ * entries of the scene's index arrays (or an index is out of range), they
+ * are rebuilt instead.  The workspace must have room for scene->n Gaussians
+ * (cg_opts.n_capacity).  Calling it is optional: cg_codebook_reduce rebuilds
+ * lists that no longer match the index arrays. */
+cg_status cg_codebook_append(const cg_scene *scene, const cg_camera *cams, int n_views, const cg_opts *opts,
+                             void *workspace, size_t ws_bytes, int n_old, cg_stream_t stream);
 
 /* Synchronises `stream` and returns the device status of the workspace
  * (CG_OK, CG_ERR_INDEX or CG_ERR_CAPACITY).  *pairs_out (host, may be NULL)
@@ -297,6 +314,23 @@ cg_status cg_codebook_split(const cg_mh_opts *opts, void *rows, int32_t *parent,
 cg_status cg_codebook_merge(const cg_mh_opts *opts, void *rows, int32_t *parent, uint16_t *g2x, int32_t *k_out,
                             void *workspace, size_t ws_bytes, cg_stream_t stream);
 
+/* Growth (Sec. 5.1 grows the model by 5 % every 100 iterations; an elided
+ * passage of the method names duplication): m new Gaussians are appended
+ * after the n existing ones, each an exact copy (position, opacity logit,
+ * both indices) of an existing Gaussian drawn with probability proportional
+ * to its opacity.  Weights are the integers floor(o 2^24) of the FP32
+ * opacity (uniform if all are 0); new Gaussian j draws the 64-bit
+ * (y << 32) | x of Philox counter (j, stream 24, step) and copies the
+ * Gaussian whose weight interval holds that value modulo the weight total.
+ *   params    n = current count; pos, opacity_logit hold n + m entries
+ *   g2sr, g2sh  [n + m] uint16, entries n .. n + m - 1 are written
+ *   src_out   device int32 [m] (may be NULL): the copied Gaussian of each
+ * Codebook rows are not touched (the copies share their rows, so the row
+ * membership grows; cg_codebook_reduce updates its kept membership). */
+size_t cg_grow_workspace_bytes(int n);
+cg_status cg_grow(const cg_params *params, uint16_t *g2sr, uint16_t *g2sh, int m, uint64_t seed, uint64_t step,
+                  int32_t *src_out, void *workspace, size_t ws_bytes, cg_stream_t stream);
+
 /* Internal arrays of the workspace, for inspection by tests (device pointer
  * and element count written to the host outputs).  Layouts:
  *   CG_WS_RECT        [V*n] uint16x4  tile rectangle x0, y0, x1, y1 (x1 == x0 when culled)
@@ -310,10 +344,14 @@ cg_status cg_codebook_merge(const cg_mh_opts *opts, void *rows, int32_t *parent,
  *   CG_WS_DRGB        [V*n] float x3  dL/dcolour per view and Gaussian, after the clamp mask
  *   CG_WS_GEO         [V*n] float x8  mean x, y, -c0/2, -c1, -c2/2, opacity, skip bound, 0
  *   CG_WS_RGB         [V*n] float x4  colour r, g, b, clamp mask bits
- *   CG_WS_SIGMA3      [k_sr] float x6 Sigma of each SR row (Eq. 2, FP32) */
+ *   CG_WS_SIGMA3      [k_sr] float x6 Sigma of each SR row (Eq. 2, FP32)
+ *   CG_WS_CSR_STATE   [2]  40 B       kept-membership record of the SR and SH codebooks:
+ *                                     uint64 tag, uint64 index-array address, uint32 rows,
+ *                                     uint32 Gaussians, uint32 pending flags, uint32 count of
+ *                                     incremental updates, uint64 chunk count */
 typedef enum {
   CG_WS_RECT = 0, CG_WS_DEPTH, CG_WS_PAIRS, CG_WS_RANGES, CG_WS_NCONTRIB, CG_WS_TFINAL,
-  CG_WS_DSIGMA, CG_WS_DRGB, CG_WS_GEO, CG_WS_RGB, CG_WS_SIGMA3
+  CG_WS_DSIGMA, CG_WS_DRGB, CG_WS_GEO, CG_WS_RGB, CG_WS_SIGMA3, CG_WS_CSR_STATE
 } cg_ws_array;
 cg_status cg_workspace_array(void *workspace, size_t ws_bytes, cg_ws_array which, void **ptr_out,
                              uint64_t *count_out);

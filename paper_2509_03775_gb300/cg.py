@@ -24,8 +24,8 @@ STATUS_NAMES = {0: "CG_OK", 1: "CG_ERR_ARG", 2: "CG_ERR_INDEX", 3: "CG_ERR_CAPAC
 CG_F32, CG_BF16 = 0, 1
 MAX_VIEWS = 64
 
-WS_RECT, WS_DEPTH, WS_PAIRS, WS_RANGES, WS_NCONTRIB, WS_TFINAL, WS_DSIGMA, WS_DRGB, WS_GEO, WS_RGB, WS_SIGMA3 = \
-    range(11)
+WS_RECT, WS_DEPTH, WS_PAIRS, WS_RANGES, WS_NCONTRIB, WS_TFINAL, WS_DSIGMA, WS_DRGB, WS_GEO, WS_RGB, WS_SIGMA3, \
+    WS_CSR_STATE = range(12)
 
 # every symbol include/cg.h declares
 EXPORTS = ["cg_workspace_bytes", "cg_render_fwd", "cg_render_bwd", "cg_codebook_reduce", "cg_last_device_status",
@@ -33,7 +33,7 @@ EXPORTS = ["cg_workspace_bytes", "cg_render_fwd", "cg_render_bwd", "cg_codebook_
            "cg_host_tile_keep", "cg_timing_enable", "cg_timing_read", "cg_launch_count", "cg_version",
            "cg_l1_loss_static", "cg_recon_workspace_bytes", "cg_recon_loss", "cg_sgld_update", "cg_mh_workspace_bytes",
            "cg_codebook_split", "cg_codebook_merge", "cg_host_philox4x32_10", "cg_host_normal4", "cg_host_log32",
-           "cg_host_sincos2pi32"]
+           "cg_host_sincos2pi32", "cg_grow_workspace_bytes", "cg_grow", "cg_codebook_append"]
 STAGES = ["preprocess", "sort", "blend_fwd", "blend_bwd", "gauss_bwd", "reduce", "loss", "sgld", "split", "merge"]
 
 
@@ -59,7 +59,7 @@ class Scene(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int), ("batch", ctypes.c_int), ("batch_bwd", ctypes.c_int),
                 ("ppt_fwd", ctypes.c_int), ("ppt_bwd", ctypes.c_int), ("bg", ctypes.c_float * 3),
-                ("pair_capacity", ctypes.c_uint32)]
+                ("pair_capacity", ctypes.c_uint32), ("n_capacity", ctypes.c_uint32)]
 
 
 class Params(ctypes.Structure):
@@ -129,9 +129,13 @@ def load(path: str | None = None) -> ctypes.CDLL:
         L.cg_host_log32.argtypes = [ctypes.c_float]
         L.cg_host_log32.restype = ctypes.c_float
         L.cg_host_sincos2pi32.argtypes = [ctypes.c_float, P]
+        L.cg_codebook_append.argtypes = [P, P, ctypes.c_int, P, P, ctypes.c_size_t, ctypes.c_int, P]
+        L.cg_grow_workspace_bytes.argtypes = [ctypes.c_int]
+        L.cg_grow_workspace_bytes.restype = ctypes.c_size_t
+        L.cg_grow.argtypes = [P, P, P, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, P, P, ctypes.c_size_t, P]
         for name in ("cg_render_fwd", "cg_render_bwd", "cg_codebook_reduce", "cg_last_device_status", "cg_l1_loss",
                      "cg_workspace_array", "cg_recon_loss", "cg_sgld_update", "cg_codebook_split",
-                     "cg_codebook_merge"):
+                     "cg_codebook_merge", "cg_grow", "cg_codebook_append"):
             getattr(L, name).restype = ctypes.c_int
         if path is None:
             _lib = L
@@ -284,6 +288,31 @@ class Codebook:
         return self._run("cg_codebook_merge", lam, eps_split, eps_merge, seed, step, stream, sync)
 
 
+def grow_workspace(n: int, device="cuda") -> tuple[torch.Tensor, ctypes.c_void_p, int]:
+    """A workspace for cg_grow on n Gaussians (keep it to call grow() inside a
+    CUDA graph capture)."""
+    nbytes = int(load().cg_grow_workspace_bytes(n))
+    ws, wsp = _aligned_workspace(nbytes, torch.device(device))
+    return ws, wsp, nbytes
+
+
+def grow(pos: torch.Tensor, logit: torch.Tensor, g2sr: torch.Tensor, g2sh: torch.Tensor, n: int, m: int,
+         seed: int, step: int, src_out: torch.Tensor | None = None, stream=None, workspace=None) -> torch.Tensor:
+    """Appends m opacity-weighted copies after the first n Gaussians, in place
+    (the tensors hold at least n + m entries).  Returns the copied indices."""
+    for t, k in ((pos, 3 * (n + m)), (logit, n + m), (g2sr, n + m), (g2sh, n + m)):
+        if not (t.is_cuda and t.is_contiguous()) or t.numel() < k:
+            raise ValueError("growth needs contiguous CUDA tensors with room for n + m Gaussians")
+    if src_out is None:
+        src_out = torch.empty(max(m, 1), dtype=torch.int32, device=pos.device)
+    L = load()
+    ws, wsp, nbytes = workspace if workspace is not None else grow_workspace(n, pos.device)
+    p = Params(n, 1, 1, 0, CG_F32, pos.data_ptr(), logit.data_ptr(), 0, 0)
+    _check("cg_grow", L.cg_grow(ctypes.byref(p), _ptr(g2sr), _ptr(g2sh), int(m), int(seed), int(step), _ptr(src_out),
+                                wsp, nbytes, _stream_ptr(stream)))
+    return src_out[:m]
+
+
 def host_philox(ctr, key) -> np.ndarray:
     c = np.ascontiguousarray(ctr, dtype=np.uint32)
     k = np.ascontiguousarray(key, dtype=np.uint32)
@@ -359,7 +388,7 @@ class Renderer:
 
     def __init__(self, cams: Sequence, tile: int = 16, batch: int = 0, bg=(0.0, 0.0, 0.0),
                  pair_capacity: int = 1 << 20, device: str | torch.device = "cuda", batch_bwd: int = 0,
-                 ppt_fwd: int = 0, ppt_bwd: int = 0):
+                 ppt_fwd: int = 0, ppt_bwd: int = 0, n_capacity: int = 0):
         self.lib = load()
         self.cams = list(cams)
         self._cams = camera_array(self.cams)
@@ -367,6 +396,7 @@ class Renderer:
         self.batch_bwd, self.ppt_fwd, self.ppt_bwd = int(batch_bwd), int(ppt_fwd), int(ppt_bwd)
         self.bg = tuple(float(b) for b in bg)
         self.pair_capacity = int(pair_capacity)
+        self.n_capacity = int(n_capacity)
         self.device = torch.device(device)
         self.ws = None
         self.ws_bytes = 0
@@ -380,10 +410,13 @@ class Renderer:
         for i in range(3):
             o.bg[i] = self.bg[i]
         o.pair_capacity = self.pair_capacity
+        o.n_capacity = self.n_capacity
         return o
 
     def _ensure(self, sc: Scene):
-        key = (sc.n, sc.k_sr, sc.k_sh, sc.sh_degree, self.pair_capacity)
+        if self.n_capacity and sc.n > self.n_capacity:
+            raise ValueError(f"{sc.n} Gaussians exceed the renderer's capacity {self.n_capacity}")
+        key = (max(sc.n, self.n_capacity), sc.k_sr, sc.k_sh, sc.sh_degree, self.pair_capacity)
         if self._key == key and self.ws is not None:
             return
         o = self.opts()
@@ -456,6 +489,17 @@ class Renderer:
                                                                  ctypes.byref(o), self._ws_ptr, self.ws_bytes,
                                                                  _ptr(d_sr), _ptr(d_sh), _stream_ptr(stream)))
         return d_sr, d_sh
+
+    def codebook_append(self, scene: "SceneTensors", n_old: int, stream=None):
+        """After growth from n_old Gaussians: extend the kept codebook
+        memberships instead of rebuilding them (cg_codebook_append)."""
+        sc = scene.struct()
+        self._ensure(sc)
+        self._scene = scene
+        o = self.opts()
+        _check("cg_codebook_append", self.lib.cg_codebook_append(ctypes.byref(sc), self._cams, len(self.cams),
+                                                                 ctypes.byref(o), self._ws_ptr, self.ws_bytes,
+                                                                 int(n_old), _stream_ptr(stream)))
 
     def l1_loss(self, images: torch.Tensor, target: torch.Tensor, d_images: torch.Tensor | None = None,
                 loss: torch.Tensor | None = None, stream=None):

@@ -90,7 +90,10 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
   if (o->pair_capacity < 1) return CG_ERR_ARG;
   const int64_t n = s->n;
   const int64_t R = n * n_views;
-  if (R >= (int64_t(1) << 32)) return CG_ERR_ARG;
+  // regions are sized for n_cap Gaussians, so a workspace outlives growth
+  const int64_t n_cap = std::max<int64_t>(n, (int64_t)o->n_capacity);
+  const int64_t R_cap = n_cap * n_views;
+  if (R_cap >= (int64_t(1) << 32)) return CG_ERR_ARG;
   memset(table, 0, sizeof(*table));
   table->n_views = n_views;
   table->tile = o->tile;
@@ -112,7 +115,7 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
     P += (int64_t)c.width * c.height;
   }
   // key layout (pair_key): records < 2^26, tiles per view < 2^17, tiles < 2^21
-  if (R > (int64_t)kKeyRecMask + 1) return CG_ERR_ARG;
+  if (R_cap > (int64_t)kKeyRecMask + 1) return CG_ERR_ARG;
   for (int v = 0; v < n_views; ++v)
     if ((int64_t)table->v[v].tiles_x * table->v[v].tiles_y > (int64_t)kKeyRankMask + 1) return CG_ERR_ARG;
   if (T > (int64_t(1) << (64 - kKeyTileShift))) return CG_ERR_ARG;
@@ -122,10 +125,10 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
   L->n = n; L->R = R; L->T = T; L->P = P; L->Kc = Kc;
   L->k_sr = s->k_sr; L->k_sh = s->k_sh; L->nb = nb; L->n_views = n_views; L->tile = o->tile;
   L->tile_bits = std::max(1, ceil_log2(T));
-  L->sort_blocks_cap = (std::max(Kc, R) + 4095) / 4096 + 1;  // 4096 keys per sort block
+  L->sort_blocks_cap = (std::max(Kc, R_cap) + 4095) / 4096 + 1;  // 4096 keys per sort block
   const int64_t kmax = std::max(s->k_sr, s->k_sh) + 1;
-  L->scan_blocks_cap = (std::max(R, kmax) + 4095) / 4096 + 1;
-  L->chunks_cap = (n + 1023) / 1024 + kmax;  // chunks of 1024 members
+  L->scan_blocks_cap = (std::max(R_cap, kmax) + 4095) / 4096 + 1;
+  L->chunks_cap = (n_cap + 1023) / 1024 + kmax;  // chunks of 1024 members
   uint64_t off = 0;
   auto take = [&](uint64_t bytes) {
     const uint64_t at = off;
@@ -136,17 +139,17 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
   L->l1 = take(sizeof(double) * 1024);  // fixed offset: cg_l1_loss needs no layout
   L->views = take(sizeof(ViewInfo) * CG_MAX_VIEWS);
   L->sigma3 = take(sizeof(float) * 6 * s->k_sr);
-  L->geo = take(sizeof(float4) * 2 * R);
-  L->rgbm = take(sizeof(float4) * R);
-  L->rect = take(sizeof(ushort4) * R);
-  L->ntiles = take(sizeof(uint32_t) * R);
-  L->depth = take(sizeof(uint32_t) * R);
-  L->offrec = take(sizeof(uint32_t) * R);
-  L->nemit = take(sizeof(uint32_t) * R);
-  L->kmask = take(sizeof(uint64_t) * R);
-  L->scan = take(sizeof(uint32_t) * std::max(R, kmax));
-  L->dkeys0 = take(sizeof(uint64_t) * R);
-  L->dkeys1 = take(sizeof(uint64_t) * R);
+  L->geo = take(sizeof(float4) * 2 * R_cap);
+  L->rgbm = take(sizeof(float4) * R_cap);
+  L->rect = take(sizeof(ushort4) * R_cap);
+  L->ntiles = take(sizeof(uint32_t) * R_cap);
+  L->depth = take(sizeof(uint32_t) * R_cap);
+  L->offrec = take(sizeof(uint32_t) * R_cap);
+  L->nemit = take(sizeof(uint32_t) * R_cap);
+  L->kmask = take(sizeof(uint64_t) * R_cap);
+  L->scan = take(sizeof(uint32_t) * std::max(R_cap, kmax));
+  L->dkeys0 = take(sizeof(uint64_t) * R_cap);
+  L->dkeys1 = take(sizeof(uint64_t) * R_cap);
   L->pairs0 = take(sizeof(uint64_t) * Kc);
   L->pairs1 = take(sizeof(uint64_t) * Kc);
   L->ranges = take(sizeof(uint32_t) * 2 * T);
@@ -154,20 +157,21 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
   L->ncontrib = take(sizeof(uint32_t) * P);
   L->pairgrad = take(sizeof(float4) * 2 * Kc);   // 8 sums per pair, one 32-byte sector
   L->pairgrad1 = take(sizeof(float) * Kc);        // the opacity sum per pair
-  L->recgrad = take(sizeof(float) * 10 * R);
-  L->dsigma = take(sizeof(float) * 6 * n);
-  L->drgb = take(sizeof(float) * 3 * R);
-  L->csr_keys0 = take(sizeof(uint64_t) * n);
-  L->csr_keys1 = take(sizeof(uint64_t) * n);
+  L->recgrad = take(sizeof(float) * 10 * R_cap);
+  L->dsigma = take(sizeof(float) * 6 * n_cap);
+  L->drgb = take(sizeof(float) * 3 * R_cap);
+  L->csr_keys0 = take(sizeof(uint64_t) * n_cap);
+  L->csr_keys1 = take(sizeof(uint64_t) * n_cap);
   L->csr_off_sr = take(sizeof(uint32_t) * (3 * (int64_t)s->k_sr + 1));
   L->csr_off_sh = take(sizeof(uint32_t) * (3 * (int64_t)s->k_sh + 1));
-  L->csr_ids_sr = take(sizeof(uint32_t) * n);
-  L->csr_ids_sh = take(sizeof(uint32_t) * n);
+  L->csr_ids_sr = take(sizeof(uint32_t) * n_cap);
+  L->csr_ids_sh = take(sizeof(uint32_t) * n_cap);
   L->chunks = take(sizeof(uint4) * L->chunks_cap);
   L->chunks_sh = take(sizeof(uint4) * L->chunks_cap);
-  L->csr_idx_sr = take(sizeof(uint16_t) * n);
-  L->csr_idx_sh = take(sizeof(uint16_t) * n);
+  L->csr_idx_sr = take(sizeof(uint16_t) * n_cap);
+  L->csr_idx_sh = take(sizeof(uint16_t) * n_cap);
   L->csr_state = take(2 * sizeof(CsrState));
+  L->csr_tmp = take(sizeof(uint32_t) * (4 * (kmax + 1) + n_cap));  // incremental membership update
   L->partials = take(sizeof(float) * std::max(6, 3 * nb) * L->chunks_cap);
   L->hist = take(sizeof(uint32_t) * (256 * L->sort_blocks_cap + 256));
   L->blocksums = take(sizeof(uint64_t) * L->scan_blocks_cap);
@@ -289,6 +293,17 @@ cg_status cg_codebook_reduce(const cg_scene* scene, const cg_camera* cams, int n
   return cuda_status(launch_codebook_reduce(scene_args(scene), L, workspace, d_sr_rows, d_sh_rows, s));
 }
 
+cg_status cg_codebook_append(const cg_scene* scene, const cg_camera* cams, int n_views, const cg_opts* opts,
+                             void* workspace, size_t ws_bytes, int n_old, cg_stream_t stream) {
+  Layout L;
+  cg_status st = plan_call(scene, cams, n_views, opts, workspace, ws_bytes, &L);
+  if (st == CG_OK && (n_old < 1 || n_old > scene->n)) st = CG_ERR_ARG;
+  if (st != CG_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  StageTimer t(CG_STAGE_REDUCE, s);
+  return cuda_status(launch_codebook_append(scene_args(scene), L, workspace, n_old, s));
+}
+
 cg_status cg_last_device_status(void* workspace, size_t ws_bytes, cg_stream_t stream, uint64_t* pairs_out) {
   if (!workspace || ws_bytes < sizeof(WsHeader) || !aligned(workspace, kAlign)) return CG_ERR_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -336,6 +351,7 @@ cg_status cg_workspace_array(void* workspace, size_t ws_bytes, cg_ws_array which
     case CG_WS_GEO: off = L.geo; cnt = L.R; break;
     case CG_WS_RGB: off = L.rgbm; cnt = L.R; break;
     case CG_WS_SIGMA3: off = L.sigma3; cnt = L.k_sr; break;
+    case CG_WS_CSR_STATE: off = L.csr_state; cnt = 2; break;
     default: return CG_ERR_ARG;
   }
   *ptr_out = b + off;
@@ -470,6 +486,28 @@ cg_status cg_codebook_split(const cg_mh_opts* opts, void* rows, int32_t* parent,
 cg_status cg_codebook_merge(const cg_mh_opts* opts, void* rows, int32_t* parent, uint16_t* g2x, int32_t* k_out,
                             void* workspace, size_t ws_bytes, cg_stream_t stream) {
   return mh_call(false, opts, rows, parent, g2x, k_out, workspace, ws_bytes, stream);
+}
+
+size_t cg_grow_workspace_bytes(int n) { return n < 1 ? 0 : (size_t)grow_workspace_bytes(n); }
+
+cg_status cg_grow(const cg_params* p, uint16_t* g2sr, uint16_t* g2sh, int m, uint64_t seed, uint64_t step,
+                  int32_t* src_out, void* workspace, size_t ws_bytes, cg_stream_t stream) {
+  if (!p || p->n < 1 || m < 0 || (int64_t)p->n + m > (int64_t)1 << 30 || !p->pos || !p->opacity_logit || !g2sr ||
+      !g2sh || !aligned(p->pos, 4) || !aligned(p->opacity_logit, 4) || !aligned(g2sr, 2) || !aligned(g2sh, 2) ||
+      (src_out && !aligned(src_out, 4)) || !workspace || !aligned(workspace, kAlign) ||
+      ws_bytes < grow_workspace_bytes(p->n))
+    return CG_ERR_ARG;
+  GrowArgs a;
+  a.n = p->n;
+  a.m = m;
+  a.pos = p->pos;
+  a.logit = p->opacity_logit;
+  a.g2sr = g2sr;
+  a.g2sh = g2sh;
+  a.src_out = src_out;
+  a.seed = seed;
+  a.step = step;
+  return cuda_status(launch_grow(a, workspace, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 float cg_host_exp32(float x) { return exp32(x); }

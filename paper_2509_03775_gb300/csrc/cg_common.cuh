@@ -266,7 +266,7 @@ struct Layout {
   uint64_t total;
   uint64_t hdr, views, sigma3, geo, rgbm, rect, ntiles, depth, offrec, scan, dkeys0, dkeys1, pairs0, pairs1,
       ranges, tfinal, ncontrib, pairgrad, pairgrad1, recgrad, nemit, kmask, dsigma, drgb, csr_keys0, csr_keys1, csr_off_sr, csr_off_sh, csr_ids_sr, csr_ids_sh, chunks, chunks_sh,
-      csr_idx_sr, csr_idx_sh, csr_state,
+      csr_idx_sr, csr_idx_sh, csr_state, csr_tmp,
       partials, hist, blocksums, l1;
   // sizes
   int64_t n, R, T, P, Kc;
@@ -284,8 +284,8 @@ struct CsrState {
   uint64_t idx_ptr;
   uint32_t k;
   uint32_t n;
-  uint32_t changed;   // set by the check, cleared when the build is done
-  uint32_t pad;
+  uint32_t changed;   // set by the check (bit 0 rebuild, bit 1 append), cleared when done
+  uint32_t appends;   // incremental updates done (for tests)
   uint64_t nchunks;   // chunks of the cached build
 };
 constexpr uint64_t kCsrMagic = 0x43535243'00000001ull;
@@ -416,6 +416,7 @@ cudaError_t launch_gaussian_bwd(const SceneArgs& sc, const Layout& L, void* ws, 
                                 cudaStream_t s);
 cudaError_t launch_codebook_reduce(const SceneArgs& sc, const Layout& L, void* ws, float* d_sr, float* d_sh,
                                    cudaStream_t s);
+cudaError_t launch_codebook_append(const SceneArgs& sc, const Layout& L, void* ws, int64_t n_old, cudaStream_t s);
 cudaError_t launch_l1(const float* img, const float* tgt, int64_t count, float* d_img, double* loss,
                       const Layout& L, void* ws, cudaStream_t s);
 uint64_t recon_workspace_bytes(const cg_camera* cams, int n_views);

@@ -20,7 +20,7 @@ constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
 
 // Draw streams (counter word c1 = stream | call << 8).
 constexpr uint32_t kStreamPos = 0, kStreamLogit = 1, kStreamSR = 2, kStreamSH = 3;
-constexpr uint32_t kStreamSplitU = 16, kStreamSplitV = 18, kStreamMerge = 20;
+constexpr uint32_t kStreamSplitU = 16, kStreamSplitV = 18, kStreamMerge = 20, kStreamGrow = 24;
 
 // Ten rounds; each maps (c0, c1, c2, c3) under key (k0, k1) to
 // (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)), and the
@@ -182,6 +182,19 @@ struct MhLayout {
   int64_t scan_blocks_cap;
 };
 
+// Growth: m copies appended after the n Gaussians (arrays hold n + m).
+struct GrowArgs {
+  int64_t n, m;
+  float* pos;
+  float* logit;
+  uint16_t* g2sr;
+  uint16_t* g2sh;
+  int32_t* src_out;
+  uint64_t seed, step;
+};
+
+uint64_t grow_workspace_bytes(int64_t n);
+cudaError_t launch_grow(const GrowArgs& a, void* ws, cudaStream_t s);
 MhLayout mh_layout(int n, int k_cap, int width);
 cudaError_t launch_sgld(const SgldArgs& a, cudaStream_t s);
 cudaError_t launch_split(const MhArgs& a, const MhLayout& M, void* ws, cudaStream_t s);

@@ -313,7 +313,7 @@ cudaError_t launch_gaussian_bwd(const SceneArgs& sc, const Layout& L, void* ws, 
 // keyed past the last row.
 __global__ void k_row_keys(const uint16_t* __restrict__ idx, int64_t n, int k, uint64_t* __restrict__ keys,
                            uint64_t* count_slot, const CsrState* cs) {
-  if (!cs->changed) {
+  if (!(cs->changed & 1u)) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *count_slot = 0;
     return;
   }
@@ -326,7 +326,7 @@ __global__ void k_row_keys(const uint16_t* __restrict__ idx, int64_t n, int k, u
 }
 
 __global__ void k_zero_counts(uint32_t* c, int64_t m, const CsrState* cs) {
-  if (cs && !cs->changed) return;
+  if (cs && !(cs->changed & 1u)) return;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) c[i] = 0u;
 }
@@ -335,7 +335,7 @@ __global__ void k_zero_counts(uint32_t* c, int64_t m, const CsrState* cs) {
 // (rows without members keep start = end = 0).
 __global__ void k_row_bounds(const uint64_t* __restrict__ keys, int64_t n, int k, uint32_t* __restrict__ start,
                              uint32_t* __restrict__ end, uint32_t* __restrict__ ids, const CsrState* cs) {
-  if (!cs->changed) return;
+  if (!(cs->changed & 1u)) return;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const uint64_t key = keys[i];
@@ -581,6 +581,7 @@ __global__ void __launch_bounds__(256) k_csr_check(const uint16_t* __restrict__ 
 // Records the chunk count and the key of a new build; clears the flag.
 __global__ void k_csr_done(CsrState* cs, const uint64_t* nchunks_dev, const uint16_t* idx, int64_t n, int k) {
   if (!cs->changed) return;
+  cs->appends = cs->changed == 2u ? cs->appends + 1u : 0u;  // counts appends since the last rebuild
   cs->nchunks = *nchunks_dev;
   cs->magic = kCsrMagic;
   cs->idx_ptr = (uint64_t)(uintptr_t)idx;
@@ -615,6 +616,138 @@ static cudaError_t build_csr(void* ws, const Layout& L, const uint16_t* idx, uin
   count_launch(), k_fill_chunks<<<gk, 256, 0, s>>>(start, end, cbase, k, chunks, cs);
   count_launch(), k_csr_done<<<1, 1, 0, s>>>(cs, &st->red_a, idx, n, k);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// incremental membership update after growth
+// ---------------------------------------------------------------------------
+// Gaussians n_old .. n - 1 were appended.  If the kept membership belongs to
+// the first n_old entries of this index array (key and copy match), each
+// row's member list becomes its old list followed by its new members in
+// index order: new members are sorted by (row, index) alone, rows' new
+// starts come from a scan of old + new counts, old members move by their
+// row's shift, new members fill the tails.  Otherwise the membership is
+// rebuilt.  cs->changed: bit 0 full rebuild, bit 1 append.
+
+__global__ void __launch_bounds__(256) k_csr_check_append(const uint16_t* __restrict__ idx, uint16_t* __restrict__ copy,
+                                                          int64_t n_old, int64_t n, int k, CsrState* cs) {
+  bool full = cs->magic != kCsrMagic || cs->idx_ptr != (uint64_t)(uintptr_t)idx || cs->k != (uint32_t)k ||
+              cs->n != (uint32_t)n_old || n_old >= n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += stride) {
+    const uint16_t v = idx[g];
+    if ((g < n_old && copy[g] != v) || v >= (uint32_t)k) full = true;
+    copy[g] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&cs->changed, 2u);
+  if (__syncthreads_or(full) && threadIdx.x == 0) atomicOr(&cs->changed, 1u);
+}
+
+// Keys of the new members only (the full rebuild uses k_row_keys).
+__global__ void k_app_keys(const uint16_t* __restrict__ idx, int64_t n_old, int64_t n, int k,
+                           uint64_t* __restrict__ keys, uint64_t* count_slot, const CsrState* cs) {
+  if (cs->changed != 2u) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *count_slot = 0;
+    return;
+  }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = n_old + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += stride) {
+    const uint32_t r = idx[g];
+    keys[g - n_old] = ((uint64_t)(r < (uint32_t)k ? r : (uint32_t)k) << 32) | (uint64_t)g;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *count_slot = (uint64_t)(n - n_old);
+}
+
+// Per row: old count, new count, the first new member's position in the
+// sorted new keys, and old + new (the scan inputs).
+__global__ void k_app_rows(const uint32_t* __restrict__ start, const uint32_t* __restrict__ end, int k,
+                           const uint64_t* __restrict__ nkeys, int64_t m, uint32_t* __restrict__ t_old,
+                           uint32_t* __restrict__ t_excl, uint32_t* __restrict__ t_tot, uint32_t* __restrict__ t_first,
+                           uint64_t* count_slot, const CsrState* cs) {
+  if (cs->changed != 2u) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *count_slot = 0;
+    return;
+  }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < k; r += stride) {
+    // [lo, hi): the new members of row r in the sorted keys
+    int64_t lo = 0, hi = m;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((nkeys[mid] >> 32) < (uint64_t)r) lo = mid + 1; else hi = mid;
+    }
+    int64_t lo2 = lo, hi2 = m;
+    while (lo2 < hi2) {
+      const int64_t mid = (lo2 + hi2) >> 1;
+      if ((nkeys[mid] >> 32) <= (uint64_t)r) lo2 = mid + 1; else hi2 = mid;
+    }
+    const uint32_t oc = end[r] - start[r], ac = (uint32_t)(lo2 - lo);
+    t_old[r] = oc;
+    t_excl[r] = oc;
+    t_tot[r] = oc + ac;
+    t_first[r] = (uint32_t)lo;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *count_slot = (uint64_t)k;
+}
+
+__global__ void k_app_copy(const uint32_t* __restrict__ ids, int64_t n_old, uint32_t* __restrict__ tmp,
+                           const CsrState* cs) {
+  if (cs->changed != 2u) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_old; p += stride) tmp[p] = ids[p];
+}
+
+// Old member at position p of row r (old_excl[r] <= p) moves to
+// new_start[r] + (p - old_excl[r]); new member q of row r goes to
+// new_start[r] + old[r] + (q - first[r]).
+__global__ void k_app_place(const uint32_t* __restrict__ tmp, int64_t n_old, const uint64_t* __restrict__ nkeys,
+                            int64_t m, int k, const uint32_t* __restrict__ t_old,
+                            const uint32_t* __restrict__ old_excl, const uint32_t* __restrict__ new_start,
+                            const uint32_t* __restrict__ t_first, uint32_t* __restrict__ ids, const CsrState* cs) {
+  if (cs->changed != 2u) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_old + m; p += stride) {
+    if (p < n_old) {
+      // the last row whose old block starts at or before p and is not empty
+      int lo = 0, hi = k - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (old_excl[mid] <= (uint32_t)p) lo = mid; else hi = mid - 1;
+      }
+      while (lo > 0 && t_old[lo] == 0u) --lo;  // rows without old members share the next start
+      ids[new_start[lo] + ((uint32_t)p - old_excl[lo])] = tmp[p];
+    } else {
+      const int64_t q = p - n_old;
+      const uint64_t key = nkeys[q];
+      const uint32_t r = (uint32_t)(key >> 32);
+      if (r >= (uint32_t)k) continue;  // index past the rows (reported by the forward)
+      ids[new_start[r] + t_old[r] + ((uint32_t)q - t_first[r])] = (uint32_t)key;
+    }
+  }
+}
+
+// Row bounds after the move: start = the scanned start, length = old count
+// plus the row's new members (from the sorted new keys).
+__global__ void k_app_rows_total(const uint32_t* __restrict__ t_old, const uint32_t* __restrict__ new_start,
+                                 const uint64_t* __restrict__ nkeys, int64_t m, int k, uint32_t* __restrict__ start,
+                                 uint32_t* __restrict__ end, const CsrState* cs) {
+  if (cs->changed != 2u) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < k; r += stride) {
+    int64_t lo = 0, hi = m;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((nkeys[mid] >> 32) < (uint64_t)r) lo = mid + 1; else hi = mid;
+    }
+    int64_t lo2 = lo, hi2 = m;
+    while (lo2 < hi2) {
+      const int64_t mid = (lo2 + hi2) >> 1;
+      if ((nkeys[mid] >> 32) <= (uint64_t)r) lo2 = mid + 1; else hi2 = mid;
+    }
+    const uint32_t t = t_old[r] + (uint32_t)(lo2 - lo);
+    start[r] = t ? new_start[r] : 0u;
+    end[r] = t ? new_start[r] + t : 0u;
+  }
 }
 
 cudaError_t launch_codebook_reduce(const SceneArgs& sc, const Layout& L, void* ws, float* d_sr, float* d_sh,
@@ -711,6 +844,61 @@ __global__ void k_l1_final(const double* __restrict__ part, int64_t count, doubl
     for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
     *loss = t / (double)count;
   }
+}
+
+static cudaError_t append_csr(void* ws, const Layout& L, const uint16_t* idx, uint16_t* copy, int k, int64_t n_old,
+                              uint32_t* csr, uint32_t* ids, uint4* chunks, CsrState* cs, DeviceState* st,
+                              cudaStream_t s) {
+  const int64_t n = L.n, m = n - n_old;
+  uint32_t* start = csr;
+  uint32_t* end = csr + k;
+  uint32_t* cbase = csr + 2 * (int64_t)k;
+  uint64_t* k0 = ws_ptr<uint64_t>(ws, L.csr_keys0);
+  uint64_t* k1 = ws_ptr<uint64_t>(ws, L.csr_keys1);
+  const int64_t K1 = std::max(L.k_sr, L.k_sh) + 2;
+  uint32_t* t_old = ws_ptr<uint32_t>(ws, L.csr_tmp);
+  uint32_t* t_excl = t_old + K1;
+  uint32_t* t_tot = t_old + 2 * K1;
+  uint32_t* t_first = t_old + 3 * K1;
+  uint32_t* tmp = t_old + 4 * K1;
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
+  const int gk = std::max(1, std::min((2 * k + 255) / 256, 152 * 8));
+  count_launch(), k_csr_check_append<<<g, 256, 0, s>>>(idx, copy, n_old, n, k, cs);
+  count_launch(), k_zero_counts<<<gk, 256, 0, s>>>(start, 2 * (int64_t)k, cs);
+  count_launch(), k_row_keys<<<g, 256, 0, s>>>(idx, n, k, k0, &st->red_a, cs);
+  count_launch(), k_app_keys<<<g, 256, 0, s>>>(idx, n_old, n, k, k0, &st->red_a, cs);
+  bool in_b = false;
+  cudaError_t e = sort_u64(ws, L, k0, k1, &st->red_a, n, 32, k >= 65536 ? 3 : 2, &in_b, s);
+  if (e != cudaSuccess) return e;
+  const uint64_t* sorted = in_b ? k1 : k0;
+  count_launch(), k_row_bounds<<<g, 256, 0, s>>>(sorted, n, k, start, end, ids, cs);
+  count_launch(), k_app_rows<<<gk, 256, 0, s>>>(start, end, k, sorted, m, t_old, t_excl, t_tot, t_first, &st->red_b,
+                                                cs);
+  e = scan_u32(ws, L, t_tot, t_tot, &st->red_b, k, &st->red_a, s);  // t_tot <- new starts
+  if (e == cudaSuccess) e = scan_u32(ws, L, t_excl, t_excl, &st->red_b, k, &st->red_a, s);
+  if (e != cudaSuccess) return e;
+  count_launch(), k_app_copy<<<g, 256, 0, s>>>(ids, n_old, tmp, cs);
+  count_launch(), k_app_place<<<g, 256, 0, s>>>(tmp, n_old, sorted, m, k, t_old, t_excl, t_tot, t_first, ids, cs);
+  // new totals per row again (t_tot now holds the starts)
+  count_launch(), k_app_rows_total<<<gk, 256, 0, s>>>(t_old, t_tot, sorted, m, k, start, end, cs);
+  count_launch(), k_chunk_counts<<<gk, 256, 0, s>>>(start, end, k, cbase, &st->red_b, cs);
+  e = scan_u32(ws, L, cbase, cbase, &st->red_b, k, &st->red_a, s);
+  if (e != cudaSuccess) return e;
+  count_launch(), k_fill_chunks<<<gk, 256, 0, s>>>(start, end, cbase, k, chunks, cs);
+  count_launch(), k_csr_done<<<1, 1, 0, s>>>(cs, &st->red_a, idx, n, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_codebook_append(const SceneArgs& sc, const Layout& L, void* ws, int64_t n_old, cudaStream_t s) {
+  DeviceState* st = &ws_ptr<WsHeader>(ws, L.hdr)->st;
+  CsrState* cs = ws_ptr<CsrState>(ws, L.csr_state);
+  cudaError_t e = append_csr(ws, L, sc.g2sr, ws_ptr<uint16_t>(ws, L.csr_idx_sr), sc.k_sr, n_old,
+                             ws_ptr<uint32_t>(ws, L.csr_off_sr), ws_ptr<uint32_t>(ws, L.csr_ids_sr),
+                             ws_ptr<uint4>(ws, L.chunks), &cs[0], st, s);
+  if (e != cudaSuccess) return e;
+  return append_csr(ws, L, sc.g2sh, ws_ptr<uint16_t>(ws, L.csr_idx_sh), sc.k_sh, n_old,
+                    ws_ptr<uint32_t>(ws, L.csr_off_sh), ws_ptr<uint32_t>(ws, L.csr_ids_sh),
+                    ws_ptr<uint4>(ws, L.chunks_sh), &cs[1], st, s);
 }
 
 cudaError_t launch_l1(const float* img, const float* tgt, int64_t count, float* d_img, double* loss,

@@ -405,4 +405,154 @@ cudaError_t launch_merge(const MhArgs& a, const MhLayout& M, void* ws, cudaStrea
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// growth: m copies of existing Gaussians, drawn in proportion to opacity
+// ---------------------------------------------------------------------------
+
+constexpr int kGrowItems = 16;
+constexpr int kGrowTile = 256 * kGrowItems;
+
+// Integer weights floor(o 2^24) (the product is exact in FP32) summed per
+// block of kGrowTile Gaussians.
+__global__ void __launch_bounds__(256) k_grow_blocksum(const float* __restrict__ logit, int64_t n,
+                                                       uint64_t* __restrict__ bsum) {
+  __shared__ uint64_t red[8];
+  const int64_t b = blockIdx.x;
+  uint64_t acc = 0;
+  for (int k = 0; k < kGrowItems; ++k) {
+    const int64_t i = b * kGrowTile + (int64_t)k * 256 + threadIdx.x;
+    if (i < n) acc += (uint64_t)floorf(sigmoid32(logit[i]) * 16777216.0f);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t t = 0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    bsum[b] = t;
+  }
+}
+
+// Exclusive scan of the block sums (one CTA); the total goes to *total.
+__global__ void __launch_bounds__(1024) k_grow_scanblocks(uint64_t* __restrict__ bsum, int64_t nb,
+                                                          uint64_t* __restrict__ total) {
+  __shared__ uint64_t ws[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint64_t carry = 0;
+  for (int64_t c = 0; c < nb; c += 1024) {
+    const int64_t i = c + threadIdx.x;
+    const uint64_t v = i < nb ? bsum[i] : 0ull;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      uint64_t sw = ws[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, sw, o);
+        if (lane >= o) sw += y;
+      }
+      ws[lane] = sw;
+    }
+    __syncthreads();
+    if (i < nb) bsum[i] = carry + (wid > 0 ? ws[wid - 1] : 0ull) + x - v;
+    const uint64_t tot = ws[31];
+    __syncthreads();
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+// Inclusive prefix of the weights per Gaussian (thread t owns kGrowItems
+// consecutive Gaussians of its block).
+__global__ void __launch_bounds__(256) k_grow_prefix(const float* __restrict__ logit, int64_t n,
+                                                     const uint64_t* __restrict__ bsum, uint64_t* __restrict__ incl) {
+  __shared__ uint64_t ws[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kGrowTile + (int64_t)threadIdx.x * kGrowItems;
+  uint64_t w[kGrowItems];
+  uint64_t local = 0;
+#pragma unroll
+  for (int k = 0; k < kGrowItems; ++k) {
+    w[k] = base + k < n ? (uint64_t)floorf(sigmoid32(logit[base + k]) * 16777216.0f) : 0ull;
+    local += w[k];
+  }
+  uint64_t x = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[wid] = x;
+  __syncthreads();
+  uint64_t pre = bsum[blockIdx.x];
+  for (int i = 0; i < wid; ++i) pre += ws[i];
+  uint64_t run = pre + x - local;
+#pragma unroll
+  for (int k = 0; k < kGrowItems; ++k) {
+    run += w[k];
+    if (base + k < n) incl[base + k] = run;
+  }
+}
+
+// New Gaussian j copies the Gaussian whose weight interval holds
+// u = x mod W (x: the 64-bit draw of counter (j, stream 24, step)); with
+// W = 0 every Gaussian has weight 1.
+__global__ void __launch_bounds__(256) k_grow_pick(const GrowArgs a, const uint64_t* __restrict__ incl,
+                                                   const uint64_t* __restrict__ total_dev) {
+  const uint64_t total = *total_dev;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.m; j += stride) {
+    const uint4 d = draw4((uint32_t)j, kStreamGrow, 0, a.step, a.seed);
+    const uint64_t x = ((uint64_t)d.y << 32) | d.x;
+    int64_t src;
+    if (total == 0) {
+      src = (int64_t)(x % (uint64_t)a.n);
+    } else {
+      const uint64_t u = x % total;
+      // first Gaussian whose inclusive prefix exceeds u
+      int64_t lo = 0, hi = a.n - 1;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (incl[mid] > u)
+          hi = mid;
+        else
+          lo = mid + 1;
+      }
+      src = lo;
+    }
+    const int64_t dst = a.n + j;
+    a.pos[3 * dst] = a.pos[3 * src];
+    a.pos[3 * dst + 1] = a.pos[3 * src + 1];
+    a.pos[3 * dst + 2] = a.pos[3 * src + 2];
+    a.logit[dst] = a.logit[src];
+    a.g2sr[dst] = a.g2sr[src];
+    a.g2sh[dst] = a.g2sh[src];
+    if (a.src_out) a.src_out[j] = (int32_t)src;
+  }
+}
+
+uint64_t grow_workspace_bytes(int64_t n) {
+  const int64_t nb = (n + kGrowTile - 1) / kGrowTile;
+  return 256 + ((8 * (uint64_t)nb + 255) & ~uint64_t(255)) + 8 * (uint64_t)n;
+}
+
+cudaError_t launch_grow(const GrowArgs& a, void* ws, cudaStream_t s) {
+  const int64_t nb = (a.n + kGrowTile - 1) / kGrowTile;
+  uint64_t* total = reinterpret_cast<uint64_t*>(ws);
+  uint64_t* bsum = ws_ptr<uint64_t>(ws, 256);
+  uint64_t* incl = ws_ptr<uint64_t>(ws, 256 + ((8 * (uint64_t)nb + 255) & ~uint64_t(255)));
+  count_launch(), k_grow_blocksum<<<(unsigned)nb, 256, 0, s>>>(a.logit, a.n, bsum);
+  count_launch(), k_grow_scanblocks<<<1, 1024, 0, s>>>(bsum, nb, total);
+  count_launch(), k_grow_prefix<<<(unsigned)nb, 256, 0, s>>>(a.logit, a.n, bsum, incl);
+  if (a.m > 0) count_launch(), k_grow_pick<<<grid_for(a.m, 256), 256, 0, s>>>(a, incl, total);
+  return cudaGetLastError();
+}
+
 }  // namespace cg

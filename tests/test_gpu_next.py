@@ -312,3 +312,62 @@ def test_training_step_with_recon_loss_and_sgld_captured_in_a_graph():
     for a, b in zip(eager, (st.pos, st.opacity_logit, st.sr_rows, st.sh_rows, bufs["loss"])):
         assert torch.equal(a, b)
     assert not torch.equal(eager[0], snap0[0])
+
+
+# ----------------------------------------------------------------------------
+# growth and the incremental membership update
+# ----------------------------------------------------------------------------
+
+def test_growth_matches_oracle_and_membership_update_matches_rebuild():
+    scene, cams = scenes.config_single(n=20_000, k=256, width=160, height=128)
+    n, m = scene.n, 1000
+    n_cap = n + m
+    dev = "cuda"
+
+    def cap(a, dt, shape_tail=()):
+        t = torch.zeros((n_cap,) + shape_tail, dtype=dt, device=dev)
+        t[:n] = torch.from_numpy(np.ascontiguousarray(a)).to(dev).view(dt) if dt == torch.int16 else \
+            torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        return t
+
+    pos = cap(scene.pos, torch.float32, (3,))
+    logit = cap(scene.opacity_logit, torch.float32)
+    g2sr = cap(scene.g2sr.view(np.int16), torch.int16)
+    g2sh = cap(scene.g2sh.view(np.int16), torch.int16)
+    sr = torch.from_numpy(scene.sr_rows).to(dev)
+    sh = torch.from_numpy(scene.sh_rows).to(dev)
+
+    def tensors(count):
+        return cg.SceneTensors(pos[:count], logit[:count], g2sr[:count], g2sh[:count], sr, sh, scene.sh_degree)
+
+    rng = np.random.default_rng(9)
+    d_img = torch.from_numpy(rng.normal(size=3 * 160 * 128).astype(np.float32)).cuda()
+
+    def grads(r, st):
+        r.forward(st)
+        r.backward(d_img)
+        return [t.clone() for t in r.codebook_reduce()]
+
+    r = cg.Renderer(cams, pair_capacity=1 << 22, n_capacity=n_cap)
+    grads(r, tensors(n))                                  # keeps the memberships of n Gaussians
+    src = cg.grow(pos, logit, g2sr, g2sh, n, m, seed=17, step=300)
+    torch.cuda.synchronize()
+    ref = mcmc.grow(scene.pos, scene.opacity_logit, scene.g2sr, scene.g2sh, m, 300, 17)
+    assert np.array_equal(src.cpu().numpy(), ref["src"])
+    assert np.array_equal(pos.cpu().numpy(), ref["pos"])
+    assert np.array_equal(logit.cpu().numpy(), ref["logit"])
+    assert np.array_equal(g2sh.cpu().numpy().view(np.uint16), ref["g2sh"])
+    grown = tensors(n + m)
+    r.codebook_append(grown, n)                           # incremental update of the kept lists
+    state = r.array(cg.WS_CSR_STATE, torch.int32, 10).cpu().numpy().reshape(2, 10)
+    assert list(state[:, 7]) == [1, 1]                    # both lists were extended, not rebuilt
+    assert list(state[:, 5]) == [n + m, n + m]
+    got = grads(r, grown)
+    fresh = grads(cg.Renderer(cams, pair_capacity=1 << 22), grown)
+    for a, b in zip(got, fresh):
+        assert torch.equal(a, b)
+    # without the incremental call the reduction rebuilds the lists itself
+    r2 = cg.Renderer(cams, pair_capacity=1 << 22, n_capacity=n_cap)
+    grads(r2, tensors(n))
+    for a, b in zip(grads(r2, grown), fresh):
+        assert torch.equal(a, b)
