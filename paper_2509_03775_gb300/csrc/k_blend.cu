@@ -176,7 +176,9 @@ struct PixelBwd {
 };
 
 // Per-pixel backward of one Gaussian at list position `pos`; adds its nine
-// terms (summed over the thread's pixels) into g[9 * S ...].
+// terms (summed over the thread's pixels) into g[9 * S ...]: the moments
+// sum dpow dx, dpow dy, dpow dx^2, dpow dx dy, dpow dy^2 of dpow = dL/dpower,
+// dL/dopacity, dL/drgb.
 template <int PPT, int S>
 __device__ __forceinline__ bool bwd_gaussian(const float4& a, const float4& b, const float4& c, uint32_t pos,
                                              float pxc, PixelBwd<PPT>& px, float (&g)[32]) {
@@ -208,12 +210,15 @@ __device__ __forceinline__ bool bwd_gaussian(const float4& a, const float4& b, c
                            fmaf(c.y - px.acc[k][1], px.dC[k][1], (c.z - px.acc[k][2]) * px.dC[k][2]));
     const float dalpha = fmaf(Tk, dot, -px.bgdot[k] * rom);
     if (!clamped) {
+      // moments of dL/dpower: sum dpow (dx, dy, dx^2, dx dy, dy^2); the
+      // mean and conic gradients are linear in them (see k_blend_bwd)
       const float dpow = alpha * dalpha;
-      g[9 * S + 0] = fmaf(dpow, fmaf(2.0f * a.z, dx, a.w * dy), g[9 * S + 0]);
-      g[9 * S + 1] = fmaf(dpow, fmaf(2.0f * b.x, dy, a.w * dx), g[9 * S + 1]);
-      g[9 * S + 2] = fmaf(dpow, -0.5f * dx * dx, g[9 * S + 2]);
-      g[9 * S + 3] = fmaf(dpow, -dx * dy, g[9 * S + 3]);
-      g[9 * S + 4] = fmaf(dpow, -0.5f * dy * dy, g[9 * S + 4]);
+      const float px_ = dpow * dx, py_ = dpow * dy;
+      g[9 * S + 0] += px_;
+      g[9 * S + 1] += py_;
+      g[9 * S + 2] = fmaf(px_, dx, g[9 * S + 2]);
+      g[9 * S + 3] = fmaf(px_, dy, g[9 * S + 3]);
+      g[9 * S + 4] = fmaf(py_, dy, g[9 * S + 4]);
       g[9 * S + 5] = fmaf(ex, dalpha, g[9 * S + 5]);
     }
     px.acc[k][0] = fmaf(alpha, c.x - px.acc[k][0], px.acc[k][0]);
@@ -318,7 +323,10 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const Bl
       }
     }
     __syncthreads();
-    // sums over the warps, in warp order; components (0..3), (4, 6, 7, 8), 5
+    // sums over the warps, in warp order; components (0..3), (4, 6, 7, 8), 5.
+    // With power = h0 dx^2 + h1 dx dy + h2 dy^2 and d = mean - pixel, the
+    // pair's dL/dmean = (2 h0 Sx + h1 Sy, 2 h2 Sy + h1 Sx) and dL/d(conic
+    // c0, c1, c2) = (-Sxx / 2, -Sxy, -Syy / 2) from the moment sums S.
     for (int i = threadIdx.x; i < n_in * 3; i += NT) {
       const int j = i / 3, q = i - 3 * j;
       if (q < 2) {
@@ -330,6 +338,12 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const Bl
           t.y += part[w][j][e1];
           t.z += part[w][j][e2];
           t.w += part[w][j][e3];
+        }
+        if (q == 0) {
+          const float h0 = sA[j].z, h1 = sA[j].w, h2 = sB[j].x;
+          t = make_float4(fmaf(2.0f * h0, t.x, h1 * t.y), fmaf(2.0f * h2, t.y, h1 * t.x), -0.5f * t.z, -t.w);
+        } else {
+          t.x = -0.5f * t.x;
         }
         args.pairgrad[2 * (size_t)sSlot[j] + q] = t;
       } else {
