@@ -425,17 +425,20 @@ cudaError_t launch_recon_loss(const float* x, const float* y, const cg_camera* c
 
 // The depth-sorted visible records (4 sort passes end in dkeys0).
 inline uint64_t* depth_sorted(void* ws, const Layout& L) { return ws_ptr<uint64_t>(ws, L.dkeys0); }
-// The tile-sorted pairs (tile passes of 8 bits: an odd count ends in pairs1).
-inline int tile_passes(const Layout& L) { return (L.tile_bits + 7) / 8; }
+// Passes of a radix sort on nbits bits (digits of at most 8 bits).
+inline int sort_passes(int nbits) { return (nbits + 7) / 8; }
+// The tile-sorted pairs (an odd number of passes ends in pairs1).
+inline int tile_passes(const Layout& L) { return sort_passes(L.tile_bits); }
 inline uint64_t* sorted_pairs(void* ws, const Layout& L) {
   return ws_ptr<uint64_t>(ws, (tile_passes(L) & 1) ? L.pairs1 : L.pairs0);
 }
 
-// Radix sort of `count` (device value) uint64 keys on bits [lo, lo + 8 * passes),
-// stable, ping-pong between a and b; returns in *result_in_b whether the
-// sorted keys end in b.  Used for depth keys, tile keys and codebook rows.
+// Radix sort of `count` (device value) uint64 keys on bits [lo, lo + nbits),
+// stable, in sort_passes(nbits) passes of equal digits (4 to 8 bits),
+// ping-pong between a and b; returns in *result_in_b whether the sorted keys
+// end in b.  Used for depth keys, tile keys and codebook rows.
 cudaError_t sort_u64(void* ws, const Layout& L, uint64_t* a, uint64_t* b, const uint64_t* count_dev,
-                     int64_t count_cap, int lo_bit, int passes, bool* result_in_b, cudaStream_t s);
+                     int64_t count_cap, int lo_bit, int nbits, bool* result_in_b, cudaStream_t s);
 // Exclusive scan of `count` (device value) uint32 values into out (may alias in),
 // total written to *total_dev.
 cudaError_t scan_u32(void* ws, const Layout& L, const uint32_t* in, uint32_t* out, const uint64_t* count_dev,

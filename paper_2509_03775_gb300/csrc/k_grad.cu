@@ -607,7 +607,7 @@ static cudaError_t build_csr(void* ws, const Layout& L, const uint16_t* idx, uin
   count_launch(), k_zero_counts<<<gk, 256, 0, s>>>(start, 2 * (int64_t)k, cs);
   count_launch(), k_row_keys<<<g, 256, 0, s>>>(idx, n, k, k0, &st->red_a, cs);
   bool in_b = false;
-  cudaError_t e = sort_u64(ws, L, k0, k1, &st->red_a, n, 32, k >= 65536 ? 3 : 2, &in_b, s);
+  cudaError_t e = sort_u64(ws, L, k0, k1, &st->red_a, n, 32, k >= 65536 ? 24 : 16, &in_b, s);
   if (e != cudaSuccess) return e;
   count_launch(), k_row_bounds<<<g, 256, 0, s>>>(in_b ? k1 : k0, n, k, start, end, ids, cs);
   count_launch(), k_chunk_counts<<<gk, 256, 0, s>>>(start, end, k, cbase, &st->red_b, cs);
@@ -868,7 +868,7 @@ static cudaError_t append_csr(void* ws, const Layout& L, const uint16_t* idx, ui
   count_launch(), k_row_keys<<<g, 256, 0, s>>>(idx, n, k, k0, &st->red_a, cs);
   count_launch(), k_app_keys<<<g, 256, 0, s>>>(idx, n_old, n, k, k0, &st->red_a, cs);
   bool in_b = false;
-  cudaError_t e = sort_u64(ws, L, k0, k1, &st->red_a, n, 32, k >= 65536 ? 3 : 2, &in_b, s);
+  cudaError_t e = sort_u64(ws, L, k0, k1, &st->red_a, n, 32, k >= 65536 ? 24 : 16, &in_b, s);
   if (e != cudaSuccess) return e;
   const uint64_t* sorted = in_b ? k1 : k0;
   count_launch(), k_row_bounds<<<g, 256, 0, s>>>(sorted, n, k, start, end, ids, cs);

@@ -28,15 +28,19 @@ constexpr int kGrid = 152 * 8;
 // radix sort
 // ---------------------------------------------------------------------------
 
+// Digits of BITS bits (4..8); a pass over bits [shift, shift + BITS).
+template <int BITS>
 __global__ void __launch_bounds__(kSortThreads) k_sort_upsweep(const uint64_t* __restrict__ keys,
                                                                const uint64_t* count_dev, int64_t count_cap,
                                                                int shift, uint32_t* __restrict__ hist,
                                                                int64_t nb_cap) {
-  __shared__ uint32_t h[256];
+  constexpr int kDigits = 1 << BITS;
+  constexpr uint32_t kMask = kDigits - 1;
+  __shared__ uint32_t h[kDigits];
   const int64_t count = min((int64_t)*count_dev, count_cap);
   const int64_t nb = (count + kSortTile - 1) / kSortTile;
   for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
-    h[threadIdx.x] = 0;
+    if (threadIdx.x < kDigits) h[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = b * kSortTile;
     uint64_t k[kSortItems];
@@ -47,9 +51,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_upsweep(const uint64_t* _
     }
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r)
-      if (base + r * kSortThreads + threadIdx.x < count) atomicAdd(&h[(uint32_t)(k[r] >> shift) & 255u], 1u);
+      if (base + r * kSortThreads + threadIdx.x < count) atomicAdd(&h[(uint32_t)(k[r] >> shift) & kMask], 1u);
     __syncthreads();
-    hist[(int64_t)threadIdx.x * nb_cap + b] = h[threadIdx.x];
+    if (threadIdx.x < kDigits) hist[(int64_t)threadIdx.x * nb_cap + b] = h[threadIdx.x];
     __syncthreads();
   }
 }
@@ -102,6 +106,7 @@ __global__ void __launch_bounds__(1024) k_sort_scan_rows(uint32_t* __restrict__ 
   if (threadIdx.x == 0) digit_tot[blockIdx.x] = carry;
 }
 
+template <int BITS>
 __global__ void __launch_bounds__(kSortThreads, 3) k_sort_downsweep(const uint64_t* __restrict__ in,
                                                                  uint64_t* __restrict__ out,
                                                                  const uint64_t* count_dev, int64_t count_cap,
@@ -109,23 +114,27 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_downsweep(const uint64
                                                                  const uint32_t* __restrict__ digit_tot,
                                                                  int64_t nb_cap) {
   constexpr int kWarps = kSortThreads / 32;
+  constexpr int kDigits = 1 << BITS;
+  constexpr uint32_t kMask = kDigits - 1;
+  static_assert(kDigits <= kSortThreads, "one thread per digit");
   __shared__ uint64_t stage[kSortTile];
-  __shared__ uint32_t wcnt[kWarps][256];
-  __shared__ uint32_t digit_base[256];
-  __shared__ uint32_t bstart[256];
-  __shared__ uint32_t gbase[256];
+  __shared__ uint32_t wcnt[kWarps][kDigits];
+  __shared__ uint32_t digit_base[kDigits];
+  __shared__ uint32_t bstart[kDigits];
+  __shared__ uint32_t gbase[kDigits];
   __shared__ uint32_t scan_ws[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t count = min((int64_t)*count_dev, count_cap);
   const int64_t nb = (count + kSortTile - 1) / kSortTile;
   // global start of each digit
   {
-    const uint32_t t = digit_tot[threadIdx.x];
-    digit_base[threadIdx.x] = block_exclusive_scan<kSortThreads>(t, scan_ws, nullptr);
+    const uint32_t t = threadIdx.x < kDigits ? digit_tot[threadIdx.x] : 0u;
+    const uint32_t ex = block_exclusive_scan<kSortThreads>(t, scan_ws, nullptr);
+    if (threadIdx.x < kDigits) digit_base[threadIdx.x] = ex;
   }
   const uint32_t lt_mask = (1u << lane) - 1u;
   for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
-    for (int i = threadIdx.x; i < kWarps * 256; i += kSortThreads) (&wcnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kWarps * kDigits; i += kSortThreads) (&wcnt[0][0])[i] = 0;
     __syncthreads();
     const int64_t base = b * kSortTile + (int64_t)wid * (32 * kSortItems);
     uint64_t key[kSortItems];
@@ -140,21 +149,23 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_downsweep(const uint64
     for (int r = 0; r < kSortItems; ++r) {
       const int64_t idx = base + r * 32 + lane;
       const bool valid = idx < count;
-      const uint32_t d = valid ? ((uint32_t)(key[r] >> shift) & 255u) : 256u;
-      // lanes holding the same 9-bit value (digit, or 256 for no key): one
-      // ballot per bit
+      // Positions past the end (only in the last block) take the largest
+      // digit: they follow every key of the block in (warp, round, lane)
+      // order, so they rank after all valid keys of that digit and change
+      // no valid key's rank; they are never written out.
+      const uint32_t d = valid ? ((uint32_t)(key[r] >> shift) & kMask) : kMask;
+      // lanes holding the same digit: one ballot per bit
       uint32_t peers = 0xffffffffu;
 #pragma unroll
-      for (int bit = 0; bit < 9; ++bit) {
+      for (int bit = 0; bit < BITS; ++bit) {
         const uint32_t on = (d >> bit) & 1u;
         const uint32_t m = __ballot_sync(0xffffffffu, on != 0u);
         peers &= on ? m : ~m;
       }
       const uint32_t before = __popc(peers & lt_mask);
-      uint32_t old = 0;
-      if (valid) old = wcnt[wid][d];
+      const uint32_t old = wcnt[wid][d];
       __syncwarp();
-      if (valid && before == 0) wcnt[wid][d] = old + __popc(peers);
+      if (before == 0) wcnt[wid][d] = old + __popc(peers);
       __syncwarp();
       rank[r] = old + before;
     }
@@ -163,22 +174,26 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_downsweep(const uint64
     {
       const int d = threadIdx.x;
       uint32_t acc = 0;
+      if (d < kDigits) {
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) {
-        const uint32_t c = wcnt[w][d];
-        wcnt[w][d] = acc;
-        acc += c;
+        for (int w = 0; w < kWarps; ++w) {
+          const uint32_t c = wcnt[w][d];
+          wcnt[w][d] = acc;
+          acc += c;
+        }
       }
       const uint32_t start = block_exclusive_scan<kSortThreads>(acc, scan_ws, nullptr);
-      bstart[d] = start;
-      gbase[d] = digit_base[d] + hist[(int64_t)d * nb_cap + b];
+      if (d < kDigits) {
+        bstart[d] = start;
+        gbase[d] = digit_base[d] + hist[(int64_t)d * nb_cap + b];
+      }
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
       const int64_t idx = base + r * 32 + lane;
       if (idx < count) {
-        const uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
+        const uint32_t d = (uint32_t)(key[r] >> shift) & kMask;
         stage[bstart[d] + wcnt[wid][d] + rank[r]] = key[r];
       }
     }
@@ -186,28 +201,45 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_downsweep(const uint64
     const int valid_n = (int)min((int64_t)kSortTile, count - b * kSortTile);
     for (int i = threadIdx.x; i < valid_n; i += kSortThreads) {
       const uint64_t k = stage[i];
-      const uint32_t d = (uint32_t)(k >> shift) & 255u;
+      const uint32_t d = (uint32_t)(k >> shift) & kMask;
       out[gbase[d] + (uint32_t)i - bstart[d]] = k;
     }
     __syncthreads();
   }
 }
 
+template <int BITS>
+static void sort_pass(const uint64_t* src, uint64_t* dst, const uint64_t* count_dev, int64_t count_cap, int shift,
+                      uint32_t* hist, uint32_t* digit_tot, int64_t nb_cap, int grid, cudaStream_t s) {
+  count_launch(), k_sort_upsweep<BITS><<<grid, kSortThreads, 0, s>>>(src, count_dev, count_cap, shift, hist, nb_cap);
+  count_launch(), k_sort_scan_rows<<<1 << BITS, 1024, 0, s>>>(hist, count_dev, count_cap, nb_cap, digit_tot);
+  count_launch(), k_sort_downsweep<BITS><<<grid, kSortThreads, 0, s>>>(src, dst, count_dev, count_cap, shift, hist,
+                                                                        digit_tot, nb_cap);
+}
+
 cudaError_t sort_u64(void* ws, const Layout& L, uint64_t* a, uint64_t* b, const uint64_t* count_dev,
-                     int64_t count_cap, int lo_bit, int passes, bool* result_in_b, cudaStream_t s) {
+                     int64_t count_cap, int lo_bit, int nbits, bool* result_in_b, cudaStream_t s) {
   uint32_t* hist = ws_ptr<uint32_t>(ws, L.hist);
   uint32_t* digit_tot = hist + 256 * L.sort_blocks_cap;
   const int64_t nb_cap = (count_cap + kSortTile - 1) / kSortTile;
-  if (nb_cap > L.sort_blocks_cap) return cudaErrorInvalidValue;
+  if (nb_cap > L.sort_blocks_cap || nbits < 1 || lo_bit + nbits > 64) return cudaErrorInvalidValue;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nb_cap, kGrid));
+  // the fewest passes of at most 8 bits, with digits as narrow as they allow
+  // (fewer ballots per key); bits above the key's range read as zero digits
+  const int passes = sort_passes(nbits);
+  const int bits = std::max(4, (nbits + passes - 1) / passes);
   uint64_t* src = a;
   uint64_t* dst = b;
   for (int p = 0; p < passes; ++p) {
-    const int shift = lo_bit + 8 * p;
-    count_launch(), k_sort_upsweep<<<grid, kSortThreads, 0, s>>>(src, count_dev, count_cap, shift, hist, L.sort_blocks_cap);
-    count_launch(), k_sort_scan_rows<<<256, 1024, 0, s>>>(hist, count_dev, count_cap, L.sort_blocks_cap, digit_tot);
-    count_launch(), k_sort_downsweep<<<grid, kSortThreads, 0, s>>>(src, dst, count_dev, count_cap, shift, hist, digit_tot,
-                                                   L.sort_blocks_cap);
+    const int shift = lo_bit + bits * p;
+    if (shift + bits > 64) return cudaErrorInvalidValue;
+    switch (bits) {
+      case 4: sort_pass<4>(src, dst, count_dev, count_cap, shift, hist, digit_tot, L.sort_blocks_cap, grid, s); break;
+      case 5: sort_pass<5>(src, dst, count_dev, count_cap, shift, hist, digit_tot, L.sort_blocks_cap, grid, s); break;
+      case 6: sort_pass<6>(src, dst, count_dev, count_cap, shift, hist, digit_tot, L.sort_blocks_cap, grid, s); break;
+      case 7: sort_pass<7>(src, dst, count_dev, count_cap, shift, hist, digit_tot, L.sort_blocks_cap, grid, s); break;
+      default: sort_pass<8>(src, dst, count_dev, count_cap, shift, hist, digit_tot, L.sort_blocks_cap, grid, s); break;
+    }
     uint64_t* t = src;
     src = dst;
     dst = t;
@@ -659,7 +691,7 @@ cudaError_t launch_build_pairs(const Layout& L, void* ws, int tile_bits, cudaStr
   count_launch(), k_compact_depth<<<g, 256, 0, s>>>(ntiles, depth, scan, dk0, R);
   // 2. stable sort by depth (records in index order for equal depth)
   bool in_b = false;
-  e = sort_u64(ws, L, dk0, dk1, &st->visible, R, 32, 4, &in_b, s);
+  e = sort_u64(ws, L, dk0, dk1, &st->visible, R, 32, 32, &in_b, s);
   if (e != cudaSuccess) return e;
   const uint64_t* dsorted = in_b ? dk1 : dk0;
   if (dsorted != depth_sorted(ws, L)) return cudaErrorInvalidValue;
@@ -680,7 +712,7 @@ cudaError_t launch_build_pairs(const Layout& L, void* ws, int tile_bits, cudaStr
                                                  L.n, L.tile, ws_ptr<const uint64_t>(ws, L.kmask),
                                                  ws_ptr<uint32_t>(ws, L.offrec), p0, st);
   // 5. stable sort on the tile bits
-  e = sort_u64(ws, L, p0, p1, &st->pairs, L.Kc, kKeyTileShift, tile_passes(L), &in_b, s);
+  e = sort_u64(ws, L, p0, p1, &st->pairs, L.Kc, kKeyTileShift, L.tile_bits, &in_b, s);
   if (e != cudaSuccess) return e;
   const uint64_t* psorted = in_b ? p1 : p0;
   if (psorted != sorted_pairs(ws, L)) return cudaErrorInvalidValue;
