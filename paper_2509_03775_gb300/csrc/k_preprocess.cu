@@ -46,7 +46,7 @@ cudaError_t launch_sigma3(const SceneArgs& sc, const Layout& L, void* ws, cudaSt
 
 // One thread per (view, Gaussian) record, record = v * n + g.
 template <int NB>
-__global__ void __launch_bounds__(256) k_preprocess(const SceneArgs sc, const ViewInfo* __restrict__ views,
+__global__ void __launch_bounds__(256, 3) k_preprocess(const SceneArgs sc, const ViewInfo* __restrict__ views,
                                                     int n_views, int tile, const float* __restrict__ sig3,
                                                     float4* __restrict__ geo, float4* __restrict__ rgbm,
                                                     ushort4* __restrict__ rect, uint32_t* __restrict__ ntiles,
