@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(256) k_slot_sum(const uint32_t* __restrict__ n
 // the position, logit and Sigma gradients; culled records contribute zero
 // (and get a zero colour gradient).
 template <int NB>
-__global__ void __launch_bounds__(256, 3) k_chain_sum(const SceneArgs sc, int n_views, const ViewInfo* __restrict__ views,
+__global__ void __launch_bounds__(256, 4) k_chain_sum(const SceneArgs sc, int n_views, const ViewInfo* __restrict__ views,
                                                    const float* __restrict__ sig3, const float4* __restrict__ geo,
                                                    const float4* __restrict__ rgbm,
                                                    const uint32_t* __restrict__ ntiles, const float* __restrict__ rg,
@@ -373,6 +373,9 @@ __global__ void k_fill_chunks(const uint32_t* __restrict__ start, const uint32_t
   }
 }
 
+// Members whose gathers a lane issues together in the partial-sum kernels.
+constexpr int kGatherBatch = 4;
+
 // warp per chunk: SR terms are the 6 entries of dL/dSigma of each member
 __global__ void __launch_bounds__(256) k_sr_partials(const uint4* __restrict__ chunks, const uint64_t* n_chunks_dev,
                                                      const uint32_t* __restrict__ ids,
@@ -383,10 +386,26 @@ __global__ void __launch_bounds__(256) k_sr_partials(const uint4* __restrict__ c
   for (int64_t c = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); c < nch; c += warps) {
     const uint4 ch = chunks[c];
     float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-    for (uint32_t i = ch.y + lane; i < ch.z; i += 32) {
-      const float* d = dsigma + 6 * (size_t)ids[i];
+    // members lane, lane + 32, ... in order; four at a time with every load
+    // issued before the sums (the gathers overlap)
+    for (uint32_t i0 = ch.y + lane; i0 < ch.z; i0 += 32 * kGatherBatch) {
+      uint32_t g[kGatherBatch];
 #pragma unroll
-      for (int e = 0; e < 6; ++e) acc[e] += d[e];
+      for (int u = 0; u < kGatherBatch; ++u) {
+        const uint32_t i = i0 + 32u * u;
+        g[u] = i < ch.z ? ids[i] : 0xffffffffu;
+      }
+      float d[kGatherBatch][6];
+#pragma unroll
+      for (int u = 0; u < kGatherBatch; ++u)
+#pragma unroll
+        for (int e = 0; e < 6; ++e) d[u][e] = g[u] != 0xffffffffu ? dsigma[6 * (size_t)g[u] + e] : 0.0f;
+#pragma unroll
+      for (int u = 0; u < kGatherBatch; ++u)
+        if (g[u] != 0xffffffffu) {
+#pragma unroll
+          for (int e = 0; e < 6; ++e) acc[e] += d[u][e];
+        }
     }
 #pragma unroll
     for (int e = 0; e < 6; ++e) {
@@ -414,23 +433,50 @@ __global__ void __launch_bounds__(256) k_sh_partials(const uint4* __restrict__ c
     float acc[NB * 3];
 #pragma unroll
     for (int e = 0; e < NB * 3; ++e) acc[e] = 0.0f;
-    for (uint32_t i = ch.y + lane; i < ch.z; i += 32) {
-      const uint32_t g = ids[i];
-      const float p0 = pos[3 * (size_t)g], p1 = pos[3 * (size_t)g + 1], p2 = pos[3 * (size_t)g + 2];
-      for (int v = 0; v < n_views; ++v) {
-        const float* d = drgb + 3 * ((size_t)v * n + g);
-        const float d0 = d[0], d1 = d[1], d2 = d[2];
-        if (d0 == 0.0f && d1 == 0.0f && d2 == 0.0f) continue;
-        const ViewInfo& cam = views[v];
-        const float dx = p0 - cam.campos[0], dy = p1 - cam.campos[1], dz = p2 - cam.campos[2];
-        const float inv = 1.0f / sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-        float Y[kMaxBasis];
-        sh_basis_only<NB>(dx * inv, dy * inv, dz * inv, Y);
+    // members lane, lane + 32, ... in order, views in order; the index,
+    // position and first-view colour-gradient gathers of four members are
+    // issued together
+    for (uint32_t i0 = ch.y + lane; i0 < ch.z; i0 += 32 * kGatherBatch) {
+      uint32_t gg[kGatherBatch];
 #pragma unroll
-        for (int k = 0; k < NB; ++k) {
-          acc[3 * k] = fmaf(Y[k], d0, acc[3 * k]);
-          acc[3 * k + 1] = fmaf(Y[k], d1, acc[3 * k + 1]);
-          acc[3 * k + 2] = fmaf(Y[k], d2, acc[3 * k + 2]);
+      for (int u = 0; u < kGatherBatch; ++u) {
+        const uint32_t i = i0 + 32u * u;
+        gg[u] = i < ch.z ? ids[i] : 0xffffffffu;
+      }
+      float P[kGatherBatch][3], D[kGatherBatch][3];
+#pragma unroll
+      for (int u = 0; u < kGatherBatch; ++u) {
+        const bool ok = gg[u] != 0xffffffffu;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          P[u][a] = ok ? pos[3 * (size_t)gg[u] + a] : 0.0f;
+          D[u][a] = ok ? drgb[3 * (size_t)gg[u] + a] : 0.0f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kGatherBatch; ++u) {
+        if (gg[u] == 0xffffffffu) continue;
+        const uint32_t g = gg[u];
+        for (int v = 0; v < n_views; ++v) {
+          float d0 = D[u][0], d1 = D[u][1], d2 = D[u][2];
+          if (v > 0) {
+            const float* d = drgb + 3 * ((size_t)v * n + g);
+            d0 = d[0];
+            d1 = d[1];
+            d2 = d[2];
+          }
+          if (d0 == 0.0f && d1 == 0.0f && d2 == 0.0f) continue;
+          const ViewInfo& cam = views[v];
+          const float dx = P[u][0] - cam.campos[0], dy = P[u][1] - cam.campos[1], dz = P[u][2] - cam.campos[2];
+          const float inv = 1.0f / sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+          float Y[kMaxBasis];
+          sh_basis_only<NB>(dx * inv, dy * inv, dz * inv, Y);
+#pragma unroll
+          for (int k = 0; k < NB; ++k) {
+            acc[3 * k] = fmaf(Y[k], d0, acc[3 * k]);
+            acc[3 * k + 1] = fmaf(Y[k], d1, acc[3 * k + 1]);
+            acc[3 * k + 2] = fmaf(Y[k], d2, acc[3 * k + 2]);
+          }
         }
       }
     }
