@@ -410,12 +410,14 @@ __device__ __forceinline__ bool tile_decide(const TileRec& t, float pmax) {
 // rectangle).  A warp takes 32 consecutive records and lays their rectangle
 // tiles end to end (an exclusive prefix of the tile counts); its lanes then
 // test 32 consecutive tiles of that list at a time, whatever record they
-// belong to, so every lane has work until the warp's list ends.  Each
-// record's kept tiles of a 32-tile step are counted by the first lane of
-// its run (lanes holding the same record are found with one match); records
-// of at most 64 tiles also collect their kept-tile bits for the emit pass.
-// Writes the count per record and, in depth order, the input of the offset
-// scan.
+// belong to, so every lane has work until the warp's list ends.  The record
+// of each lane comes from one OR-reduction of the bits of the records that
+// start inside the 32-tile window (every visible record has at least one
+// tile, so starts are distinct): lane l belongs to the window's first record
+// plus the number of starts at or below l.  Each record's kept tiles of a
+// window are counted by the first lane of its run; records of at most 64
+// tiles also collect their kept-tile bits for the emit pass.  Writes the
+// count per record and, in depth order, the input of the offset scan.
 __global__ void __launch_bounds__(256) k_count_emit(const uint64_t* __restrict__ dkeys,
                                                     const float4* __restrict__ geo,
                                                     const ushort4* __restrict__ rect, int64_t R, int tile,
@@ -427,6 +429,7 @@ __global__ void __launch_bounds__(256) k_count_emit(const uint64_t* __restrict__
   __shared__ uint64_t sMask[8][32];
   const int64_t vis = min((int64_t)*visible_dev, R);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t upto = lane == 31 ? 0xffffffffu : (2u << lane) - 1u;  // bits 0..lane
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t base = warp * 32; base < vis; base += nwarps * 32) {
@@ -444,19 +447,20 @@ __global__ void __launch_bounds__(256) k_count_emit(const uint64_t* __restrict__
       const uint32_t up = __shfl_up_sync(0xffffffffu, incl, d);
       if (lane >= d) incl += up;
     }
-    sPre[wid][lane] = incl - nt;
+    const uint32_t my_start = incl - nt;
+    sPre[wid][lane] = my_start;
     sCnt[wid][lane] = 0;
     sMask[wid][lane] = 0ull;
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const bool has = i < vis;  // records past the end have no tiles and start nowhere
     __syncwarp();
+    int q0 = 0;  // the record holding list position c0 (warp-uniform)
     for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+      const uint32_t rel = my_start - c0;
+      const uint32_t starts = __reduce_or_sync(0xffffffffu, has && rel - 1u < 31u ? 1u << rel : 0u);
       const uint32_t p = c0 + lane;
       const bool valid = p < total;
-      // the record of list position p: the last one whose start is <= p
-      int q = 0;
-#pragma unroll
-      for (int stp = 16; stp > 0; stp >>= 1)
-        if (sPre[wid][q + stp] <= p) q += stp;
+      const int q = q0 + __popc(starts & upto);
       bool keep = false;
       int k = 0;
       if (valid) {
@@ -468,13 +472,19 @@ __global__ void __launch_bounds__(256) k_count_emit(const uint64_t* __restrict__
         keep = tile_decide(t, tile_pmax(t.a.x, t.a.y, t.a.z, t.a.w, t.b.x, t.b.z, t.b.w, x0 + xx, y0 + yy, tile));
       }
       const uint32_t m = __ballot_sync(0xffffffffu, keep);
-      const uint32_t peers = __match_any_sync(0xffffffffu, valid ? q : 32);
-      const bool head = valid && (peers & ((1u << lane) - 1u)) == 0u;
-      if (head) {
-        const uint32_t mine = (m & peers) >> lane;  // bit j: list position p + j
+      // runs of lanes with one record begin at lane 0 and at every start
+      const uint32_t heads = starts | 1u;
+      if (valid && ((heads >> lane) & 1u)) {
+        const uint32_t above = heads & ~upto;
+        const uint32_t run_end = above ? (above & (0u - above)) : 0u;  // lowest head above, 0 if none
+        const uint32_t run = (run_end ? run_end - 1u : 0xffffffffu) & ~((1u << lane) - 1u);
+        const uint32_t mine = (m & run) >> lane;  // bit j: list position p + j
         sCnt[wid][q] += (uint32_t)__popc(mine);
         if (k < 64) sMask[wid][q] |= (uint64_t)mine << k;
       }
+      // the next window's first record: the starts inside this window, plus
+      // one if a record starts exactly at the next window
+      q0 += __popc(starts) + (__any_sync(0xffffffffu, has && my_start == c0 + 32u) ? 1 : 0);
       __syncwarp();
     }
     if (i < vis) {
@@ -496,31 +506,15 @@ __global__ void k_capacity(DeviceState* st, int64_t cap) {
   if (!ok) set_status(st, CG_ERR_CAPACITY, 0);
 }
 
-// Position of the r-th (from 0) set bit of x (r < popc(x)).
-__device__ __forceinline__ int select_bit32(uint32_t x, int r) {
-  int pos = 0;
-#pragma unroll
-  for (int width = 16; width > 0; width >>= 1) {
-    const int c = __popc(x & ((1u << width) - 1u));
-    if (r >= c) {
-      r -= c;
-      x >>= width;
-      pos += width;
-    }
-  }
-  return pos;
-}
-
 // Pairs of one record in depth order: its kept tiles (tile_keep) in
 // row-major order of its rectangle, each as pair_key(global tile, rank among
 // the kept tiles, record) at offset + rank.  A warp takes 32 consecutive
-// records.  The pairs of its records of at most 64 rectangle tiles (whose
-// kept-tile bits the count pass left in kmask) are spread over the lanes:
-// lane l writes pair p = l, l + 32, ... of the warp's list, finding its
-// record by a search over the warp's prefix of pair counts and its tile as
-// the rank-th set bit of the record's mask, so consecutive lanes write
-// consecutive pairs.  Larger records are then written by the whole warp,
-// one at a time, recomputing the tile test.
+// records and walks them one after another.  For a record of at most 64
+// rectangle tiles (whose kept-tile bits the count pass left in kmask), lane
+// l looks at tiles l and 32 + l: if kept, its rank is the number of kept
+// bits below it, so the record's pairs are written by consecutive lanes to
+// consecutive slots.  Larger records are written by the whole warp, 32 tiles
+// at a time, recomputing the tile test.
 __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__ dkeys,
                                                     const uint32_t* __restrict__ off_sorted,
                                                     const float4* __restrict__ geo,
@@ -529,13 +523,12 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__
                                                     const uint64_t* __restrict__ kmask,
                                                     uint32_t* __restrict__ offrec, uint64_t* __restrict__ pairs,
                                                     const DeviceState* state) {
-  __shared__ TileRec st[8][32];
-  __shared__ uint2 sro[8][32];       // record, offset (large records)
+  __shared__ TileRec st[8][32];      // tile test data (large records)
   __shared__ uint64_t sMask[8][32];  // kept-tile bits (small records)
-  __shared__ uint4 sInfo[8][32];     // record, offset, x0 | y0 << 16, rectangle width
+  __shared__ uint4 sInfo[8][32];     // record, offset, x0 | y0 << 16, rectangle width | height << 16
   __shared__ int64_t sTB[8][32];     // first global tile of the record's view
   __shared__ int sTX[8][32];         // tiles per row of that view
-  __shared__ uint32_t sP[8][32];     // exclusive prefix of the small records' pair counts
+  __shared__ float sRW[8][32];       // 1 / rectangle width
   const int64_t vis = (int64_t)state->visible;
   const bool ok = state->pairs_ok != 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -544,82 +537,66 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t base = warp * 32; base < vis; base += nwarps * 32) {
     const int64_t i = base + lane;
-    bool big = false;
-    uint32_t c = 0;
     if (i < vis) {
       const uint32_t rec = (uint32_t)dkeys[i];
       const uint32_t off = off_sorted[i];
       offrec[rec] = off;
       const ushort4 r = rect[rec];
-      const int w = (int)r.z - (int)r.x, total = w * ((int)r.w - (int)r.y);
-      big = total > 64;
-      if (big) {
+      const int w = (int)r.z - (int)r.x, h = (int)r.w - (int)r.y;
+      if (w * h > 64) {
         stage_record(st[wid][lane], geo, rect, rec);
-        sro[wid][lane] = make_uint2(rec, off);
       } else {
-        const uint64_t m = kmask[rec];
-        c = (uint32_t)__popcll((long long)m);
-        sMask[wid][lane] = m;
-        sInfo[wid][lane] = make_uint4(rec, off, (uint32_t)r.x | ((uint32_t)r.y << 16), (uint32_t)w);
-        const ViewInfo& cam = views[rec / (uint32_t)n];
-        sTB[wid][lane] = cam.tile_base;
-        sTX[wid][lane] = cam.tiles_x;
+        sMask[wid][lane] = kmask[rec];
+        sRW[wid][lane] = 1.0f / (float)max(1, w);
       }
+      sInfo[wid][lane] = make_uint4(rec, off, (uint32_t)r.x | ((uint32_t)r.y << 16), (uint32_t)w | ((uint32_t)h << 16));
+      const ViewInfo& cam = views[rec / (uint32_t)n];
+      sTB[wid][lane] = cam.tile_base;
+      sTX[wid][lane] = cam.tiles_x;
     }
-    // exclusive prefix of the small records' pair counts over the lanes
-    uint32_t incl = c;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t up = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += up;
-    }
-    sP[wid][lane] = incl - c;
-    const uint32_t tw = __shfl_sync(0xffffffffu, incl, 31);
-    uint32_t bigs = __ballot_sync(0xffffffffu, big);
     __syncwarp();
+    const int nrec = (int)min((int64_t)32, vis - base);
     if (ok) {
-      for (uint32_t p = lane; p < tw; p += 32) {
-        int q = 0;
-#pragma unroll
-        for (int stp = 16; stp > 0; stp >>= 1)
-          if (sP[wid][q + stp] <= p) q += stp;
-        const uint32_t rank = p - sP[wid][q];
-        const uint64_t m = sMask[wid][q];
-        const uint32_t lo = (uint32_t)m, cl = (uint32_t)__popc(lo);
-        const int k = rank < cl ? select_bit32(lo, (int)rank) : 32 + select_bit32((uint32_t)(m >> 32), (int)(rank - cl));
+      for (int q = 0; q < nrec; ++q) {
         const uint4 inf = sInfo[wid][q];
-        const int w = (int)inf.w;
-        const int yy = (int)(((float)k + 0.5f) * (1.0f / (float)w)), xx = k - yy * w;
         const int x0 = (int)(inf.z & 0xffffu), y0 = (int)(inf.z >> 16);
-        pairs[inf.y + rank] =
-            pair_key((uint64_t)(sTB[wid][q] + (int64_t)(y0 + yy) * sTX[wid][q] + (x0 + xx)), rank, inf.x);
-      }
-      while (bigs != 0u) {
-        const int q = __ffs(bigs) - 1;
-        bigs &= bigs - 1u;
-        const TileRec& t = st[wid][q];
-        const uint2 ro = sro[wid][q];
-        const int x0 = (int)(t.r01 & 0xffffu), y0 = (int)(t.r01 >> 16);
-        const int w = (int)(t.r23 & 0xffffu) - x0, total = w * ((int)(t.r23 >> 16) - y0);
-        const ViewInfo& cam = views[ro.x / (uint32_t)n];
-        const int64_t tb = cam.tile_base;
-        const int tx = cam.tiles_x;
-        uint32_t rank0 = 0;
-        for (int t0 = 0; t0 < total; t0 += 32) {
-          const int k = t0 + lane;
-          bool keep = false;
-          int xx = 0, yy = 0;
-          if (k < total) {
-            yy = (int)(((float)k + 0.5f) * t.rw);
-            xx = k - yy * w;
-            keep = tile_decide(t, tile_pmax(t.a.x, t.a.y, t.a.z, t.a.w, t.b.x, t.b.z, t.b.w, x0 + xx, y0 + yy, tile));
+        const int w = (int)(inf.w & 0xffffu), total = w * (int)(inf.w >> 16);
+        const int64_t tb = sTB[wid][q];
+        const int tx = sTX[wid][q];
+        if (total <= 64) {
+          const uint64_t m = sMask[wid][q];
+          const float rw = sRW[wid][q];
+          const uint32_t lo = (uint32_t)m, hi = (uint32_t)(m >> 32);
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            if (half == 1 && total <= 32) break;
+            const uint32_t bits = half == 0 ? lo : hi;
+            if ((bits >> lane) & 1u) {
+              const int k = 32 * half + lane;
+              const uint32_t rank = (half == 0 ? 0u : (uint32_t)__popc(lo)) + (uint32_t)__popc(bits & lt_mask);
+              const int yy = (int)(((float)k + 0.5f) * rw), xx = k - yy * w;
+              pairs[inf.y + rank] = pair_key((uint64_t)(tb + (int64_t)(y0 + yy) * tx + (x0 + xx)), rank, inf.x);
+            }
           }
-          const uint32_t mk = __ballot_sync(0xffffffffu, keep);
-          if (keep) {
-            const uint32_t rank = rank0 + __popc(mk & lt_mask);
-            pairs[ro.y + rank] = pair_key((uint64_t)(tb + (int64_t)(y0 + yy) * tx + (x0 + xx)), rank, ro.x);
+        } else {
+          const TileRec& t = st[wid][q];
+          uint32_t rank0 = 0;
+          for (int t0 = 0; t0 < total; t0 += 32) {
+            const int k = t0 + lane;
+            bool keep = false;
+            int xx = 0, yy = 0;
+            if (k < total) {
+              yy = (int)(((float)k + 0.5f) * t.rw);
+              xx = k - yy * w;
+              keep = tile_decide(t, tile_pmax(t.a.x, t.a.y, t.a.z, t.a.w, t.b.x, t.b.z, t.b.w, x0 + xx, y0 + yy, tile));
+            }
+            const uint32_t mk = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+              const uint32_t rank = rank0 + __popc(mk & lt_mask);
+              pairs[inf.y + rank] = pair_key((uint64_t)(tb + (int64_t)(y0 + yy) * tx + (x0 + xx)), rank, inf.x);
+            }
+            rank0 += __popc(mk);
           }
-          rank0 += __popc(mk);
         }
       }
     }
