@@ -614,7 +614,22 @@ __global__ void __launch_bounds__(256) k_csr_check(const uint16_t* __restrict__ 
   bool diff = cs->magic != kCsrMagic || cs->idx_ptr != (uint64_t)(uintptr_t)idx || cs->k != (uint32_t)k ||
               cs->n != (uint32_t)n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += stride) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t done = 0;
+  if ((((uintptr_t)idx | (uintptr_t)copy) & 15u) == 0) {
+    // eight indices per 16-byte load
+    const uint4* iv = reinterpret_cast<const uint4*>(idx);
+    uint4* cv = reinterpret_cast<uint4*>(copy);
+    done = n / 8 * 8;
+    for (int64_t g = tid; g < n / 8; g += stride) {
+      const uint4 v = iv[g], c = cv[g];
+      if (v.x != c.x || v.y != c.y || v.z != c.z || v.w != c.w) {
+        diff = true;
+        cv[g] = v;
+      }
+    }
+  }
+  for (int64_t g = done + tid; g < n; g += stride) {
     const uint16_t v = idx[g];
     if (copy[g] != v) {
       diff = true;
