@@ -148,6 +148,7 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
   L->nemit = take(sizeof(uint32_t) * R_cap);
   L->kmask = take(sizeof(uint64_t) * R_cap);
   L->scan = take(sizeof(uint32_t) * std::max(R_cap, kmax));
+  L->gsum = take(sizeof(uint32_t) * (R_cap / 32 + 1));  // per group of 32 records
   L->dkeys0 = take(sizeof(uint64_t) * R_cap);
   L->dkeys1 = take(sizeof(uint64_t) * R_cap);
   L->pairs0 = take(sizeof(uint64_t) * Kc);

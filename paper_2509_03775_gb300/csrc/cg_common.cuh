@@ -266,7 +266,7 @@ struct Layout {
   uint64_t total;
   uint64_t hdr, views, sigma3, geo, rgbm, rect, ntiles, depth, offrec, scan, dkeys0, dkeys1, pairs0, pairs1,
       ranges, tfinal, ncontrib, pairgrad, pairgrad1, recgrad, nemit, kmask, dsigma, drgb, csr_keys0, csr_keys1, csr_off_sr, csr_off_sh, csr_ids_sr, csr_ids_sh, chunks, chunks_sh,
-      csr_idx_sr, csr_idx_sh, csr_state, csr_tmp,
+      csr_idx_sr, csr_idx_sh, csr_state, csr_tmp, gsum,
       partials, hist, blocksums, l1;
   // sizes
   int64_t n, R, T, P, Kc;
@@ -299,7 +299,7 @@ struct DeviceState {
   uint64_t scan_total;  // scratch total written by the scan kernels
   uint32_t pairs_ok;    // 1 if pairs <= capacity
   uint32_t pad;
-  uint64_t red_a, red_b;  // counts used by the codebook reduction
+  uint64_t red_a, red_b;  // scratch counts (scan lengths and totals of the pair list and codebook builds)
 };
 
 struct WsHeader {

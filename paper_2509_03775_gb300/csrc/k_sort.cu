@@ -357,19 +357,40 @@ cudaError_t scan_u32(void* ws, const Layout& L, const uint32_t* in, uint32_t* ou
 // pair list
 // ---------------------------------------------------------------------------
 
-__global__ void k_visible_flags(const uint32_t* __restrict__ ntiles, uint32_t* __restrict__ flags, int64_t R,
-                                uint64_t* count_slot) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R; i += stride)
-    flags[i] = ntiles[i] > 0 ? 1u : 0u;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *count_slot = (uint64_t)R;
+// Records are grouped by 32 (one warp); the scans that place visible
+// records and pairs run over the group sums, and each warp adds its lanes'
+// prefix itself.
+
+// Visible records of each group of 32 consecutive records; *ngroups <- the
+// group count (the length of the following scan).
+__global__ void k_visible_groups(const uint32_t* __restrict__ ntiles, uint32_t* __restrict__ gsum, int64_t R,
+                                 uint64_t* ngroups) {
+  const int lane = threadIdx.x & 31;
+  const int64_t G = (R + 31) / 32;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = warp; g < G; g += nwarps) {
+    const int64_t i = 32 * g + lane;
+    const uint32_t m = __ballot_sync(0xffffffffu, i < R && ntiles[i] > 0);
+    if (lane == 0) gsum[g] = (uint32_t)__popc(m);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *ngroups = (uint64_t)G;
 }
 
+// Visible records in index order, keyed (FP32 depth bits << 32 | record);
+// gbase = exclusive scan of k_visible_groups' sums.
 __global__ void k_compact_depth(const uint32_t* __restrict__ ntiles, const uint32_t* __restrict__ depth,
-                                const uint32_t* __restrict__ pos, uint64_t* __restrict__ dkeys, int64_t R) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < R; i += stride)
-    if (ntiles[i] > 0) dkeys[pos[i]] = ((uint64_t)depth[i] << 32) | (uint64_t)i;
+                                const uint32_t* __restrict__ gbase, uint64_t* __restrict__ dkeys, int64_t R) {
+  const int lane = threadIdx.x & 31;
+  const int64_t G = (R + 31) / 32;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = warp; g < G; g += nwarps) {
+    const int64_t i = 32 * g + lane;
+    const bool v = i < R && ntiles[i] > 0;
+    const uint32_t m = __ballot_sync(0xffffffffu, v);
+    if (v) dkeys[gbase[g] + (uint32_t)__popc(m & ((1u << lane) - 1u))] = ((uint64_t)depth[i] << 32) | (uint64_t)i;
+  }
 }
 
 // Per-record data of the tile test, staged in shared memory for the warp
@@ -417,12 +438,14 @@ __device__ __forceinline__ bool tile_decide(const TileRec& t, float pmax) {
 // plus the number of starts at or below l.  Each record's kept tiles of a
 // window are counted by the first lane of its run; records of at most 64
 // tiles also collect their kept-tile bits for the emit pass.  Writes the
-// count per record and, in depth order, the input of the offset scan.
+// count per record, in depth order, and the sum of each group of 32 records
+// (the input of the offset scan).
 __global__ void __launch_bounds__(256) k_count_emit(const uint64_t* __restrict__ dkeys,
                                                     const float4* __restrict__ geo,
                                                     const ushort4* __restrict__ rect, int64_t R, int tile,
                                                     uint32_t* __restrict__ nemit, uint32_t* __restrict__ counts,
-                                                    uint64_t* __restrict__ kmask, const uint64_t* visible_dev) {
+                                                    uint64_t* __restrict__ kmask, const uint64_t* visible_dev,
+                                                    uint32_t* __restrict__ gsum, uint64_t* ngroups) {
   __shared__ TileRec st[8][32];
   __shared__ uint32_t sPre[8][32];
   __shared__ uint32_t sCnt[8][32];
@@ -487,14 +510,18 @@ __global__ void __launch_bounds__(256) k_count_emit(const uint64_t* __restrict__
       q0 += __popc(starts) + (__any_sync(0xffffffffu, has && my_start == c0 + 32u) ? 1 : 0);
       __syncwarp();
     }
+    uint32_t c = 0;
     if (i < vis) {
-      const uint32_t c = sCnt[wid][lane];
+      c = sCnt[wid][lane];
       nemit[rec] = c;
       counts[i] = c;
       if (nt <= 64u) kmask[rec] = sMask[wid][lane];  // the emit pass reuses the decisions
     }
+    const uint32_t gs = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0) gsum[base >> 5] = gs;
     __syncwarp();
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *ngroups = (uint64_t)((vis + 31) / 32);
 }
 
 __global__ void k_capacity(DeviceState* st, int64_t cap) {
@@ -508,7 +535,8 @@ __global__ void k_capacity(DeviceState* st, int64_t cap) {
 
 // Pairs of one record in depth order: its kept tiles (tile_keep) in
 // row-major order of its rectangle, each as pair_key(global tile, rank among
-// the kept tiles, record) at offset + rank.  A warp takes 32 consecutive
+// the kept tiles, record) at offset + rank (offset = the exclusive prefix of
+// the kept counts in depth order).  A warp takes 32 consecutive
 // records and walks them one after another.  For a record of at most 64
 // rectangle tiles (whose kept-tile bits the count pass left in kmask), lane
 // l looks at tiles l and 32 + l: if kept, its rank is the number of kept
@@ -516,7 +544,8 @@ __global__ void k_capacity(DeviceState* st, int64_t cap) {
 // consecutive slots.  Larger records are written by the whole warp, 32 tiles
 // at a time, recomputing the tile test.
 __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__ dkeys,
-                                                    const uint32_t* __restrict__ off_sorted,
+                                                    const uint32_t* __restrict__ counts,
+                                                    const uint32_t* __restrict__ gbase,
                                                     const float4* __restrict__ geo,
                                                     const ushort4* __restrict__ rect,
                                                     const ViewInfo* __restrict__ views, int64_t n, int tile,
@@ -537,9 +566,18 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t base = warp * 32; base < vis; base += nwarps * 32) {
     const int64_t i = base + lane;
+    // the record's first slot: its group's offset plus the counts of the
+    // lanes before it
+    const uint32_t c = i < vis ? counts[i] : 0u;
+    uint32_t incl = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t up = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += up;
+    }
     if (i < vis) {
       const uint32_t rec = (uint32_t)dkeys[i];
-      const uint32_t off = off_sorted[i];
+      const uint32_t off = gbase[base >> 5] + incl - c;
       offrec[rec] = off;
       const ushort4 r = rect[rec];
       const int w = (int)r.z - (int)r.x, h = (int)r.w - (int)r.y;
@@ -661,30 +699,32 @@ cudaError_t launch_build_pairs(const Layout& L, void* ws, int tile_bits, cudaStr
   uint64_t* dk1 = ws_ptr<uint64_t>(ws, L.dkeys1);
   const int64_t R = L.R;
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>((R + 255) / 256, kGrid));
+  uint32_t* gsum = ws_ptr<uint32_t>(ws, L.gsum);
+  const int64_t G = (R + 31) / 32;
   // 1. compact visible records, keyed by FP32 depth bits (record index low)
-  count_launch(), k_visible_flags<<<g, 256, 0, s>>>(ntiles, scan, R, &st->scan_total);
-  cudaError_t e = scan_u32(ws, L, scan, scan, &st->scan_total, R, &st->visible, s);
+  count_launch(), k_visible_groups<<<g, 256, 0, s>>>(ntiles, gsum, R, &st->red_a);
+  cudaError_t e = scan_u32(ws, L, gsum, gsum, &st->red_a, G, &st->visible, s);
   if (e != cudaSuccess) return e;
-  count_launch(), k_compact_depth<<<g, 256, 0, s>>>(ntiles, depth, scan, dk0, R);
+  count_launch(), k_compact_depth<<<g, 256, 0, s>>>(ntiles, depth, gsum, dk0, R);
   // 2. stable sort by depth (records in index order for equal depth)
   bool in_b = false;
   e = sort_u64(ws, L, dk0, dk1, &st->visible, R, 32, 32, &in_b, s);
   if (e != cudaSuccess) return e;
   const uint64_t* dsorted = in_b ? dk1 : dk0;
   if (dsorted != depth_sorted(ws, L)) return cudaErrorInvalidValue;
-  // 3. kept tiles per record, pair offsets in depth order, total pair count
-  //    and capacity check
+  // 3. kept tiles per record, pair offsets of the groups of 32 records in
+  //    depth order, total pair count and capacity check
   count_launch(), k_count_emit<<<g, 256, 0, s>>>(dsorted, ws_ptr<const float4>(ws, L.geo),
                                                  ws_ptr<const ushort4>(ws, L.rect), R, L.tile,
                                                  ws_ptr<uint32_t>(ws, L.nemit), scan, ws_ptr<uint64_t>(ws, L.kmask),
-                                                 &st->visible);
-  e = scan_u32(ws, L, scan, scan, &st->visible, R, &st->scan_total, s);
+                                                 &st->visible, gsum, &st->red_b);
+  e = scan_u32(ws, L, gsum, gsum, &st->red_b, G, &st->scan_total, s);
   if (e != cudaSuccess) return e;
   count_launch(), k_capacity<<<1, 1, 0, s>>>(st, L.Kc);
   // 4. emit pairs in depth order
   uint64_t* p0 = ws_ptr<uint64_t>(ws, L.pairs0);
   uint64_t* p1 = ws_ptr<uint64_t>(ws, L.pairs1);
-  count_launch(), k_emit_pairs<<<g, 256, 0, s>>>(dsorted, scan, ws_ptr<const float4>(ws, L.geo),
+  count_launch(), k_emit_pairs<<<g, 256, 0, s>>>(dsorted, scan, gsum, ws_ptr<const float4>(ws, L.geo),
                                                  ws_ptr<const ushort4>(ws, L.rect), ws_ptr<ViewInfo>(ws, L.views),
                                                  L.n, L.tile, ws_ptr<const uint64_t>(ws, L.kmask),
                                                  ws_ptr<uint32_t>(ws, L.offrec), p0, st);
