@@ -128,7 +128,7 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
   L->sort_blocks_cap = (std::max(Kc, R_cap) + 4095) / 4096 + 1;  // 4096 keys per sort block
   const int64_t kmax = std::max(s->k_sr, s->k_sh) + 1;
   L->scan_blocks_cap = (std::max(R_cap, kmax) + 4095) / 4096 + 1;
-  L->chunks_cap = (n_cap + 1023) / 1024 + kmax;  // chunks of 1024 members
+  L->chunks_cap = (n_cap + kCodebookChunk - 1) / kCodebookChunk + kmax;  // chunks of the codebook reduction
   uint64_t off = 0;
   auto take = [&](uint64_t bytes) {
     const uint64_t at = off;

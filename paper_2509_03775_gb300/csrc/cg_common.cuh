@@ -425,6 +425,9 @@ cudaError_t launch_recon_loss(const float* x, const float* y, const cg_camera* c
 
 // The depth-sorted visible records (4 sort passes end in dkeys0).
 inline uint64_t* depth_sorted(void* ws, const Layout& L) { return ws_ptr<uint64_t>(ws, L.dkeys0); }
+// Members per chunk of the codebook reduction (one warp sums a chunk).
+constexpr int kCodebookChunk = 512;
+
 // Passes of a radix sort on nbits bits (digits of at most 8 bits).
 inline int sort_passes(int nbits) { return (nbits + 7) / 8; }
 // The tile-sorted pairs (an odd number of passes ends in pairs1).

@@ -9,7 +9,7 @@
 
 namespace cg {
 
-constexpr int kChunk = 1024;  // members per chunk of the codebook reduction
+constexpr int kChunk = kCodebookChunk;  // members per chunk of the codebook reduction
 
 // Y_k and dY_k/d(x, y, z) (x, y, z treated as independent), FP32.
 template <int NB>
@@ -590,7 +590,36 @@ __global__ void __launch_bounds__(256) k_sh_rows(const uint32_t* __restrict__ st
   float acc[W];
 #pragma unroll
   for (int e = 0; e < W; ++e) acc[e] = 0.0f;
-  for (uint32_t c = lane; c < nch; c += 32) {
+  uint32_t c = lane;
+  if constexpr (W % 4 == 0) {
+    // two chunks per step, 16-byte loads (each chunk's W floats are 16-byte
+    // aligned: the partials start aligned and W * 4 is a multiple of 16)
+    for (; c + 32 < nch; c += 64) {
+      const float4* p0 = reinterpret_cast<const float4*>(part + (size_t)W * (cb + c));
+      const float4* p1 = reinterpret_cast<const float4*>(part + (size_t)W * (cb + c + 32));
+      float4 v0[W / 4], v1[W / 4];
+#pragma unroll
+      for (int q = 0; q < W / 4; ++q) {
+        v0[q] = p0[q];
+        v1[q] = p1[q];
+      }
+#pragma unroll
+      for (int q = 0; q < W / 4; ++q) {
+        acc[4 * q] += v0[q].x;
+        acc[4 * q + 1] += v0[q].y;
+        acc[4 * q + 2] += v0[q].z;
+        acc[4 * q + 3] += v0[q].w;
+      }
+#pragma unroll
+      for (int q = 0; q < W / 4; ++q) {
+        acc[4 * q] += v1[q].x;
+        acc[4 * q + 1] += v1[q].y;
+        acc[4 * q + 2] += v1[q].z;
+        acc[4 * q + 3] += v1[q].w;
+      }
+    }
+  }
+  for (; c < nch; c += 32) {
     const float* p = part + (size_t)W * (cb + c);
 #pragma unroll
     for (int e = 0; e < W; ++e) acc[e] += p[e];
