@@ -40,20 +40,21 @@ FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
 
 # Algorithmic FP32 operations per (pixel, listed Gaussian) evaluation of the
-# blend kernels (an FMA counts 2, an exponential 1): the quadratic form of
-# Eq. 1 (10), exp (1), alpha and the Eq. 3 update with three colour FMAs (10)
-# in the forward; the same recomputation with alpha (12) plus the derivatives
-# of Eq. 3 and of the quadratic form (56) in the backward.
-FLOPS_PER_EVAL = {"blend_fwd": 21, "blend_bwd": 68}
+# blend kernels (an FMA counts 2, an exponential or reciprocal 1): the
+# quadratic form of Eq. 1 (10), exp (1), alpha and the Eq. 3 update with three
+# colour FMAs (10) in the forward; the same recomputation with alpha (12), the
+# derivatives of Eq. 3 with the transmittance undone by one reciprocal (30)
+# and the five moments of dL/dpower plus the opacity term (13) in the
+# backward (the mean and conic gradients are linear in the moments and are
+# formed once per pair, not per pixel).
+FLOPS_PER_EVAL = {"blend_fwd": 21, "blend_bwd": 55}
 
-# DRAM bytes per launch measured by ncu for a kernel, keyed by the SHA-256 of
-# the kernel's source file at capture time (summaries under profiles/).  A
-# changed source reports null.
-# DRAM bytes (read + write) per launch from one ncu capture of the kernel
-# (profiles/), valid while its source file hashes to `src`
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel on
+# the named workload (summaries under profiles/), valid while the kernel's
+# source file hashes (SHA-256, first 16 hex digits) to `src`; null otherwise.
 NCU_TRAFFIC = {
-    "blend_bwd": {"bytes": 363697920 + 904256256, "src": "f24a2dcb808d376f", "workload": "truck"},
-    "blend_fwd": {"bytes": 26072832 + 996096, "src": "f24a2dcb808d376f", "workload": "truck"},
+    "blend_bwd": {"bytes": 366160384 + 907180288, "src": "0cb74b4455c2c0ae", "workload": "truck"},
+    "blend_fwd": {"bytes": 26038784 + 976640, "src": "0cb74b4455c2c0ae", "workload": "truck"},
 }
 
 
