@@ -254,6 +254,19 @@ struct ViewInfo {
   int64_t pix_base;   // first pixel of the view (images hold 3 * pix_base floats before it)
 };
 
+// Copies the first n_views entries of the view table into shared memory
+// (every thread of the block takes part; ends with a barrier), so per-record
+// kernels read camera fields with broadcast shared loads instead of one
+// global load per field.
+__device__ __forceinline__ void stage_views(ViewInfo* dst, const ViewInfo* src, int n_views) {
+  static_assert(sizeof(ViewInfo) % 4 == 0, "view table copied as words");
+  const int words = n_views * (int)(sizeof(ViewInfo) / 4);
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = s[i];
+  __syncthreads();
+}
+
 struct ViewTable {
   int n_views;
   int tile;

@@ -114,8 +114,9 @@ __device__ __forceinline__ void record_chain(const SceneArgs& sc, const ViewInfo
     T[j] = fmaf(J00, W[j], J02 * W[8 + j]);
     T[3 + j] = fmaf(J11, W[4 + j], J12 * W[8 + j]);
   }
-  const float* sgp = sig3 + (size_t)isr * 6;
-  const float S[9] = {sgp[0], sgp[1], sgp[2], sgp[1], sgp[3], sgp[4], sgp[2], sgp[4], sgp[5]};
+  const float2* sgp = reinterpret_cast<const float2*>(sig3 + (size_t)isr * 6);  // 24-byte rows: 8-byte loads
+  const float2 s01 = sgp[0], s23 = sgp[1], s45 = sgp[2];
+  const float S[9] = {s01.x, s01.y, s23.x, s01.y, s23.y, s45.x, s23.x, s45.x, s45.y};
   float ST0[3], ST1[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
@@ -246,6 +247,8 @@ __global__ void __launch_bounds__(256, 4) k_chain_sum(const SceneArgs sc, int n_
                                                    const DeviceState* st, float* __restrict__ d_pos,
                                                    float* __restrict__ d_logit, float* __restrict__ dsigma,
                                                    float* __restrict__ drgb) {
+  __shared__ ViewInfo sviews[CG_MAX_VIEWS];
+  stage_views(sviews, views, n_views);
   const bool ok = st->pairs_ok != 0;
   const int64_t n = sc.n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -255,10 +258,16 @@ __global__ void __launch_bounds__(256, 4) k_chain_sum(const SceneArgs sc, int n_
       const int64_t rec = (int64_t)v * n + g;
       if (ok && ntiles[rec] > 0) {
         float gs[9], out[10];
-        const float* r = rg + 10 * (size_t)rec;
+        // the record's nine sums (40-byte records: 8-byte loads)
+        const float2* r2 = reinterpret_cast<const float2*>(rg + 10 * (size_t)rec);
 #pragma unroll
-        for (int e = 0; e < 9; ++e) gs[e] = r[e];
-        record_chain<NB>(sc, views, sig3, geo, rgbm, (uint32_t)rec, gs, out, drgb);
+        for (int e = 0; e < 4; ++e) {
+          const float2 u = r2[e];
+          gs[2 * e] = u.x;
+          gs[2 * e + 1] = u.y;
+        }
+        gs[8] = rg[10 * (size_t)rec + 8];
+        record_chain<NB>(sc, sviews, sig3, geo, rgbm, (uint32_t)rec, gs, out, drgb);
 #pragma unroll
         for (int e = 0; e < 10; ++e) acc[e] += out[e];
       } else {

@@ -51,12 +51,14 @@ __global__ void __launch_bounds__(256, 3) k_preprocess(const SceneArgs sc, const
                                                     float4* __restrict__ geo, float4* __restrict__ rgbm,
                                                     ushort4* __restrict__ rect, uint32_t* __restrict__ ntiles,
                                                     uint32_t* __restrict__ depth, DeviceState* st) {
+  __shared__ ViewInfo sviews[CG_MAX_VIEWS];
+  stage_views(sviews, views, n_views);
   const int64_t R = (int64_t)sc.n * n_views;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t rec = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; rec < R; rec += stride) {
     const int v = (int)(rec / sc.n);
     const int64_t g = rec - (int64_t)v * sc.n;
-    const ViewInfo& cam = views[v];
+    const ViewInfo& cam = sviews[v];
     ntiles[rec] = 0u;
     rect[rec] = make_ushort4(0, 0, 0, 0);
     depth[rec] = 0xffffffffu;
@@ -81,8 +83,9 @@ __global__ void __launch_bounds__(256, 3) k_preprocess(const SceneArgs sc, const
       T[j] = fmaf(J00, W[j], J02 * W[8 + j]);
       T[3 + j] = fmaf(J11, W[4 + j], J12 * W[8 + j]);
     }
-    const float* sg = sig3 + (size_t)isr * 6;
-    const float S[9] = {sg[0], sg[1], sg[2], sg[1], sg[3], sg[4], sg[2], sg[4], sg[5]};
+    const float2* sg = reinterpret_cast<const float2*>(sig3 + (size_t)isr * 6);  // 24-byte rows: 8-byte loads
+    const float2 s01 = sg[0], s23 = sg[1], s45 = sg[2];
+    const float S[9] = {s01.x, s01.y, s23.x, s01.y, s23.y, s45.x, s23.x, s45.x, s45.y};
     float U[6];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
