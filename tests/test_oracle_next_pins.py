@@ -5,6 +5,8 @@ generator's published known-answer vectors, FP64 library functions, the
 distribution the draws must follow, the stationary law of Langevin dynamics,
 closed forms, a library convolution, finite differences, and structural
 identities of the split and merge transitions."""
+import json
+import os
 import types
 
 import numpy as np
@@ -200,6 +202,75 @@ def test_split_acceptance_rate_matches_min_one_exp():
     el = sp["eligible"]
     p = a[el].mean()
     assert abs(sp["accepted"][el].mean() - p) < 5 * np.sqrt(p * (1 - p) / el.sum())
+
+
+def _paper():
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_hyperparameters.json")) as f:
+        return json.load(f)
+
+
+def test_paper_hyperparameters_fixture():
+    """The printed values (Sec. 5.1, Sec. 4.4): a probability mixture and the
+    split / merge widths with eps_merge < eps_split, the regime in which the
+    split kernel q_sm grows with |u| (kc < 0)."""
+    hp = _paper()
+    assert abs(hp["p_update"] + hp["p_split"] + hp["p_merge"] - 1.0) < 1e-12
+    assert hp["eps_merge"] < hp["eps_split"]
+    _, kc, km = mcmc._coefs(hp["eps_split"], hp["eps_merge"])
+    assert float(kc) == pytest.approx(0.5 * (1 / 0.1 ** 2 - 1 / 0.05 ** 2), rel=1e-6)   # -150
+    assert float(km) == pytest.approx(0.5 / 0.05 ** 2, rel=1e-6)                       # 200
+
+
+def test_split_acceptance_closed_form_at_paper_hyperparameters():
+    """With the paper's lambda_SR, eps_split and eps_merge, e^-lambda / q_sm(u)
+    = exp(-lambda + kc |u|^2) < 1 for every u (kc < 0), and |u|^2 =
+    eps_split^2 chi^2_D, so an eligible proposal is accepted with probability
+    e^-lambda E[exp(kc eps_split^2 chi^2_D)] = e^-lambda (1 - 2 kc eps_split^2)^(-D/2)
+    (the chi-square moment generating function): e^-3 4^-3.5 = e^-3 / 128 for
+    the 7 moved values of an SR row.  The oracle's accepted count must match
+    that binomial mean."""
+    hp = _paper()
+    rng = np.random.default_rng(11)
+    k, n = 32, 600_000
+    rows, parent, g2x = _codebook(k, k + n, 8, n, rng, zipf=False)
+    sp = mcmc.split(rows, parent, g2x, k, k + n, 0, 3, lam=hp["lambda_sr"], eps_split=hp["eps_split"],
+                    eps_merge=hp["eps_merge"], step=5, seed=13)
+    es, em = hp["eps_split"], hp["eps_merge"]
+    kc = 0.5 * (1 / es ** 2 - 1 / em ** 2)
+    p = np.exp(-hp["lambda_sr"]) * (1 - 2 * kc * es ** 2) ** (-7 / 2)
+    assert p == pytest.approx(np.exp(-3.0) / 128, rel=1e-12)
+    el = int(sp["eligible"].sum())
+    assert el > n - 2 * k
+    got = int(sp["accepted"].sum())
+    assert abs(got - el * p) < 5 * np.sqrt(el * p * (1 - p)), (got, el * p)
+    # the SH rows' 48 moved values make a split practically impossible at these settings
+    p_sh = np.exp(-hp["lambda_sh"]) * (1 - 2 * kc * es ** 2) ** (-48 / 2)
+    assert p_sh < 1e-15
+
+
+def test_merge_closed_form_at_paper_hyperparameters():
+    """A row split off its parent by u ~ N(0, eps_split^2 I) (D = 7 moved values)
+    is proposed for merging with exp(-km |u|^2) and, with lambda > 0 and
+    kc < 0, always accepted (min(1, exp(lambda - kc |u|^2)) = 1); so it merges
+    with probability E[exp(-km eps_split^2 chi^2_7)] = (1 + 2 km eps_split^2)^(-7/2)
+    = 5^-3.5 at the paper's values (parents that are roots never merge)."""
+    hp = _paper()
+    rng = np.random.default_rng(12)
+    k0, width = 200_000, 8
+    rows = np.zeros((2 * k0, width), dtype=np.float32)
+    rows[:k0] = rng.normal(size=(k0, width)).astype(np.float32)
+    rows[k0:] = rows[:k0]
+    rows[k0:, :7] += (hp["eps_split"] * rng.normal(size=(k0, 7))).astype(np.float32)
+    parent = np.concatenate([np.full(k0, -1), np.arange(k0)]).astype(np.int32)
+    g2x = np.arange(2 * k0)
+    mg = mcmc.merge(rows, parent, g2x, 2 * k0, 0, 3, lam=hp["lambda_sr"], eps_split=hp["eps_split"],
+                    eps_merge=hp["eps_merge"], step=6, seed=14)
+    km = 0.5 / hp["eps_merge"] ** 2
+    p = (1 + 2 * km * hp["eps_split"] ** 2) ** (-7 / 2)
+    assert p == pytest.approx(5.0 ** -3.5, rel=1e-12)
+    got = int(mg["merged"][k0:].sum())
+    assert not mg["merged"][:k0].any()
+    assert abs(got - k0 * p) < 5 * np.sqrt(k0 * p * (1 - p)), (got, k0 * p)
 
 
 def test_merge_acceptance_rate_and_parent_rule():
