@@ -243,3 +243,117 @@ def test_codebook_membership_cache_follows_index_changes():
         for a, b in zip(got, fresh):
             assert torch.equal(a, b), which
     assert not torch.equal(got[0], g0[0]) and not torch.equal(got[1], g0[1])
+
+
+# ----------------------------------------------------------------------------
+# edge cases: empty lists, one Gaussian, every SH degree, degenerate
+# Gaussians, the largest codebooks and the most views of one launch
+# ----------------------------------------------------------------------------
+
+def test_no_visible_gaussian():
+    """Every Gaussian behind the camera: no record, no pair, every tile list
+    empty; the image is the background and every gradient is zero."""
+    scene, cams, _ = scenes.config_tiny()
+    s = scene.copy()
+    eye = cams[0].campos.astype(np.float64)
+    s.pos = (eye * 1.5 + 0.05 * np.random.default_rng(1).normal(size=(s.n, 3))).astype(np.float32)
+    ref, gpu = _case(s, cams, bg=(0.3, 0.6, 0.9))
+    assert ref.k_pairs == 0 and gpu["pairs"].size == 0
+    _compare(ref, gpu)
+    img = gpu["image"].reshape(3, -1)
+    assert np.array_equal(img, np.repeat(np.array([[0.3], [0.6], [0.9]], np.float32), img.shape[1], 1))
+    for k in ("dpos", "dlogit", "d_sr", "d_sh"):
+        assert not gpu[k].any(), k
+
+
+def test_single_gaussian():
+    scene, cams, _ = scenes.config_tiny()
+    s = scene.copy()
+    keep = slice(0, 1)
+    s.pos = np.zeros((1, 3), np.float32)
+    s.opacity_logit = np.array([2.0], np.float32)
+    s.g2sr, s.g2sh = scene.g2sr[keep].copy(), scene.g2sh[keep].copy()
+    s.sr_rows = scene.sr_rows.copy()
+    s.sr_rows[:, 0:3] = -1.5   # ~20 px across at this distance
+    ref, gpu = _case(s, cams, bg=(0.1, 0.2, 0.3))
+    assert ref.k_pairs > 1
+    _compare(ref, gpu)
+
+
+@pytest.mark.parametrize("degree", [0, 2])
+def test_sh_degrees_zero_and_two(degree):
+    """SH degrees 0 and 2 (the other workloads use 1 and 3)."""
+    scene, cams, _ = scenes.config_tiny()
+    rng = np.random.default_rng(20 + degree)
+    s = scene.copy()
+    s.sh_degree = degree
+    s.sh_rows = scenes._sh_rows(rng, scene.k_sh, degree)
+    ref, gpu = _case(s, cams)
+    _compare(ref, gpu)
+
+
+def test_degenerate_gaussians():
+    """Gaussians at the limits of the method: straddling the near plane,
+    needle-thin, larger than the image, opacity above the 0.99 clamp,
+    opacity below the 1/255 skip, colours clamped at zero."""
+    scene, cams, _ = scenes.config_tiny()
+    rng = np.random.default_rng(31)
+    s = scene.copy()
+    n = s.n
+    eye = cams[0].campos.astype(np.float64)
+    fwd = -eye / np.linalg.norm(eye)
+    s.pos = s.pos.copy()
+    s.opacity_logit = s.opacity_logit.copy()
+    s.g2sr, s.g2sh = s.g2sr.copy(), s.g2sh.copy()
+    k = s.k_sr
+    sr = np.concatenate([s.sr_rows, np.zeros((4, 8), np.float32)])
+    sr[k + 0, 0:3] = (-9.0, -9.0, -1.0)           # needle
+    sr[k + 1, 0:3] = (0.5, 0.5, 0.5)              # larger than the image
+    sr[k + 2, 0:3] = (-2.0, -2.0, -2.0)
+    sr[k + 3, 0:3] = (-6.0, -1.0, -6.0)           # thin disc
+    sr[k:, 3] = 1.0
+    sr[k + 3, 3:7] = (0.6, 0.0, 0.8, 0.0)
+    s.sr_rows = sr
+    sel = rng.choice(n, 120, replace=False)
+    groups = np.array_split(sel, 6)
+    s.g2sr[groups[0]] = k + 0
+    s.g2sr[groups[1]] = k + 1
+    s.g2sr[groups[2]] = k + 3
+    s.opacity_logit[groups[3]] = 9.0               # o > 0.99: alpha clamped
+    s.opacity_logit[groups[4]] = -7.0              # o < 1/255: always skipped
+    near = groups[5]
+    s.g2sr[near] = k + 2
+    s.pos[near] = (eye + fwd * rng.uniform(0.15, 0.3, size=(near.size, 1))
+                   + 0.05 * rng.normal(size=(near.size, 3))).astype(np.float32)
+    sh = s.sh_rows.copy()
+    sh[:8, 0, :] = -3.0                            # colours clamped at zero
+    s.sh_rows = sh
+    ref, gpu = _case(s, cams, bg=(0.05, 0.05, 0.05))
+    _compare(ref, gpu)
+
+
+def test_largest_codebooks():
+    """65,536 rows per codebook (the largest 16-bit index; the membership sort
+    takes 24 bits), most rows with zero or one member."""
+    scene, cams = scenes.config_single(n=30_000, k=1024, width=160, height=128)
+    rng = np.random.default_rng(41)
+    s = scene.copy()
+    k = 65536
+    s.sr_rows = scenes._sr_rows(rng, k, -3.0, 0.5)
+    s.sh_rows = scenes._sh_rows(rng, k, 3)
+    s.g2sr = rng.integers(0, k, size=s.n).astype(np.uint16)
+    s.g2sh = rng.integers(0, k, size=s.n).astype(np.uint16)
+    s.g2sr[:3] = k - 1
+    ref, gpu = _case(s, cams)
+    _compare(ref, gpu)
+
+
+def test_most_views_in_one_launch():
+    """64 views (the most one call takes) of small, uneven resolutions."""
+    scene, _ = scenes.config_single(n=5_000, k=256, width=8, height=8)
+    rng = np.random.default_rng(51)
+    dirs = scenes.fibonacci_dirs(64, rng)
+    cams = [scenes.look_at(3.0 * d, int(w), int(h))
+            for d, w, h in zip(dirs, rng.integers(9, 41, 64), rng.integers(9, 41, 64))]
+    ref, gpu = _case(scene, cams, bg=(0.2, 0.2, 0.2))
+    _compare(ref, gpu)
