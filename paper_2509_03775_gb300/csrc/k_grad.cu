@@ -404,11 +404,18 @@ __global__ void __launch_bounds__(256) k_sr_partials(const uint4* __restrict__ c
         const uint32_t i = i0 + 32u * u;
         g[u] = i < ch.z ? ids[i] : 0xffffffffu;
       }
+      // 24-byte rows: three 8-byte loads each
       float d[kGatherBatch][6];
 #pragma unroll
-      for (int u = 0; u < kGatherBatch; ++u)
+      for (int u = 0; u < kGatherBatch; ++u) {
+        const float2* row = reinterpret_cast<const float2*>(dsigma + 6 * (size_t)(g[u] != 0xffffffffu ? g[u] : 0u));
 #pragma unroll
-        for (int e = 0; e < 6; ++e) d[u][e] = g[u] != 0xffffffffu ? dsigma[6 * (size_t)g[u] + e] : 0.0f;
+        for (int e = 0; e < 3; ++e) {
+          const float2 v = g[u] != 0xffffffffu ? row[e] : make_float2(0.0f, 0.0f);
+          d[u][2 * e] = v.x;
+          d[u][2 * e + 1] = v.y;
+        }
+      }
 #pragma unroll
       for (int u = 0; u < kGatherBatch; ++u)
         if (g[u] != 0xffffffffu) {

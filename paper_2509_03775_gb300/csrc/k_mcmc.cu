@@ -55,8 +55,6 @@ __global__ void __launch_bounds__(256) k_sgld(const __grid_constant__ SgldArgs a
       ++seg;
     }
     const SgldSeg& sg = a.seg[seg];
-    const float4 z = normal4(draw4((uint32_t)c, sg.stream, 0, a.step, a.seed));
-    const float zz[4] = {z.x, z.y, z.z, z.w};
     const int64_t e0 = 4 * c;
     const int nv = (int)min((int64_t)4, sg.count - e0);
     float x[4] = {0.0f, 0.0f, 0.0f, 0.0f}, g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -92,6 +90,10 @@ __global__ void __launch_bounds__(256) k_sgld(const __grid_constant__ SgldArgs a
       for (int q = 0; q < 4; ++q)
         if (q < nv) g[q] = sg.g[e0 + q];
     }
+    // the draws after the loads, so the loads are in flight while the
+    // normals are computed
+    const float4 z = normal4(draw4((uint32_t)c, sg.stream, 0, a.step, a.seed));
+    const float zz[4] = {z.x, z.y, z.z, z.w};
     float y[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
