@@ -371,3 +371,26 @@ def test_growth_matches_oracle_and_membership_update_matches_rebuild():
     grads(r2, tensors(n))
     for a, b in zip(grads(r2, grown), fresh):
         assert torch.equal(a, b)
+
+
+def test_recon_loss_images_smaller_than_the_window():
+    """Views of 1x1, 11x11 (exactly one window), 1x17 and 23x2 pixels: the
+    zero-padded window sums reach past every edge."""
+    rng = np.random.default_rng(4)
+    cams = [types.SimpleNamespace(width=w, height=h, fx=1.0, fy=1.0, cx=0.0, cy=0.0, world_to_cam=np.zeros(12),
+                                  campos=np.zeros(3), near=0.2) for w, h in [(1, 1), (11, 11), (1, 17), (23, 2)]]
+    x, y = _smooth_pair(cams, rng)
+    _check_loss(x, y, cams, 0.2)
+
+
+def test_growth_by_zero_leaves_the_scene_unchanged():
+    scene, _ = scenes.config_single(n=5_000, k=64, width=8, height=8)
+    pos = torch.from_numpy(scene.pos).cuda()
+    logit = torch.from_numpy(scene.opacity_logit).cuda()
+    g2sr = torch.from_numpy(scene.g2sr.view(np.int16)).cuda()
+    g2sh = torch.from_numpy(scene.g2sh.view(np.int16)).cuda()
+    before = [t.clone() for t in (pos, logit, g2sr, g2sh)]
+    src = cg.grow(pos, logit, g2sr, g2sh, scene.n, 0, seed=3, step=1)
+    torch.cuda.synchronize()
+    assert src.numel() == 0
+    assert all(torch.equal(a, b) for a, b in zip(before, (pos, logit, g2sr, g2sh)))
