@@ -158,6 +158,7 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
   L->ncontrib = take(sizeof(uint32_t) * P);
   L->pairgrad = take(sizeof(float4) * 2 * Kc);   // 8 sums per pair, one 32-byte sector
   L->pairgrad1 = take(sizeof(float) * Kc);        // the opacity sum per pair
+  L->pairlive = take(sizeof(uint8_t) * Kc);       // 1 if the pair's sums were written this backward
   L->recgrad = take(sizeof(float) * 10 * R_cap);
   L->dsigma = take(sizeof(float) * 6 * n_cap);
   L->drgb = take(sizeof(float) * 3 * R_cap);

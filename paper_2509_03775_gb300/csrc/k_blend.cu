@@ -16,9 +16,13 @@
 // by a reduce-scatter butterfly over groups of three Gaussians (27 values,
 // 31 shuffles, lane l ends with value l), then over the warps in index order.
 // The pair's sums go to its slot, offset[record] + rank (the key carries the
-// rank; slots of a Gaussian are contiguous, in tile order): eight of them as one aligned 32-byte sector (mean x/y,
-// conic 0/1/2, colour r/g/b), the opacity sum in a separate array.  The
-// per-Gaussian gradient later sums a fixed set of slots in a fixed order.
+// rank; slots of a Gaussian are contiguous, in tile order): eight of them as
+// one aligned 32-byte sector (mean x/y, conic 0/1/2, colour r/g/b), the
+// opacity sum in a separate array, and a live flag of 1.  Pairs past every
+// pixel's last contributor have zero gradient; their slots only get a live
+// flag of 0.  The per-Gaussian gradient later sums a fixed set of slots in a
+// fixed order, skipping the dead ones (adding their zeros would change no
+// bit).
 // No floating-point atomics.
 //
 // The backward takes the forward's decisions exactly, but it only needs
@@ -47,6 +51,7 @@ struct BlendArgs {
   uint32_t* ncontrib;
   float4* pairgrad;   // [K][2]
   float* pairgrad1;   // [K]
+  uint8_t* pairlive;  // [K]
 };
 
 // power = h0 dx^2 + h1 dx dy + h2 dy^2 with d = mean - pixel centre
@@ -281,14 +286,11 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const Bl
   __syncthreads();
   const uint32_t maxc = s_maxc;
   const uint32_t len = rg.y - rg.x;
-  // pairs past the last contributor of every pixel get zero gradient
+  // pairs past the last contributor of every pixel have zero gradient: only
+  // their slots' live flags are cleared (the per-record sums skip them)
   for (uint32_t j = maxc + threadIdx.x; j < len; j += NT) {
     const uint64_t key = args.pairs[rg.x + j];
-    const uint32_t slot = args.offrec[key_rec(key)] + key_rank(key);
-    const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    args.pairgrad[2 * (size_t)slot] = z;
-    args.pairgrad[2 * (size_t)slot + 1] = z;
-    args.pairgrad1[slot] = 0.0f;
+    args.pairlive[args.offrec[key_rec(key)] + key_rank(key)] = 0;
   }
   // batches from the back: [b0, b1)
   for (int64_t b1 = (int64_t)rg.x + maxc; b1 > (int64_t)rg.x; b1 -= BATCH) {
@@ -351,6 +353,7 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const Bl
 #pragma unroll
         for (int w = 1; w < NW; ++w) t += part[w][j][5];
         args.pairgrad1[sSlot[j]] = t;
+        args.pairlive[sSlot[j]] = 1;
       }
     }
   }
@@ -402,6 +405,7 @@ static BlendArgs blend_args(const Layout& L, void* ws, const float bg[3]) {
   a.ncontrib = ws_ptr<uint32_t>(ws, L.ncontrib);
   a.pairgrad = ws_ptr<float4>(ws, L.pairgrad);
   a.pairgrad1 = ws_ptr<float>(ws, L.pairgrad1);
+  a.pairlive = ws_ptr<uint8_t>(ws, L.pairlive);
   return a;
 }
 

@@ -177,11 +177,19 @@ __device__ __forceinline__ void record_chain(const SceneArgs& sc, const ViewInfo
 // sums of each record go to rg[rec][0..8].
 constexpr int kSlotGroup = 8;
 
+// The nine sums of a slot; zeros for a dead slot (live flag 0), whose sums
+// were not written.
 __device__ __forceinline__ void load_slot(const float4* __restrict__ pairgrad, const float* __restrict__ pairgrad1,
-                                          uint32_t slot, float (&v)[9]) {
-  const float4 u = __ldcs(pairgrad + 2 * (size_t)slot), w = __ldcs(pairgrad + 2 * (size_t)slot + 1);
+                                          bool live, uint32_t slot, float (&v)[9]) {
+  float4 u = make_float4(0.0f, 0.0f, 0.0f, 0.0f), w = u;
+  float o = 0.0f;
+  if (live) {
+    u = __ldcs(pairgrad + 2 * (size_t)slot);
+    w = __ldcs(pairgrad + 2 * (size_t)slot + 1);
+    o = __ldcs(pairgrad1 + slot);
+  }
   v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w; v[4] = w.x;
-  v[5] = __ldcs(pairgrad1 + slot);
+  v[5] = o;
   v[6] = w.y; v[7] = w.z; v[8] = w.w;
 }
 
@@ -189,6 +197,7 @@ __global__ void __launch_bounds__(256) k_slot_sum(const uint32_t* __restrict__ n
                                                   const uint32_t* __restrict__ offrec,
                                                   const float4* __restrict__ pairgrad,
                                                   const float* __restrict__ pairgrad1,
+                                                  const uint8_t* __restrict__ pairlive,
                                                   const uint64_t* __restrict__ dsorted, const DeviceState* st,
                                                   float* __restrict__ rg) {
   if (st->pairs_ok == 0) return;
@@ -211,14 +220,15 @@ __global__ void __launch_bounds__(256) k_slot_sum(const uint32_t* __restrict__ n
     uint32_t t = sub;
     for (; t + kSlotGroup < nt; t += 2 * kSlotGroup) {
       float v0[9], v1[9];
-      load_slot(pairgrad, pairgrad1, off + t, v0);
-      load_slot(pairgrad, pairgrad1, off + t + kSlotGroup, v1);
+      const bool l0 = pairlive[off + t] != 0, l1 = pairlive[off + t + kSlotGroup] != 0;
+      load_slot(pairgrad, pairgrad1, l0, off + t, v0);
+      load_slot(pairgrad, pairgrad1, l1, off + t + kSlotGroup, v1);
 #pragma unroll
       for (int e = 0; e < 9; ++e) acc[e] = (acc[e] + v0[e]) + v1[e];
     }
     if (t < nt) {
       float v0[9];
-      load_slot(pairgrad, pairgrad1, off + t, v0);
+      load_slot(pairgrad, pairgrad1, pairlive[off + t] != 0, off + t, v0);
 #pragma unroll
       for (int e = 0; e < 9; ++e) acc[e] += v0[e];
     }
@@ -294,12 +304,13 @@ cudaError_t launch_gaussian_bwd(const SceneArgs& sc, const Layout& L, void* ws, 
   const uint32_t* off = ws_ptr<uint32_t>(ws, L.offrec);
   const float4* pg = ws_ptr<float4>(ws, L.pairgrad);
   const float* pg1 = ws_ptr<float>(ws, L.pairgrad1);
+  const uint8_t* live = ws_ptr<uint8_t>(ws, L.pairlive);
   float* rg = ws_ptr<float>(ws, L.recgrad);
   float* dsig = ws_ptr<float>(ws, L.dsigma);
   float* drgb = ws_ptr<float>(ws, L.drgb);
   const uint64_t* dsorted = depth_sorted(ws, L);
   const int grid_r = (int)std::max<int64_t>(1, std::min<int64_t>((L.R + 255) / 256, 152 * 16));
-  count_launch(), k_slot_sum<<<grid_r, 256, 0, s>>>(ws_ptr<const uint32_t>(ws, L.nemit), off, pg, pg1, dsorted,
+  count_launch(), k_slot_sum<<<grid_r, 256, 0, s>>>(ws_ptr<const uint32_t>(ws, L.nemit), off, pg, pg1, live, dsorted,
                                                     &hdr->st, rg);
   const int grid_g = (int)std::max<int64_t>(1, std::min<int64_t>((L.n + 255) / 256, 152 * 16));
 #define CG_CS(NBV) count_launch(), k_chain_sum<NBV><<<grid_g, 256, 0, s>>>(sc, L.n_views, views, sig, geo, rgbm, nt, rg, &hdr->st, d_pos, d_logit, dsig, drgb)
