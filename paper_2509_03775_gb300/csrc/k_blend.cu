@@ -19,10 +19,10 @@
 // rank; slots of a Gaussian are contiguous, in tile order): eight of them as
 // one aligned 32-byte sector (mean x/y, conic 0/1/2, colour r/g/b), the
 // opacity sum in a separate array, and a live flag of 1.  Pairs past every
-// pixel's last contributor have zero gradient; their slots only get a live
-// flag of 0.  The per-Gaussian gradient later sums a fixed set of slots in a
-// fixed order, skipping the dead ones (adding their zeros would change no
-// bit).
+// pixel's last contributor have zero gradient and are not touched: their
+// slots keep the live flag of 0 that pair emission wrote.  The per-Gaussian
+// gradient later sums a fixed set of slots in a fixed order, skipping the
+// dead ones (adding their zeros would change no bit).
 // No floating-point atomics.
 //
 // The backward takes the forward's decisions exactly, but it only needs
@@ -285,13 +285,6 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const Bl
   const uint32_t warp_max = __reduce_max_sync(0xffffffffu, my_max);
   __syncthreads();
   const uint32_t maxc = s_maxc;
-  const uint32_t len = rg.y - rg.x;
-  // pairs past the last contributor of every pixel have zero gradient: only
-  // their slots' live flags are cleared (the per-record sums skip them)
-  for (uint32_t j = maxc + threadIdx.x; j < len; j += NT) {
-    const uint64_t key = args.pairs[rg.x + j];
-    args.pairlive[args.offrec[key_rec(key)] + key_rank(key)] = 0;
-  }
   // batches from the back: [b0, b1)
   for (int64_t b1 = (int64_t)rg.x + maxc; b1 > (int64_t)rg.x; b1 -= BATCH) {
     const int64_t b0 = max((int64_t)rg.x, b1 - BATCH);

@@ -536,7 +536,8 @@ __global__ void k_capacity(DeviceState* st, int64_t cap) {
 // Pairs of one record in depth order: its kept tiles (tile_keep) in
 // row-major order of its rectangle, each as pair_key(global tile, rank among
 // the kept tiles, record) at offset + rank (offset = the exclusive prefix of
-// the kept counts in depth order).  A warp takes 32 consecutive
+// the kept counts in depth order), and a live flag of 0 in the pair's
+// gradient slot (the backward sets it for the pairs whose sums it writes).  A warp takes 32 consecutive
 // records and walks them one after another.  For a record of at most 64
 // rectangle tiles (whose kept-tile bits the count pass left in kmask), lane
 // l looks at tiles l and 32 + l: if kept, its rank is the number of kept
@@ -551,7 +552,7 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__
                                                     const ViewInfo* __restrict__ views, int64_t n, int tile,
                                                     const uint64_t* __restrict__ kmask,
                                                     uint32_t* __restrict__ offrec, uint64_t* __restrict__ pairs,
-                                                    const DeviceState* state) {
+                                                    uint8_t* __restrict__ pairlive, const DeviceState* state) {
   __shared__ TileRec st[8][32];      // tile test data (large records)
   __shared__ uint64_t sMask[8][32];  // kept-tile bits (small records)
   __shared__ uint4 sInfo[8][32];     // record, offset, x0 | y0 << 16, rectangle width | height << 16
@@ -614,6 +615,7 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__
               const uint32_t rank = (half == 0 ? 0u : (uint32_t)__popc(lo)) + (uint32_t)__popc(bits & lt_mask);
               const int yy = (int)(((float)k + 0.5f) * rw), xx = k - yy * w;
               pairs[inf.y + rank] = pair_key((uint64_t)(tb + (int64_t)(y0 + yy) * tx + (x0 + xx)), rank, inf.x);
+              pairlive[inf.y + rank] = 0;
             }
           }
         } else {
@@ -632,6 +634,7 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__
             if (keep) {
               const uint32_t rank = rank0 + __popc(mk & lt_mask);
               pairs[inf.y + rank] = pair_key((uint64_t)(tb + (int64_t)(y0 + yy) * tx + (x0 + xx)), rank, inf.x);
+              pairlive[inf.y + rank] = 0;
             }
             rank0 += __popc(mk);
           }
@@ -727,7 +730,7 @@ cudaError_t launch_build_pairs(const Layout& L, void* ws, int tile_bits, cudaStr
   count_launch(), k_emit_pairs<<<g, 256, 0, s>>>(dsorted, scan, gsum, ws_ptr<const float4>(ws, L.geo),
                                                  ws_ptr<const ushort4>(ws, L.rect), ws_ptr<ViewInfo>(ws, L.views),
                                                  L.n, L.tile, ws_ptr<const uint64_t>(ws, L.kmask),
-                                                 ws_ptr<uint32_t>(ws, L.offrec), p0, st);
+                                                 ws_ptr<uint32_t>(ws, L.offrec), p0, ws_ptr<uint8_t>(ws, L.pairlive), st);
   // 5. stable sort on the tile bits
   e = sort_u64(ws, L, p0, p1, &st->pairs, L.Kc, kKeyTileShift, L.tile_bits, &in_b, s);
   if (e != cudaSuccess) return e;
