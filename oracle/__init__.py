@@ -101,7 +101,7 @@ def lib():
             L.or_tile_keep32.argtypes = [ctypes.c_float] * 6 + [ctypes.c_int] * 3
             L.or_tile_keep32.restype = ctypes.c_int
             L.or_blend_forward.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P,
-                                           _P, _P, _P, _P, _P]
+                                           _P, _P, _P, _P, _P, _P]
             L.or_blend_backward.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, _P,
                                             _P, _P, _P, _P, _P]
             L.or_pair_sum.argtypes = [_P, ctypes.c_int64, _P, ctypes.c_int64, _P]
@@ -283,7 +283,7 @@ class Render:
         self.rec64 = self._preprocess(self.sb)
         t3 = time.perf_counter()
         self.timing["preprocess"] = t3 - t2
-        self.image, self.t_final, self.n_contrib = self._forward(self.rec64)
+        self.image, self.t_final, self.n_contrib, self.term_pos = self._forward(self.rec64)
         self.timing["blend_fwd"] = time.perf_counter() - t3
 
     # -- steps ---------------------------------------------------------------
@@ -296,11 +296,12 @@ class Render:
         image = np.zeros(3 * self.P)
         t_final = np.zeros(self.P)
         n_contrib = np.zeros(self.P, dtype=np.int32)
+        term_pos = np.full(self.P, -1, dtype=np.int32)
         mask = _ptr(self.tile_mask) if self.tile_mask is not None else None
         lib().or_blend_forward(self._c, self.V, self.tile, _ptr(self.bg), self.mode, _ptr(self.rec32),
                                _ptr(rec64), _ptr(self.list), _ptr(self.ranges), mask, _ptr(image),
-                               _ptr(t_final), _ptr(n_contrib))
-        return image, t_final, n_contrib
+                               _ptr(t_final), _ptr(n_contrib), _ptr(term_pos))
+        return image, t_final, n_contrib, term_pos
 
     def replay(self, scene, sr_rows=None, sh_rows=None) -> np.ndarray:
         """FP64 image of a (perturbed) scene under this render's decisions."""

@@ -650,11 +650,14 @@ static int find_view(const view_geom *vg, int n_views, int64_t gt) {
 
 /* image[3 * pix_base + c * H * W + y * W + x]; t_final / n_contrib indexed
  * by pix_base + y * W + x.  tile_mask (may be NULL) restricts the work to
- * tiles with a non-zero byte; other pixels are left untouched. */
+ * tiles with a non-zero byte; other pixels are left untouched.  term_pos
+ * (may be NULL) receives, per pixel, the list position of the Gaussian at
+ * which compositing stopped (the transmittance would have fallen below its
+ * floor), or -1 when the pixel went through its whole list. */
 void or_blend_forward(const or_camera *cams, int n_views, int tile, const double bg[3], int mode,
                       const or_rec32 *rec32, const or_rec64 *rec64, const uint32_t *list,
                       const uint32_t *ranges, const uint8_t *tile_mask, double *image, double *t_final,
-                      int32_t *n_contrib) {
+                      int32_t *n_contrib, int32_t *term_pos) {
   view_geom vg[64];
   make_geoms(cams, n_views, tile, vg);
   const int64_t n_tiles = vg[n_views - 1].tile_base + (int64_t)vg[n_views - 1].tiles_x * vg[n_views - 1].tiles_y;
@@ -672,7 +675,7 @@ void or_blend_forward(const or_camera *cams, int n_views, int tile, const double
         const double pxc = x + 0.5, pyc = y + 0.5;
         float T32 = 1.0f;
         double T = 1.0, C[3] = {0, 0, 0};
-        int32_t last = 0;
+        int32_t last = 0, stop = -1;
         for (uint32_t i = beg; i < end; ++i) {
           const uint32_t rid = list[i];
           const or_rec64 *r = &rec64[rid];
@@ -683,7 +686,10 @@ void or_blend_forward(const or_camera *cams, int n_views, int tile, const double
             alpha = r->opacity * Gv;
           } else {
             const int code = decide32(&rec32[rid], pxc32, pyc32, &T32);
-            if (code < 0) break;
+            if (code < 0) {
+              stop = (int32_t)(i - beg);
+              break;
+            }
             if (code == CODE_SKIP) continue;
             alpha = code == CODE_ADD_CLAMPED ? 0.99 : r->opacity * Gv;
           }
@@ -697,6 +703,7 @@ void or_blend_forward(const or_camera *cams, int n_views, int tile, const double
           image[3 * G->pix_base + c * hw + (int64_t)y * G->width + x] = C[c] + T * bg[c];
         t_final[pix] = T;
         n_contrib[pix] = last;
+        if (term_pos) term_pos[pix] = stop;
       }
   }
 }

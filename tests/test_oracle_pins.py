@@ -516,3 +516,42 @@ def test_tile_test_drops_only_pairs_every_pixel_skips():
     ga, gb = a.backward(w), b.backward(w)
     for k in ("dpos", "dlogit", "d_sr", "d_sh"):
         assert np.allclose(ga[k], gb[k], rtol=1e-13, atol=1e-18), k
+
+
+def test_stop_positions_bound_the_lists():
+    """Where a pixel stops compositing (its transmittance would fall below
+    the floor), nothing later in its tile's list can change it: rendering
+    with every tile's list cut right after the last stop of its pixels, for
+    the tiles whose pixels all stop, gives bit-identical image, final
+    transmittance and contributor counts.  Stops follow the last
+    contributor; pixels that never stop keep their full lists."""
+    sc, cams = scenes.config_single(n=20_000, k=256, width=96, height=80)
+    r = oracle.Render(sc, cams)
+    stop = r.term_pos
+    assert np.all((stop == -1) | (stop >= r.n_contrib))
+    assert (stop >= 0).mean() > 0.2          # enough stopped pixels for the cut to bite
+    cut = r.ranges.astype(np.int64).copy()
+    cam = cams[0]
+    tx = -(-cam.width // 16)
+    st = stop.reshape(cam.height, cam.width)
+    shortened = 0
+    for gt in range(r.n_tiles):
+        ty, txx = divmod(gt, tx)
+        blk = st[16 * ty:16 * ty + 16, 16 * txx:16 * txx + 16]
+        if np.all(blk >= 0):
+            new_end = cut[gt, 0] + int(blk.max()) + 1
+            shortened += int(cut[gt, 1] - new_end)
+            cut[gt, 1] = new_end
+    assert shortened > 0
+    image = np.zeros(3 * r.P)
+    t_final = np.zeros(r.P)
+    n_contrib = np.zeros(r.P, dtype=np.int32)
+    stop2 = np.zeros(r.P, dtype=np.int32)
+    ranges = np.ascontiguousarray(cut.astype(np.uint32))
+    _p = oracle._ptr
+    oracle.lib().or_blend_forward(r._c, r.V, r.tile, _p(r.bg), r.mode, _p(r.rec32), _p(r.rec64), _p(r.list),
+                                  _p(ranges), None, _p(image), _p(t_final), _p(n_contrib), _p(stop2))
+    assert np.array_equal(image, r.image)
+    assert np.array_equal(t_final, r.t_final)
+    assert np.array_equal(n_contrib, r.n_contrib)
+    assert np.array_equal(stop2, stop)
