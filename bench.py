@@ -380,7 +380,9 @@ def run_cg(args):
 
     # stage breakdown and the dominant kernel's roofline
     ncontrib = r.array(cg.WS_NCONTRIB, torch.int32).to(torch.int64).sum().item()
-    stages = {k: {"ms_per_launch": (v[0] / v[1] if v[1] else None), "launches": v[1]} for k, v in stage.items()}
+    # per step: a forward times its list construction and compositing twice
+    # (the two list parts), so stage times are summed over the step
+    stages = {k: {"ms_per_step": (v[0] / args.steps if v[1] else None), "launches": v[1]} for k, v in stage.items()}
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
     hbm_src = "of measured" if hbm_peak else "of fallback"
@@ -389,8 +391,8 @@ def run_cg(args):
     R = n * n_views
     cb_bytes = (scene.k_sr * 32 + scene.k_sh * 4 * 3 * nb) // (2 if bf16 else 1)
     step_bytes = 200 * R + 44 * pairs + 40 * P + 3 * cb_bytes
-    dominant = max((k for k in stages if stages[k]["ms_per_launch"]), key=lambda k: stages[k]["ms_per_launch"])
-    dom_ms = stages[dominant]["ms_per_launch"]
+    dominant = max((k for k in stages if stages[k]["ms_per_step"]), key=lambda k: stages[k]["ms_per_step"])
+    dom_ms = stages[dominant]["ms_per_step"]
     traffic = None
     rec = NCU_TRAFFIC.get(dominant)
     if rec and rec.get("src") == _src_hash(KERNEL_SOURCE[dominant]) and rec.get("workload") == args.workload:
@@ -439,7 +441,7 @@ def run_cg(args):
                               "model": "200 R + 44 K + 40 P + codebooks (read twice, gradients once); R = views x Gaussians",
                               "note": hbm_src},
         "roofline": roofline,
-        "stages_ms": {k: (round(v["ms_per_launch"], 4) if v["ms_per_launch"] else None) for k, v in stages.items()},
+        "stages_ms": {k: (round(v["ms_per_step"], 4) if v["ms_per_step"] else None) for k, v in stages.items()},
         "evaluations": int(ncontrib),
         "gpu_launches": int(launches),
         "clocks": clk,

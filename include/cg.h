@@ -121,13 +121,22 @@ typedef struct {
 } cg_opts;
 
 /* Workspace bytes for rendering `n_views` cameras (host array) of `scene`
- * with these options.  Returns 0 for invalid arguments. */
+ * with these options.  Returns 0 for invalid arguments.  The workspace keeps
+ * the codebook memberships between calls; before its first call, zero its
+ * first 4096 bytes (the header), and do not let other code write it between
+ * calls.  The header records the layout the workspace was last used with:
+ * a call with another layout, or on a header the library did not write,
+ * starts a new epoch and rebuilds everything kept. */
 size_t cg_workspace_bytes(const cg_scene *scene, const cg_camera *cams, int n_views, const cg_opts *opts);
 
 /* Forward render I_P(G, C) of every view (Eqs. 1-3, Sec. 4.1 indirection):
  * codebook gather, Eq. 2, EWA projection, SH colour, tile/depth keys (a
  * Gaussian is listed in the tiles of its 3-sigma rectangle where alpha can
- * reach 1/255), radix sort, per-tile front-to-back compositing.
+ * reach 1/255), radix sort, per-tile front-to-back compositing.  The tile
+ * lists are built and composited in two parts: the nearest tenth of the
+ * visible Gaussians (by depth) first, then the others in the tiles where
+ * some pixel is still compositing; a tile's list is cut only where every one
+ * of its pixels has stopped, so the result is that of the whole lists.
  *   cams      host array of n_views cameras (1 <= n_views <= CG_MAX_VIEWS)
  *   images    device float, views packed one after the other, each [3][H][W]
  * The workspace keeps what the backward needs (per-Gaussian records, sorted
@@ -172,8 +181,9 @@ cg_status cg_codebook_append(const cg_scene *scene, const cg_camera *cams, int n
 
 /* Synchronises `stream` and returns the device status of the workspace
  * (CG_OK, CG_ERR_INDEX or CG_ERR_CAPACITY).  *pairs_out (host, may be NULL)
- * receives the pair count of the last forward, which is also the capacity
- * needed when the status is CG_ERR_CAPACITY. */
+ * receives the pair count of the last forward (both list parts), which is
+ * also the capacity needed when the status is CG_ERR_CAPACITY (when the
+ * first part alone overflowed, an upper bound). */
 cg_status cg_last_device_status(void *workspace, size_t ws_bytes, cg_stream_t stream, uint64_t *pairs_out);
 
 /* L1 loss of Eq. 4's first term as a test harness: *loss_out (device, one
@@ -335,9 +345,16 @@ cg_status cg_grow(const cg_params *params, uint16_t *g2sr, uint16_t *g2sh, int m
  * and element count written to the host outputs).  Layouts:
  *   CG_WS_RECT        [V*n] uint16x4  tile rectangle x0, y0, x1, y1 (x1 == x0 when culled)
  *   CG_WS_DEPTH       [V*n] uint32    IEEE bits of the FP32 camera depth
- *   CG_WS_PAIRS       [K]   uint64    sorted (global tile << 43) | (rank << 26) | (v*n + g),
+ *   CG_WS_PAIRS       [K_a] uint64    first part of the tile lists (the pairs of the nearest
+ *                                     ceil(visible / 10) records in depth order), sorted
+ *                                     (global tile << 43) | (rank << 26) | (v*n + g),
  *                                     rank = index among the record's listed tiles
- *   CG_WS_RANGES      [T]   uint32x2  [start, end) of each global tile in the pairs
+ *   CG_WS_RANGES      [T]   uint32x2  [start, end) of each global tile in the first part
+ *   CG_WS_PAIRS_B     [K_b] uint64    second part: the pairs of the other records, listed only
+ *                                     in tiles some pixel of which was still compositing
+ *                                     after the first part (a tile's list is its first part
+ *                                     followed by its second); same key layout
+ *   CG_WS_RANGES_B    [T]   uint32x2  [start, end) of each global tile in the second part
  *   CG_WS_NCONTRIB    [P]   uint32    position after the last contributor, per pixel
  *   CG_WS_TFINAL      [P]   float     final transmittance per pixel
  *   CG_WS_DSIGMA      [n]   float x6  dL/dSigma per Gaussian (unique entries 00 01 02 11 12 22)
@@ -345,13 +362,14 @@ cg_status cg_grow(const cg_params *params, uint16_t *g2sr, uint16_t *g2sh, int m
  *   CG_WS_GEO         [V*n] float x8  mean x, y, -c0/2, -c1, -c2/2, opacity, skip bound, 0
  *   CG_WS_RGB         [V*n] float x4  colour r, g, b, clamp mask bits
  *   CG_WS_SIGMA3      [k_sr] float x6 Sigma of each SR row (Eq. 2, FP32)
- *   CG_WS_CSR_STATE   [2]  40 B       kept-membership record of the SR and SH codebooks:
+ *   CG_WS_CSR_STATE   [2]  48 B       kept-membership record of the SR and SH codebooks:
  *                                     uint64 tag, uint64 index-array address, uint32 rows,
  *                                     uint32 Gaussians, uint32 pending flags, uint32 count of
- *                                     incremental updates, uint64 chunk count */
+ *                                     incremental updates, uint64 chunk count, uint64 epoch */
 typedef enum {
   CG_WS_RECT = 0, CG_WS_DEPTH, CG_WS_PAIRS, CG_WS_RANGES, CG_WS_NCONTRIB, CG_WS_TFINAL,
-  CG_WS_DSIGMA, CG_WS_DRGB, CG_WS_GEO, CG_WS_RGB, CG_WS_SIGMA3, CG_WS_CSR_STATE
+  CG_WS_DSIGMA, CG_WS_DRGB, CG_WS_GEO, CG_WS_RGB, CG_WS_SIGMA3, CG_WS_CSR_STATE,
+  CG_WS_PAIRS_B, CG_WS_RANGES_B
 } cg_ws_array;
 cg_status cg_workspace_array(void *workspace, size_t ws_bytes, cg_ws_array which, void **ptr_out,
                              uint64_t *count_out);

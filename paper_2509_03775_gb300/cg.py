@@ -22,10 +22,11 @@ CG_OK, CG_ERR_ARG, CG_ERR_INDEX, CG_ERR_CAPACITY, CG_ERR_TIMEOUT, CG_ERR_CUDA = 
 STATUS_NAMES = {0: "CG_OK", 1: "CG_ERR_ARG", 2: "CG_ERR_INDEX", 3: "CG_ERR_CAPACITY", 4: "CG_ERR_TIMEOUT",
                 5: "CG_ERR_CUDA"}
 CG_F32, CG_BF16 = 0, 1
+WS_HEADER_ZERO_BYTES = 4096   # a new workspace's leading bytes cleared before first use (the header)
 MAX_VIEWS = 64
 
 WS_RECT, WS_DEPTH, WS_PAIRS, WS_RANGES, WS_NCONTRIB, WS_TFINAL, WS_DSIGMA, WS_DRGB, WS_GEO, WS_RGB, WS_SIGMA3, \
-    WS_CSR_STATE = range(12)
+    WS_CSR_STATE, WS_PAIRS_B, WS_RANGES_B = range(14)
 
 # every symbol include/cg.h declares
 EXPORTS = ["cg_workspace_bytes", "cg_render_fwd", "cg_render_bwd", "cg_codebook_reduce", "cg_last_device_status",
@@ -196,8 +197,13 @@ def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
 
 
 def _aligned_workspace(nbytes: int, device) -> tuple[torch.Tensor, ctypes.c_void_p]:
+    """A 256-byte aligned workspace whose header is zeroed: a new buffer must
+    not carry another workspace's header, or the library would trust state
+    left in it (the kept codebook memberships)."""
     ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
-    return ws, ctypes.c_void_p(ws.data_ptr() + (-ws.data_ptr()) % 256)
+    off = (-ws.data_ptr()) % 256
+    ws[off:off + min(nbytes, WS_HEADER_ZERO_BYTES)].zero_()
+    return ws, ctypes.c_void_p(ws.data_ptr() + off)
 
 
 class ReconLoss:
@@ -423,9 +429,7 @@ class Renderer:
         nbytes = self.lib.cg_workspace_bytes(ctypes.byref(sc), self._cams, len(self.cams), ctypes.byref(o))
         if nbytes == 0:
             raise CgError("cg_workspace_bytes", CG_ERR_ARG)
-        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
-        off = (-self.ws.data_ptr()) % 256
-        self._ws_ptr = ctypes.c_void_p(self.ws.data_ptr() + off)
+        self.ws, self._ws_ptr = _aligned_workspace(nbytes, self.device)
         self.ws_bytes = nbytes
         self._key = key
 

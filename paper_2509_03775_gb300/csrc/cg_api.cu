@@ -97,7 +97,7 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
   memset(table, 0, sizeof(*table));
   table->n_views = n_views;
   table->tile = o->tile;
-  int64_t T = 0, P = 0;
+  int64_t T = 0, P = 0, S = 0;
   for (int v = 0; v < n_views; ++v) {
     const cg_camera& c = cams[v];
     if (c.width < 1 || c.height < 1 || c.width > 65535 || c.height > 65535) return CG_ERR_ARG;
@@ -111,8 +111,10 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
     vi.tiles_y = (c.height + o->tile - 1) / o->tile;
     vi.tile_base = T;
     vi.pix_base = P;
+    vi.sat_base = S;
     T += (int64_t)vi.tiles_x * vi.tiles_y;
     P += (int64_t)c.width * c.height;
+    S += (int64_t)(vi.tiles_x + 1) * (vi.tiles_y + 1);
   }
   // key layout (pair_key): records < 2^26, tiles per view < 2^17, tiles < 2^21
   if (R_cap > (int64_t)kKeyRecMask + 1) return CG_ERR_ARG;
@@ -122,7 +124,7 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
   memset(L, 0, sizeof(*L));
   const int nb = (s->sh_degree + 1) * (s->sh_degree + 1);
   const int64_t Kc = (int64_t)o->pair_capacity;
-  L->n = n; L->R = R; L->T = T; L->P = P; L->Kc = Kc;
+  L->n = n; L->R = R; L->T = T; L->P = P; L->Kc = Kc; L->S = S;
   L->k_sr = s->k_sr; L->k_sh = s->k_sh; L->nb = nb; L->n_views = n_views; L->tile = o->tile;
   L->tile_bits = std::max(1, ceil_log2(T));
   L->sort_blocks_cap = (std::max(Kc, R_cap) + 4095) / 4096 + 1;  // 4096 keys per sort block
@@ -154,6 +156,11 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
   L->pairs0 = take(sizeof(uint64_t) * Kc);
   L->pairs1 = take(sizeof(uint64_t) * Kc);
   L->ranges = take(sizeof(uint32_t) * 2 * T);
+  L->pairs_b0 = take(sizeof(uint64_t) * Kc);   // second list part
+  L->pairs_b1 = take(sizeof(uint64_t) * Kc);
+  L->ranges_b = take(sizeof(uint32_t) * 2 * T);
+  L->unsat = take(sizeof(uint8_t) * T);
+  L->sat = take(sizeof(uint32_t) * S);           // prefix sums of unfinished tiles per view
   L->tfinal = take(sizeof(float) * P);
   L->ncontrib = take(sizeof(uint32_t) * P);
   L->pairgrad = take(sizeof(float4) * 2 * Kc);   // 8 sums per pair, one 32-byte sector
@@ -249,13 +256,18 @@ cg_status cg_render_fwd(const cg_scene* scene, const cg_camera* cams, int n_view
     if (e == cudaSuccess) e = launch_sigma3(sc, L, workspace, s);
     if (e == cudaSuccess) e = launch_preprocess(sc, L, workspace, s);
   }
-  if (e == cudaSuccess) {
-    StageTimer t(CG_STAGE_SORT, s);
-    e = launch_build_pairs(L, workspace, L.tile_bits, s);
-  }
-  if (e == cudaSuccess) {
-    StageTimer t(CG_STAGE_BLEND_FWD, s);
-    e = launch_blend_fwd(L, workspace, opts->tile, fwd_batch(opts), fwd_ppt(opts), opts->bg, images, s);
+  // the tile lists in two parts: the nearest tenth of the visible records
+  // first, composited; then the rest, for the tiles that part left
+  // unfinished
+  for (int part = 0; part < 2 && e == cudaSuccess; ++part) {
+    {
+      StageTimer t(CG_STAGE_SORT, s);
+      e = launch_build_lists(L, workspace, part, s);
+    }
+    if (e == cudaSuccess) {
+      StageTimer t(CG_STAGE_BLEND_FWD, s);
+      e = launch_blend_fwd(L, workspace, opts->tile, fwd_batch(opts), fwd_ppt(opts), opts->bg, images, part, s);
+    }
   }
   return cuda_status(e);
 }
@@ -344,8 +356,10 @@ cg_status cg_workspace_array(void* workspace, size_t ws_bytes, cg_ws_array which
   switch (which) {
     case CG_WS_RECT: off = L.rect; cnt = L.R; break;
     case CG_WS_DEPTH: off = L.depth; cnt = L.R; break;
-    case CG_WS_PAIRS: off = (passes & 1) ? L.pairs1 : L.pairs0; cnt = h.st.pairs_ok ? h.st.pairs : 0; break;
+    case CG_WS_PAIRS: off = (passes & 1) ? L.pairs1 : L.pairs0; cnt = h.st.pairs_ok ? h.st.pairs_a : 0; break;
     case CG_WS_RANGES: off = L.ranges; cnt = L.T; break;
+    case CG_WS_PAIRS_B: off = (passes & 1) ? L.pairs_b1 : L.pairs_b0; cnt = h.st.pairs_ok ? h.st.pairs_b : 0; break;
+    case CG_WS_RANGES_B: off = L.ranges_b; cnt = L.T; break;
     case CG_WS_NCONTRIB: off = L.ncontrib; cnt = L.P; break;
     case CG_WS_TFINAL: off = L.tfinal; cnt = L.P; break;
     case CG_WS_DSIGMA: off = L.dsigma; cnt = L.n; break;

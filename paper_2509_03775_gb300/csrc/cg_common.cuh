@@ -252,6 +252,7 @@ struct ViewInfo {
   int tiles_x, tiles_y;
   int64_t tile_base;  // first global tile of the view
   int64_t pix_base;   // first pixel of the view (images hold 3 * pix_base floats before it)
+  int64_t sat_base;   // first entry of the view's (tiles_y + 1) x (tiles_x + 1) table of unfinished-tile prefix sums
 };
 
 // Copies the first n_views entries of the view table into shared memory
@@ -278,11 +279,11 @@ struct ViewTable {
 struct Layout {
   uint64_t total;
   uint64_t hdr, views, sigma3, geo, rgbm, rect, ntiles, depth, offrec, scan, dkeys0, dkeys1, pairs0, pairs1,
-      ranges, tfinal, ncontrib, pairgrad, pairgrad1, pairlive, recgrad, nemit, kmask, dsigma, drgb, csr_keys0, csr_keys1, csr_off_sr, csr_off_sh, csr_ids_sr, csr_ids_sh, chunks, chunks_sh,
+      ranges, tfinal, ncontrib, pairgrad, pairgrad1, pairlive, recgrad, pairs_b0, pairs_b1, ranges_b, unsat, sat, nemit, kmask, dsigma, drgb, csr_keys0, csr_keys1, csr_off_sr, csr_off_sh, csr_ids_sr, csr_ids_sh, chunks, chunks_sh,
       csr_idx_sr, csr_idx_sh, csr_state, csr_tmp, gsum,
       partials, hist, blocksums, l1;
   // sizes
-  int64_t n, R, T, P, Kc;
+  int64_t n, R, T, P, Kc, S;  // S: entries of the unfinished-tile prefix-sum tables
   int k_sr, k_sh, nb, n_views, tile, tile_bits;
   int64_t sort_blocks_cap;   // capacity of the per-block digit histograms
   int64_t scan_blocks_cap;   // capacity of the per-block scan sums
@@ -300,6 +301,7 @@ struct CsrState {
   uint32_t changed;   // set by the check (bit 0 rebuild, bit 1 append), cleared when done
   uint32_t appends;   // incremental updates done (for tests)
   uint64_t nchunks;   // chunks of the cached build
+  uint64_t epoch;     // the workspace epoch (WsHeader) the build was made in
 };
 constexpr uint64_t kCsrMagic = 0x43535243'00000001ull;
 
@@ -307,18 +309,26 @@ constexpr uint64_t kCsrMagic = 0x43535243'00000001ull;
 struct DeviceState {
   uint32_t status;      // cg_status of device-detected problems (first wins)
   uint32_t detail;
-  uint64_t pairs;       // K of the last forward
+  uint64_t pairs;       // K of the last forward (both list parts)
   uint64_t visible;     // visible (view, Gaussian) records of the last forward
   uint64_t scan_total;  // scratch total written by the scan kernels
   uint32_t pairs_ok;    // 1 if pairs <= capacity
   uint32_t pad;
   uint64_t red_a, red_b;  // scratch counts (scan lengths and totals of the pair list and codebook builds)
+  uint64_t pairs_a;       // pairs of the first list part (the nearest tenth of the visible records)
+  uint64_t pairs_b;       // pairs of the second part (the other records, unfinished tiles only)
 };
 
+// The header at the start of every workspace.  epoch changes whenever a call
+// finds the header not written by this library or written for another layout
+// (a new buffer, or one reused with other cameras or options): anything a
+// workspace keeps between calls (the codebook memberships) is trusted only
+// within one epoch.
 struct WsHeader {
   uint64_t magic;
   Layout layout;
   DeviceState st;
+  uint64_t epoch;
 };
 
 constexpr uint64_t kMagic = 0x43475753'00000001ull;  // "CGWS" v1
@@ -419,9 +429,10 @@ struct SceneArgs {
 cudaError_t launch_setup(const ViewTable& table, const Layout& L, void* ws, cudaStream_t s);
 cudaError_t launch_sigma3(const SceneArgs& sc, const Layout& L, void* ws, cudaStream_t s);
 cudaError_t launch_preprocess(const SceneArgs& sc, const Layout& L, void* ws, cudaStream_t s);
-cudaError_t launch_build_pairs(const Layout& L, void* ws, int tile_bits, cudaStream_t s);
+// Tile lists, part 0 (with visibility and depth sort) or part 1.
+cudaError_t launch_build_lists(const Layout& L, void* ws, int part, cudaStream_t s);
 cudaError_t launch_blend_fwd(const Layout& L, void* ws, int tile, int batch, int ppt, const float bg[3],
-                             float* images, cudaStream_t s);
+                             float* images, int phase, cudaStream_t s);
 cudaError_t launch_blend_bwd(const Layout& L, void* ws, int tile, int batch, int ppt, const float bg[3],
                              const float* d_images, cudaStream_t s);
 bool blend_ppt_ok(int tile, int ppt);
@@ -447,6 +458,10 @@ inline int sort_passes(int nbits) { return (nbits + 7) / 8; }
 inline int tile_passes(const Layout& L) { return sort_passes(L.tile_bits); }
 inline uint64_t* sorted_pairs(void* ws, const Layout& L) {
   return ws_ptr<uint64_t>(ws, (tile_passes(L) & 1) ? L.pairs1 : L.pairs0);
+}
+// The second list part's tile-sorted pairs (same passes).
+inline uint64_t* sorted_pairs_b(void* ws, const Layout& L) {
+  return ws_ptr<uint64_t>(ws, (tile_passes(L) & 1) ? L.pairs_b1 : L.pairs_b0);
 }
 
 // Radix sort of `count` (device value) uint64 keys on bits [lo, lo + nbits),

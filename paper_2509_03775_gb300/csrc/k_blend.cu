@@ -39,8 +39,12 @@ namespace cg {
 struct BlendArgs {
   const ViewInfo* views;
   int n_views;
-  const uint2* ranges;
+  int phase;                // forward: 0 = nearest records' lists, 1 = the rest
+  const uint2* ranges;      // lists of the nearest records (first part of every tile's list)
   const uint64_t* pairs;
+  const uint2* ranges_b;    // lists of the other records, for tiles not finished by the first part
+  const uint64_t* pairs_b;
+  uint8_t* unsat;           // per tile: 1 if some pixel was still compositing after the first part
   const float4* geo;
   const float4* rgbm;
   const uint32_t* offrec;
@@ -83,9 +87,15 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_fwd(const Bl
   const ViewInfo& cam = args.views[v];
   const int64_t lt = gt - cam.tile_base;
   const int tx = (int)(lt % cam.tiles_x), ty = (int)(lt / cam.tiles_x);
-  const uint2 rg = args.ranges[gt];
+  // the second pass only continues the tiles the first one left unfinished
+  if (args.phase == 1 && args.unsat[gt] == 0) return;
+  const uint2 rg = args.phase == 0 ? args.ranges[gt] : args.ranges_b[gt];
+  const uint64_t* pairs = args.phase == 0 ? args.pairs : args.pairs_b;
+  // list positions of this part start after the first part's
+  const uint32_t pos0 = args.phase == 0 ? 0u : args.ranges[gt].y - args.ranges[gt].x;
   const int x = tx * TILE + S::px(threadIdx.x);
   const float pxc = (float)x + 0.5f;
+  const int64_t hw = (int64_t)cam.width * cam.height;
   float pyc[PPT], T[PPT], C[PPT][3];
   uint32_t last[PPT];
   bool done[PPT];
@@ -97,6 +107,19 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_fwd(const Bl
     C[k][0] = C[k][1] = C[k][2] = 0.0f;
     last[k] = 0;
     done[k] = !(x < cam.width && y < cam.height);
+    if (args.phase == 1 && !done[k]) {
+      // state the first pass left: raw colour sums in the image, the
+      // transmittance, the contributor position with the stop flag in bit 31
+      const int64_t pix = cam.pix_base + (int64_t)y * cam.width + x;
+      const float* img = args.images + 3 * cam.pix_base + (int64_t)y * cam.width + x;
+      C[k][0] = img[0];
+      C[k][1] = img[hw];
+      C[k][2] = img[2 * hw];
+      T[k] = args.tfinal[pix];
+      const uint32_t nc = args.ncontrib[pix];
+      last[k] = nc & 0x7fffffffu;
+      done[k] = (nc >> 31) != 0u;
+    }
   }
   for (uint32_t b0 = rg.x; b0 < rg.y; b0 += BATCH) {
     bool mine = true;
@@ -105,7 +128,7 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_fwd(const Bl
     if (__syncthreads_and(mine)) break;
     const int n_in = (int)min((uint32_t)BATCH, rg.y - b0);
     for (int j = threadIdx.x; j < n_in; j += NT) {
-      const uint32_t rec = key_rec(args.pairs[b0 + j]);
+      const uint32_t rec = key_rec(pairs[b0 + j]);
       sA[j] = args.geo[2 * (size_t)rec];
       sB[j] = args.geo[2 * (size_t)rec + 1];
       sC[j] = args.rgbm[rec];
@@ -133,22 +156,35 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_fwd(const Bl
         C[k][1] = fmaf(w, c.y, C[k][1]);
         C[k][2] = fmaf(w, c.z, C[k][2]);
         T[k] = test_T;
-        last[k] = b0 - rg.x + j + 1;
+        last[k] = pos0 + (b0 - rg.x) + j + 1;
       }
     }
   }
-  const int64_t hw = (int64_t)cam.width * cam.height;
+  // after the first part: a tile whose pixels have all stopped is final;
+  // any other keeps its state for the second pass
+  bool mine = true;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) mine = mine && done[k];
+  const bool final_out = args.phase == 1 || __syncthreads_and(mine);
+  if (args.phase == 0 && threadIdx.x == 0) args.unsat[gt] = final_out ? 0 : 1;
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     const int y = ty * TILE + S::py(threadIdx.x, k);
     if (!(x < cam.width && y < cam.height)) continue;
     const int64_t pix = cam.pix_base + (int64_t)y * cam.width + x;
     float* img = args.images + 3 * cam.pix_base + (int64_t)y * cam.width + x;
-    img[0] = fmaf(T[k], args.bg0, C[k][0]);
-    img[hw] = fmaf(T[k], args.bg1, C[k][1]);
-    img[2 * hw] = fmaf(T[k], args.bg2, C[k][2]);
+    if (final_out) {
+      img[0] = fmaf(T[k], args.bg0, C[k][0]);
+      img[hw] = fmaf(T[k], args.bg1, C[k][1]);
+      img[2 * hw] = fmaf(T[k], args.bg2, C[k][2]);
+      args.ncontrib[pix] = last[k];
+    } else {
+      img[0] = C[k][0];
+      img[hw] = C[k][1];
+      img[2 * hw] = C[k][2];
+      args.ncontrib[pix] = last[k] | (done[k] ? 0x80000000u : 0u);
+    }
     args.tfinal[pix] = T[k];
-    args.ncontrib[pix] = last[k];
   }
 }
 
@@ -242,18 +278,26 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const Bl
   __shared__ uint32_t sSlot[BATCH];
   __shared__ float part[NW][BATCH][9];
   __shared__ uint32_t s_maxc;
+  __shared__ uint32_t s_list[3];  // first part's start and length, second part's start
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t gt = blockIdx.x;
   const int v = find_view(args.views, args.n_views, gt);
   const ViewInfo& cam = args.views[v];
   const int64_t lt = gt - cam.tile_base;
   const int tx = (int)(lt % cam.tiles_x), ty = (int)(lt / cam.tiles_x);
-  const uint2 rg = args.ranges[gt];
   const int64_t hw = (int64_t)cam.width * cam.height;
   const int x = tx * TILE + S::px(threadIdx.x);
   const float pxc = (float)x + 0.5f;
   PixelBwd<PPT> px;
-  if (threadIdx.x == 0) s_maxc = 0;
+  if (threadIdx.x == 0) {
+    s_maxc = 0;
+    // the tile's list: the nearest records' part, then (for tiles the first
+    // forward pass left unfinished) the rest
+    const uint2 rg = args.ranges[gt];
+    s_list[0] = rg.x;
+    s_list[1] = rg.y - rg.x;
+    s_list[2] = args.ranges_b[gt].x;
+  }
   __syncthreads();
   uint32_t my_max = 0;
 #pragma unroll
@@ -285,13 +329,15 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const Bl
   const uint32_t warp_max = __reduce_max_sync(0xffffffffu, my_max);
   __syncthreads();
   const uint32_t maxc = s_maxc;
-  // batches from the back: [b0, b1)
-  for (int64_t b1 = (int64_t)rg.x + maxc; b1 > (int64_t)rg.x; b1 -= BATCH) {
-    const int64_t b0 = max((int64_t)rg.x, b1 - BATCH);
+  // batches of list positions from the back: [b0, b1)
+  for (int64_t b1 = maxc; b1 > 0; b1 -= BATCH) {
+    const int64_t b0 = max((int64_t)0, b1 - BATCH);
     const int n_in = (int)(b1 - b0);
     __syncthreads();
     for (int j = threadIdx.x; j < n_in; j += NT) {
-      const uint64_t key = args.pairs[b0 + j];
+      // list position b0 + j: in the first part, or in the second after it
+      const uint32_t p = (uint32_t)(b0 + j), len_a = s_list[1];
+      const uint64_t key = p < len_a ? args.pairs[s_list[0] + p] : args.pairs_b[s_list[2] + (p - len_a)];
       const uint32_t rec = key_rec(key);
       sA[j] = args.geo[2 * (size_t)rec];
       sB[j] = args.geo[2 * (size_t)rec + 1];
@@ -299,7 +345,7 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const Bl
       sSlot[j] = args.offrec[rec] + key_rank(key);
     }
     __syncthreads();
-    const uint32_t pos0 = (uint32_t)(b0 - rg.x);
+    const uint32_t pos0 = (uint32_t)b0;
     // first batch entry this warp must walk: positions < warp_max
     const int j_top = (int)max((int64_t)-1, min((int64_t)n_in, (int64_t)warp_max - (int64_t)pos0) - 1);
     for (int i = lane; i < (n_in - 1 - j_top) * 9; i += 32) part[wid][j_top + 1 + i / 9][i % 9] = 0.0f;
@@ -384,8 +430,12 @@ static BlendArgs blend_args(const Layout& L, void* ws, const float bg[3]) {
   BlendArgs a;
   a.views = ws_ptr<ViewInfo>(ws, L.views);
   a.n_views = L.n_views;
+  a.phase = 0;
   a.ranges = ws_ptr<uint2>(ws, L.ranges);
   a.pairs = sorted_pairs(ws, L);
+  a.ranges_b = ws_ptr<uint2>(ws, L.ranges_b);
+  a.pairs_b = sorted_pairs_b(ws, L);
+  a.unsat = ws_ptr<uint8_t>(ws, L.unsat);
   a.geo = ws_ptr<float4>(ws, L.geo);
   a.rgbm = ws_ptr<float4>(ws, L.rgbm);
   a.offrec = ws_ptr<uint32_t>(ws, L.offrec);
@@ -410,11 +460,12 @@ bool blend_ppt_ok(int tile, int ppt) {
 }
 
 cudaError_t launch_blend_fwd(const Layout& L, void* ws, int tile, int batch, int ppt, const float bg[3],
-                             float* images, cudaStream_t s) {
+                             float* images, int phase, cudaStream_t s) {
   if (L.T <= 0) return cudaSuccess;
   const dim3 grid((unsigned)L.T);
   BlendArgs a = blend_args(L, ws, bg);
   a.images = images;
+  a.phase = phase;
   if (tile == 8 && ppt == 1) return fwd_batch<8, 1>(batch, grid, s, a);
   if (tile == 8 && ppt == 2) return fwd_batch<8, 2>(batch, grid, s, a);
   if (tile == 16 && ppt == 1) return fwd_batch<16, 1>(batch, grid, s, a);

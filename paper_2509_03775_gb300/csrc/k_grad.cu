@@ -666,9 +666,9 @@ __global__ void __launch_bounds__(256) k_sh_rows(const uint32_t* __restrict__ st
 // (and the cache key); marks the cache stale on any difference and updates
 // the copy.
 __global__ void __launch_bounds__(256) k_csr_check(const uint16_t* __restrict__ idx, uint16_t* __restrict__ copy,
-                                                   int64_t n, int k, CsrState* cs) {
+                                                   int64_t n, int k, CsrState* cs, const uint64_t* epoch) {
   bool diff = cs->magic != kCsrMagic || cs->idx_ptr != (uint64_t)(uintptr_t)idx || cs->k != (uint32_t)k ||
-              cs->n != (uint32_t)n;
+              cs->n != (uint32_t)n || cs->epoch != *epoch;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t done = 0;
@@ -696,11 +696,13 @@ __global__ void __launch_bounds__(256) k_csr_check(const uint16_t* __restrict__ 
 }
 
 // Records the chunk count and the key of a new build; clears the flag.
-__global__ void k_csr_done(CsrState* cs, const uint64_t* nchunks_dev, const uint16_t* idx, int64_t n, int k) {
+__global__ void k_csr_done(CsrState* cs, const uint64_t* nchunks_dev, const uint16_t* idx, int64_t n, int k,
+                           const uint64_t* epoch) {
   if (!cs->changed) return;
   cs->appends = cs->changed == 2u ? cs->appends + 1u : 0u;  // counts appends since the last rebuild
   cs->nchunks = *nchunks_dev;
   cs->magic = kCsrMagic;
+  cs->epoch = *epoch;
   cs->idx_ptr = (uint64_t)(uintptr_t)idx;
   cs->k = (uint32_t)k;
   cs->n = (uint32_t)n;
@@ -720,7 +722,8 @@ static cudaError_t build_csr(void* ws, const Layout& L, const uint16_t* idx, uin
   uint64_t* k1 = ws_ptr<uint64_t>(ws, L.csr_keys1);
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
   const int gk = std::max(1, std::min((2 * k + 255) / 256, 152 * 8));
-  count_launch(), k_csr_check<<<g, 256, 0, s>>>(idx, copy, n, k, cs);
+  const uint64_t* epoch = &ws_ptr<WsHeader>(ws, L.hdr)->epoch;
+  count_launch(), k_csr_check<<<g, 256, 0, s>>>(idx, copy, n, k, cs, epoch);
   count_launch(), k_zero_counts<<<gk, 256, 0, s>>>(start, 2 * (int64_t)k, cs);
   count_launch(), k_row_keys<<<g, 256, 0, s>>>(idx, n, k, k0, &st->red_a, cs);
   bool in_b = false;
@@ -731,7 +734,7 @@ static cudaError_t build_csr(void* ws, const Layout& L, const uint16_t* idx, uin
   e = scan_u32(ws, L, cbase, cbase, &st->red_b, k, &st->red_a, s);  // red_a <- chunk count
   if (e != cudaSuccess) return e;
   count_launch(), k_fill_chunks<<<gk, 256, 0, s>>>(start, end, cbase, k, chunks, cs);
-  count_launch(), k_csr_done<<<1, 1, 0, s>>>(cs, &st->red_a, idx, n, k);
+  count_launch(), k_csr_done<<<1, 1, 0, s>>>(cs, &st->red_a, idx, n, k, epoch);
   return cudaGetLastError();
 }
 
@@ -747,9 +750,10 @@ static cudaError_t build_csr(void* ws, const Layout& L, const uint16_t* idx, uin
 // rebuilt.  cs->changed: bit 0 full rebuild, bit 1 append.
 
 __global__ void __launch_bounds__(256) k_csr_check_append(const uint16_t* __restrict__ idx, uint16_t* __restrict__ copy,
-                                                          int64_t n_old, int64_t n, int k, CsrState* cs) {
+                                                          int64_t n_old, int64_t n, int k, CsrState* cs,
+                                                          const uint64_t* epoch) {
   bool full = cs->magic != kCsrMagic || cs->idx_ptr != (uint64_t)(uintptr_t)idx || cs->k != (uint32_t)k ||
-              cs->n != (uint32_t)n_old || n_old >= n;
+              cs->n != (uint32_t)n_old || cs->epoch != *epoch || n_old >= n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += stride) {
     const uint16_t v = idx[g];
@@ -980,7 +984,8 @@ static cudaError_t append_csr(void* ws, const Layout& L, const uint16_t* idx, ui
   uint32_t* tmp = t_old + 4 * K1;
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
   const int gk = std::max(1, std::min((2 * k + 255) / 256, 152 * 8));
-  count_launch(), k_csr_check_append<<<g, 256, 0, s>>>(idx, copy, n_old, n, k, cs);
+  const uint64_t* epoch = &ws_ptr<WsHeader>(ws, L.hdr)->epoch;
+  count_launch(), k_csr_check_append<<<g, 256, 0, s>>>(idx, copy, n_old, n, k, cs, epoch);
   count_launch(), k_zero_counts<<<gk, 256, 0, s>>>(start, 2 * (int64_t)k, cs);
   count_launch(), k_row_keys<<<g, 256, 0, s>>>(idx, n, k, k0, &st->red_a, cs);
   count_launch(), k_app_keys<<<g, 256, 0, s>>>(idx, n_old, n, k, k0, &st->red_a, cs);
@@ -1002,7 +1007,7 @@ static cudaError_t append_csr(void* ws, const Layout& L, const uint16_t* idx, ui
   e = scan_u32(ws, L, cbase, cbase, &st->red_b, k, &st->red_a, s);
   if (e != cudaSuccess) return e;
   count_launch(), k_fill_chunks<<<gk, 256, 0, s>>>(start, end, cbase, k, chunks, cs);
-  count_launch(), k_csr_done<<<1, 1, 0, s>>>(cs, &st->red_a, idx, n, k);
+  count_launch(), k_csr_done<<<1, 1, 0, s>>>(cs, &st->red_a, idx, n, k, epoch);
   return cudaGetLastError();
 }
 

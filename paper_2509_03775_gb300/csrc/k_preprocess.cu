@@ -12,7 +12,21 @@ __global__ void k_setup(const __grid_constant__ ViewTable table, const __grid_co
   WsHeader* hdr = ws_ptr<WsHeader>(ws, L.hdr);
   ViewInfo* views = ws_ptr<ViewInfo>(ws, L.views);
   for (int i = threadIdx.x; i < table.n_views; i += blockDim.x) views[i] = table.v[i];
+  // a new epoch unless the header holds this library's record of the same
+  // layout: the next value after a layout change, a value from the global
+  // nanosecond timer when the header was not written by this library
+  static_assert(sizeof(Layout) % 4 == 0, "layout compared as words");
+  const uint32_t* a = reinterpret_cast<const uint32_t*>(&hdr->layout);
+  const uint32_t* b = reinterpret_cast<const uint32_t*>(&L);
+  bool differs = false;
+  for (int i = threadIdx.x; i < (int)(sizeof(Layout) / 4); i += blockDim.x) differs = differs || a[i] != b[i];
+  const bool same = !__syncthreads_or(differs) && hdr->magic == kMagic;
   if (threadIdx.x == 0) {
+    if (!same) {
+      uint64_t t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      hdr->epoch = hdr->magic == kMagic ? hdr->epoch + 1 : (t | 1ull);
+    }
     hdr->magic = kMagic;
     hdr->layout = L;
     DeviceState st = {};

@@ -402,10 +402,16 @@ struct TileRec {
   float rw;       // 1 / rectangle width
   uint32_t r01;   // x0 | y0 << 16
   uint32_t r23;   // x1 | y1 << 16
+  uint32_t tb;    // first global tile of the record's view
+  uint32_t tx;    // tiles per row of that view
 };
 
 __device__ __forceinline__ void stage_record(TileRec& t, const float4* __restrict__ geo,
-                                             const ushort4* __restrict__ rect, uint32_t rec) {
+                                             const ushort4* __restrict__ rect, const ViewInfo* __restrict__ views,
+                                             int64_t n, uint32_t rec) {
+  const ViewInfo& cam = views[rec / (uint32_t)n];
+  t.tb = (uint32_t)cam.tile_base;
+  t.tx = (uint32_t)cam.tiles_x;
   const ushort4 r = rect[rec];
   t.a = geo[2 * (size_t)rec];
   const float4 gb = geo[2 * (size_t)rec + 1];
@@ -427,43 +433,111 @@ __device__ __forceinline__ bool tile_decide(const TileRec& t, float pmax) {
   return t.b.y * exp32(x) >= kAlphaMin;
 }
 
+// The tile lists are built in two parts.  The first holds the pairs of the
+// nearest tenth of the visible records (depth order); after the forward has
+// composited it, a tile none of whose pixels is still compositing is final.
+// The second holds the pairs of the other records, for the unfinished tiles
+// only.  A tile's list is its first part followed by its second: exactly the
+// depth-ordered list of every record, cut where no pixel can still use it.
+__device__ __forceinline__ int64_t list_cut(int64_t vis) { return (vis + 9) / 10; }
+
+// Per view, the 2D inclusive prefix sums of the unfinished-tile flags:
+// sat[(y + 1) (tiles_x + 1) + x + 1] = unfinished tiles in [0, x] x [0, y]
+// (row and column 0 are 0).  One block per view.
+__global__ void k_unsat_sat(const ViewInfo* __restrict__ views, const uint8_t* __restrict__ unsat,
+                            uint32_t* __restrict__ sat) {
+  const ViewInfo& cam = views[blockIdx.x];
+  const int tx = cam.tiles_x, ty = cam.tiles_y, W = tx + 1;
+  uint32_t* S = sat + cam.sat_base;
+  const uint8_t* u = unsat + cam.tile_base;
+  for (int x = threadIdx.x; x < W; x += blockDim.x) S[x] = 0u;
+  for (int r = threadIdx.x; r < ty; r += blockDim.x) {
+    uint32_t acc = 0;
+    S[(int64_t)(r + 1) * W] = 0u;
+    for (int x = 0; x < tx; ++x) {
+      acc += u[(int64_t)r * tx + x];
+      S[(int64_t)(r + 1) * W + x + 1] = acc;
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < W; c += blockDim.x) {
+    uint32_t acc = 0;
+    for (int r = 1; r <= ty; ++r) {
+      acc += S[(int64_t)r * W + c];
+      S[(int64_t)r * W + c] = acc;
+    }
+  }
+}
+
+// Unfinished tiles inside a record's rectangle [x0, x1) x [y0, y1).
+__device__ __forceinline__ uint32_t unsat_in_rect(const uint32_t* __restrict__ sat, const ViewInfo& cam,
+                                                  const ushort4 r) {
+  const uint32_t* S = sat + cam.sat_base;
+  const int64_t W = cam.tiles_x + 1;
+  return S[r.w * W + r.z] - S[r.y * W + r.z] - S[r.w * W + r.x] + S[r.y * W + r.x];
+}
+
+// Depth-order index range [lo, hi) of the records of a list part.
+__device__ __forceinline__ void part_range(const DeviceState* st, int64_t R, int part, int64_t& lo, int64_t& hi) {
+  const int64_t vis = min((int64_t)st->visible, R);
+  const int64_t cut = list_cut(vis);
+  lo = part == 0 ? 0 : cut;
+  hi = part == 0 ? cut : vis;
+}
+
 // Kept tiles of each depth-ordered record (tile_keep over the record's
 // rectangle).  A warp takes 32 consecutive records and lays their rectangle
 // tiles end to end (an exclusive prefix of the tile counts); its lanes then
 // test 32 consecutive tiles of that list at a time, whatever record they
 // belong to, so every lane has work until the warp's list ends.  The record
 // of each lane comes from one OR-reduction of the bits of the records that
-// start inside the 32-tile window (every visible record has at least one
-// tile, so starts are distinct): lane l belongs to the window's first record
-// plus the number of starts at or below l.  Each record's kept tiles of a
-// window are counted by the first lane of its run; records of at most 64
-// tiles also collect their kept-tile bits for the emit pass.  Writes the
-// count per record, in depth order, and the sum of each group of 32 records
-// (the input of the offset scan).
+// start inside the 32-tile window (records with tiles to test are packed
+// into slots and each has at least one tile, so starts are distinct): lane
+// l belongs to the window's first record plus the number of starts at or
+// below l.  Each record's kept tiles of a window are counted by the first
+// lane of its run; records of at most 64 tiles also collect their kept-tile
+// bits for the emit pass.  Writes the count per record, in depth order, and
+// the sum of each group of 32 records (the input of the offset scan).  In
+// the second list part only tiles the first forward pass left unfinished are
+// kept, and a record whose rectangle holds none of them (per-view prefix
+// sums of the unfinished flags) tests no tile at all.
 __global__ void __launch_bounds__(256) k_count_emit(const uint64_t* __restrict__ dkeys,
                                                     const float4* __restrict__ geo,
-                                                    const ushort4* __restrict__ rect, int64_t R, int tile,
+                                                    const ushort4* __restrict__ rect,
+                                                    const ViewInfo* __restrict__ views, int64_t n, int64_t R,
+                                                    int tile, int part, const uint8_t* __restrict__ unsat,
+                                                    const uint32_t* __restrict__ sat,
                                                     uint32_t* __restrict__ nemit, uint32_t* __restrict__ counts,
-                                                    uint64_t* __restrict__ kmask, const uint64_t* visible_dev,
+                                                    uint64_t* __restrict__ kmask, const DeviceState* state,
                                                     uint32_t* __restrict__ gsum, uint64_t* ngroups) {
   __shared__ TileRec st[8][32];
   __shared__ uint32_t sPre[8][32];
   __shared__ uint32_t sCnt[8][32];
   __shared__ uint64_t sMask[8][32];
-  const int64_t vis = min((int64_t)*visible_dev, R);
+  int64_t lo, hi;
+  part_range(state, R, part, lo, hi);
+  const int64_t cnt = hi - lo;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t upto = lane == 31 ? 0xffffffffu : (2u << lane) - 1u;  // bits 0..lane
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = warp * 32; base < vis; base += nwarps * 32) {
-    const int64_t i = base + lane;
-    uint32_t rec = 0, nt = 0;
-    if (i < vis) {
-      rec = (uint32_t)dkeys[i];
-      stage_record(st[wid][lane], geo, rect, rec);
-      const TileRec& t = st[wid][lane];
-      nt = ((t.r23 & 0xffffu) - (t.r01 & 0xffffu)) * ((t.r23 >> 16) - (t.r01 >> 16));
+  for (int64_t base = warp * 32; base < cnt; base += nwarps * 32) {
+    const int64_t i = base + lane;   // index within the part; depth-order index lo + i
+    uint32_t rec = 0, area = 0, nt = 0;
+    if (i < cnt) {
+      rec = (uint32_t)dkeys[lo + i];
+      const ushort4 r = rect[rec];
+      area = ((uint32_t)r.z - r.x) * ((uint32_t)r.w - r.y);
+      nt = area;
+      // second part: a rectangle without unfinished tiles lists nothing
+      if (part == 1 && unsat_in_rect(sat, views[rec / (uint32_t)n], r) == 0u) nt = 0;
     }
+    // the records with tiles to test, packed in lane order into slots
+    // 0, 1, ... (every one of them has at least one tile, so their starts in
+    // the laid-out list are distinct)
+    const bool has = nt > 0;
+    const uint32_t slot = (uint32_t)__popc(__ballot_sync(0xffffffffu, has) & ((1u << lane) - 1u));
+    if (has) stage_record(st[wid][slot], geo, rect, views, n, rec);
     uint32_t incl = nt;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -471,11 +545,12 @@ __global__ void __launch_bounds__(256) k_count_emit(const uint64_t* __restrict__
       if (lane >= d) incl += up;
     }
     const uint32_t my_start = incl - nt;
-    sPre[wid][lane] = my_start;
-    sCnt[wid][lane] = 0;
-    sMask[wid][lane] = 0ull;
+    if (has) {
+      sPre[wid][slot] = my_start;
+      sCnt[wid][slot] = 0;
+      sMask[wid][slot] = 0ull;
+    }
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    const bool has = i < vis;  // records past the end have no tiles and start nowhere
     __syncwarp();
     int q0 = 0;  // the record holding list position c0 (warp-uniform)
     for (uint32_t c0 = 0; c0 < total; c0 += 32) {
@@ -492,7 +567,8 @@ __global__ void __launch_bounds__(256) k_count_emit(const uint64_t* __restrict__
         const int x0 = (int)(t.r01 & 0xffffu), y0 = (int)(t.r01 >> 16);
         const int w = (int)(t.r23 & 0xffffu) - x0;
         const int yy = (int)(((float)k + 0.5f) * t.rw), xx = k - yy * w;
-        keep = tile_decide(t, tile_pmax(t.a.x, t.a.y, t.a.z, t.a.w, t.b.x, t.b.z, t.b.w, x0 + xx, y0 + yy, tile));
+        keep = (part == 0 || unsat[t.tb + (uint32_t)(y0 + yy) * t.tx + (uint32_t)(x0 + xx)] != 0) &&
+               tile_decide(t, tile_pmax(t.a.x, t.a.y, t.a.z, t.a.w, t.b.x, t.b.z, t.b.w, x0 + xx, y0 + yy, tile));
       }
       const uint32_t m = __ballot_sync(0xffffffffu, keep);
       // runs of lanes with one record begin at lane 0 and at every start
@@ -511,26 +587,36 @@ __global__ void __launch_bounds__(256) k_count_emit(const uint64_t* __restrict__
       __syncwarp();
     }
     uint32_t c = 0;
-    if (i < vis) {
-      c = sCnt[wid][lane];
+    if (i < cnt) {
+      c = has ? sCnt[wid][slot] : 0u;
       nemit[rec] = c;
-      counts[i] = c;
-      if (nt <= 64u) kmask[rec] = sMask[wid][lane];  // the emit pass reuses the decisions
+      counts[lo + i] = c;
+      if (area <= 64u) kmask[rec] = has ? sMask[wid][slot] : 0ull;  // the emit pass reuses the decisions
     }
     const uint32_t gs = __reduce_add_sync(0xffffffffu, c);
     if (lane == 0) gsum[base >> 5] = gs;
     __syncwarp();
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *ngroups = (uint64_t)((vis + 31) / 32);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *ngroups = (uint64_t)((cnt + 31) / 32);
 }
 
-__global__ void k_capacity(DeviceState* st, int64_t cap) {
+// After each part's offset scan (total in scan_total): the part's pair
+// count, the running total and the capacity check (slots of both parts share
+// one array of cap entries).
+__global__ void k_capacity(DeviceState* st, int64_t cap, int part) {
   const uint64_t k = st->scan_total;
-  st->pairs = k;
-  const bool ok = k <= (uint64_t)cap;
-  st->pairs_ok = ok ? 1u : 0u;
+  if (part == 0) {
+    st->pairs_a = k;
+    st->pairs_b = 0;
+    st->pairs = k;
+    st->pairs_ok = k <= (uint64_t)cap ? 1u : 0u;
+  } else {
+    st->pairs_b = k;
+    st->pairs = st->pairs_a + k;
+    st->pairs_ok = st->pairs_ok != 0u && st->pairs <= (uint64_t)cap ? 1u : 0u;
+  }
   st->pad = 0;
-  if (!ok) set_status(st, CG_ERR_CAPACITY, 0);
+  if (!st->pairs_ok) set_status(st, CG_ERR_CAPACITY, 0);
 }
 
 // Pairs of one record in depth order: its kept tiles (tile_keep) in
@@ -549,7 +635,8 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__
                                                     const uint32_t* __restrict__ gbase,
                                                     const float4* __restrict__ geo,
                                                     const ushort4* __restrict__ rect,
-                                                    const ViewInfo* __restrict__ views, int64_t n, int tile,
+                                                    const ViewInfo* __restrict__ views, int64_t n, int64_t R,
+                                                    int tile, int part, const uint8_t* __restrict__ unsat,
                                                     const uint64_t* __restrict__ kmask,
                                                     uint32_t* __restrict__ offrec, uint64_t* __restrict__ pairs,
                                                     uint8_t* __restrict__ pairlive, const DeviceState* state) {
@@ -559,31 +646,37 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__
   __shared__ int64_t sTB[8][32];     // first global tile of the record's view
   __shared__ int sTX[8][32];         // tiles per row of that view
   __shared__ float sRW[8][32];       // 1 / rectangle width
-  const int64_t vis = (int64_t)state->visible;
+  __shared__ uint32_t sCount[8][32];  // kept tiles of the record
+  int64_t lo, hi;
+  part_range(state, R, part, lo, hi);
+  const int64_t cnt = hi - lo;
+  // slots of the second part follow the first part's
+  const uint32_t slot0 = part == 0 ? 0u : (uint32_t)state->pairs_a;
   const bool ok = state->pairs_ok != 0;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = warp * 32; base < vis; base += nwarps * 32) {
-    const int64_t i = base + lane;
-    // the record's first slot: its group's offset plus the counts of the
+  for (int64_t base = warp * 32; base < cnt; base += nwarps * 32) {
+    const int64_t i = base + lane;   // index within the part
+    // the record's first pair: its group's offset plus the counts of the
     // lanes before it
-    const uint32_t c = i < vis ? counts[i] : 0u;
+    const uint32_t c = i < cnt ? counts[lo + i] : 0u;
     uint32_t incl = c;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const uint32_t up = __shfl_up_sync(0xffffffffu, incl, d);
       if (lane >= d) incl += up;
     }
-    if (i < vis) {
-      const uint32_t rec = (uint32_t)dkeys[i];
+    sCount[wid][lane] = c;
+    if (i < cnt) {
+      const uint32_t rec = (uint32_t)dkeys[lo + i];
       const uint32_t off = gbase[base >> 5] + incl - c;
-      offrec[rec] = off;
+      offrec[rec] = slot0 + off;
       const ushort4 r = rect[rec];
       const int w = (int)r.z - (int)r.x, h = (int)r.w - (int)r.y;
       if (w * h > 64) {
-        stage_record(st[wid][lane], geo, rect, rec);
+        stage_record(st[wid][lane], geo, rect, views, n, rec);
       } else {
         sMask[wid][lane] = kmask[rec];
         sRW[wid][lane] = 1.0f / (float)max(1, w);
@@ -594,9 +687,10 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__
       sTX[wid][lane] = cam.tiles_x;
     }
     __syncwarp();
-    const int nrec = (int)min((int64_t)32, vis - base);
+    const int nrec = (int)min((int64_t)32, cnt - base);
     if (ok) {
       for (int q = 0; q < nrec; ++q) {
+        if (sCount[wid][q] == 0) continue;  // no kept tile (often, in the second part)
         const uint4 inf = sInfo[wid][q];
         const int x0 = (int)(inf.z & 0xffffu), y0 = (int)(inf.z >> 16);
         const int w = (int)(inf.w & 0xffffu), total = w * (int)(inf.w >> 16);
@@ -615,7 +709,7 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__
               const uint32_t rank = (half == 0 ? 0u : (uint32_t)__popc(lo)) + (uint32_t)__popc(bits & lt_mask);
               const int yy = (int)(((float)k + 0.5f) * rw), xx = k - yy * w;
               pairs[inf.y + rank] = pair_key((uint64_t)(tb + (int64_t)(y0 + yy) * tx + (x0 + xx)), rank, inf.x);
-              pairlive[inf.y + rank] = 0;
+              pairlive[slot0 + inf.y + rank] = 0;
             }
           }
         } else {
@@ -628,13 +722,14 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint64_t* __restrict__
             if (k < total) {
               yy = (int)(((float)k + 0.5f) * t.rw);
               xx = k - yy * w;
-              keep = tile_decide(t, tile_pmax(t.a.x, t.a.y, t.a.z, t.a.w, t.b.x, t.b.z, t.b.w, x0 + xx, y0 + yy, tile));
+              keep = (part == 0 || unsat[tb + (int64_t)(y0 + yy) * tx + (x0 + xx)] != 0) &&
+                     tile_decide(t, tile_pmax(t.a.x, t.a.y, t.a.z, t.a.w, t.b.x, t.b.z, t.b.w, x0 + xx, y0 + yy, tile));
             }
             const uint32_t mk = __ballot_sync(0xffffffffu, keep);
             if (keep) {
               const uint32_t rank = rank0 + __popc(mk & lt_mask);
               pairs[inf.y + rank] = pair_key((uint64_t)(tb + (int64_t)(y0 + yy) * tx + (x0 + xx)), rank, inf.x);
-              pairlive[inf.y + rank] = 0;
+              pairlive[slot0 + inf.y + rank] = 0;
             }
             rank0 += __popc(mk);
           }
@@ -654,8 +749,8 @@ __global__ void k_zero_u32(uint32_t* p, int64_t count) {
 // 4t .. 4t + 3 with two 16-byte loads; the neighbouring keys come from the
 // adjacent lanes (the warp's first and last lanes read them directly).
 __global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ pairs, uint2* __restrict__ ranges,
-                                                const DeviceState* st) {
-  const int64_t k = st->pairs_ok ? (int64_t)st->pairs : 0;
+                                                const uint64_t* count_dev, const DeviceState* st) {
+  const int64_t k = st->pairs_ok ? (int64_t)*count_dev : 0;
   const int lane = threadIdx.x & 31;
   const int64_t groups = (k + 3) / 4;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -692,7 +787,7 @@ __global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ pai
   }
 }
 
-cudaError_t launch_build_pairs(const Layout& L, void* ws, int tile_bits, cudaStream_t s) {
+cudaError_t launch_build_lists(const Layout& L, void* ws, int part, cudaStream_t s) {
   WsHeader* hdr = ws_ptr<WsHeader>(ws, L.hdr);
   DeviceState* st = &hdr->st;
   const uint32_t* ntiles = ws_ptr<uint32_t>(ws, L.ntiles);
@@ -704,44 +799,52 @@ cudaError_t launch_build_pairs(const Layout& L, void* ws, int tile_bits, cudaStr
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>((R + 255) / 256, kGrid));
   uint32_t* gsum = ws_ptr<uint32_t>(ws, L.gsum);
   const int64_t G = (R + 31) / 32;
-  // 1. compact visible records, keyed by FP32 depth bits (record index low)
-  count_launch(), k_visible_groups<<<g, 256, 0, s>>>(ntiles, gsum, R, &st->red_a);
-  cudaError_t e = scan_u32(ws, L, gsum, gsum, &st->red_a, G, &st->visible, s);
-  if (e != cudaSuccess) return e;
-  count_launch(), k_compact_depth<<<g, 256, 0, s>>>(ntiles, depth, gsum, dk0, R);
-  // 2. stable sort by depth (records in index order for equal depth)
+  cudaError_t e = cudaSuccess;
   bool in_b = false;
-  e = sort_u64(ws, L, dk0, dk1, &st->visible, R, 32, 32, &in_b, s);
-  if (e != cudaSuccess) return e;
-  const uint64_t* dsorted = in_b ? dk1 : dk0;
-  if (dsorted != depth_sorted(ws, L)) return cudaErrorInvalidValue;
-  // 3. kept tiles per record, pair offsets of the groups of 32 records in
-  //    depth order, total pair count and capacity check
+  if (part == 0) {
+    // 1. compact visible records, keyed by FP32 depth bits (record index low)
+    count_launch(), k_visible_groups<<<g, 256, 0, s>>>(ntiles, gsum, R, &st->red_a);
+    e = scan_u32(ws, L, gsum, gsum, &st->red_a, G, &st->visible, s);
+    if (e != cudaSuccess) return e;
+    count_launch(), k_compact_depth<<<g, 256, 0, s>>>(ntiles, depth, gsum, dk0, R);
+    // 2. stable sort by depth (records in index order for equal depth)
+    e = sort_u64(ws, L, dk0, dk1, &st->visible, R, 32, 32, &in_b, s);
+    if (e != cudaSuccess) return e;
+    if ((in_b ? dk1 : dk0) != depth_sorted(ws, L)) return cudaErrorInvalidValue;
+  }
+  const uint64_t* dsorted = depth_sorted(ws, L);
+  const uint8_t* unsat = ws_ptr<uint8_t>(ws, L.unsat);
+  // 3. kept tiles per record of this part (second part: unfinished tiles
+  //    only), pair offsets of the groups of 32 records in depth order, the
+  //    part's pair count and the capacity check
+  uint32_t* sat = ws_ptr<uint32_t>(ws, L.sat);
+  if (part == 1) count_launch(), k_unsat_sat<<<L.n_views, 256, 0, s>>>(ws_ptr<ViewInfo>(ws, L.views), unsat, sat);
   count_launch(), k_count_emit<<<g, 256, 0, s>>>(dsorted, ws_ptr<const float4>(ws, L.geo),
-                                                 ws_ptr<const ushort4>(ws, L.rect), R, L.tile,
-                                                 ws_ptr<uint32_t>(ws, L.nemit), scan, ws_ptr<uint64_t>(ws, L.kmask),
-                                                 &st->visible, gsum, &st->red_b);
+                                                 ws_ptr<const ushort4>(ws, L.rect), ws_ptr<ViewInfo>(ws, L.views),
+                                                 L.n, R, L.tile, part, unsat, sat, ws_ptr<uint32_t>(ws, L.nemit), scan,
+                                                 ws_ptr<uint64_t>(ws, L.kmask), st, gsum, &st->red_b);
   e = scan_u32(ws, L, gsum, gsum, &st->red_b, G, &st->scan_total, s);
   if (e != cudaSuccess) return e;
-  count_launch(), k_capacity<<<1, 1, 0, s>>>(st, L.Kc);
-  // 4. emit pairs in depth order
-  uint64_t* p0 = ws_ptr<uint64_t>(ws, L.pairs0);
-  uint64_t* p1 = ws_ptr<uint64_t>(ws, L.pairs1);
+  count_launch(), k_capacity<<<1, 1, 0, s>>>(st, L.Kc, part);
+  // 4. emit the part's pairs in depth order
+  uint64_t* p0 = ws_ptr<uint64_t>(ws, part == 0 ? L.pairs0 : L.pairs_b0);
+  uint64_t* p1 = ws_ptr<uint64_t>(ws, part == 0 ? L.pairs1 : L.pairs_b1);
   count_launch(), k_emit_pairs<<<g, 256, 0, s>>>(dsorted, scan, gsum, ws_ptr<const float4>(ws, L.geo),
                                                  ws_ptr<const ushort4>(ws, L.rect), ws_ptr<ViewInfo>(ws, L.views),
-                                                 L.n, L.tile, ws_ptr<const uint64_t>(ws, L.kmask),
+                                                 L.n, R, L.tile, part, unsat, ws_ptr<const uint64_t>(ws, L.kmask),
                                                  ws_ptr<uint32_t>(ws, L.offrec), p0, ws_ptr<uint8_t>(ws, L.pairlive), st);
   // 5. stable sort on the tile bits
-  e = sort_u64(ws, L, p0, p1, &st->pairs, L.Kc, kKeyTileShift, L.tile_bits, &in_b, s);
+  const uint64_t* count_dev = part == 0 ? &st->pairs_a : &st->pairs_b;
+  e = sort_u64(ws, L, p0, p1, count_dev, L.Kc, kKeyTileShift, L.tile_bits, &in_b, s);
   if (e != cudaSuccess) return e;
   const uint64_t* psorted = in_b ? p1 : p0;
-  if (psorted != sorted_pairs(ws, L)) return cudaErrorInvalidValue;
-  // 6. per-tile ranges
-  uint2* ranges = ws_ptr<uint2>(ws, L.ranges);
+  if (psorted != (part == 0 ? sorted_pairs(ws, L) : sorted_pairs_b(ws, L))) return cudaErrorInvalidValue;
+  // 6. per-tile ranges of the part
+  uint2* ranges = ws_ptr<uint2>(ws, part == 0 ? L.ranges : L.ranges_b);
   const int gt = (int)std::max<int64_t>(1, std::min<int64_t>((2 * L.T + 255) / 256, kGrid));
   count_launch(), k_zero_u32<<<gt, 256, 0, s>>>(reinterpret_cast<uint32_t*>(ranges), 2 * L.T);
   const int gk = (int)std::max<int64_t>(1, std::min<int64_t>((L.Kc / 4 + 255) / 256, kGrid));
-  count_launch(), k_ranges<<<gk, 256, 0, s>>>(psorted, ranges, st);
+  count_launch(), k_ranges<<<gk, 256, 0, s>>>(psorted, ranges, count_dev, st);
   return cudaGetLastError();
 }
 

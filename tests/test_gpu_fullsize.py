@@ -16,6 +16,7 @@ import pytest
 import torch
 
 import oracle
+import two_part_lists
 from paper_2509_03775_gb300 import cg, scenes
 
 pytestmark = pytest.mark.gpu
@@ -73,15 +74,13 @@ def _run(scene, cams, blocks, bf16=False, errors_key=None, check_grads=True):
     geo = r.array(cg.WS_GEO, torch.float32, 8).cpu().numpy().reshape(-1, 8)
     for j, f in enumerate(["mx", "my", "h0", "h1", "h2", "o"]):
         assert np.array_equal(geo[vis, j].view(np.uint32), q[f][vis].view(np.uint32)), f
-    # pairs and ranges of the sampled tiles
+    # the two parts of the sampled tiles' lists against the oracle's whole lists
     pairs = r.array(cg.WS_PAIRS, torch.int64).cpu().numpy().view(np.uint64)
     ranges = r.array(cg.WS_RANGES, torch.int32, 2).cpu().numpy().view(np.uint32).reshape(-1, 2)
+    pairs_b = r.array(cg.WS_PAIRS_B, torch.int64).cpu().numpy().view(np.uint64)
+    ranges_b = r.array(cg.WS_RANGES_B, torch.int32, 2).cpu().numpy().view(np.uint32).reshape(-1, 2)
     sel = np.nonzero(mask)[0]
-    for gt in sel:
-        b, e = ranges[gt]
-        ob, oe = ref.ranges[gt]
-        assert e - b == oe - ob, gt
-        assert np.array_equal((pairs[b:e] & np.uint64((1 << 26) - 1)).astype(np.uint32), ref.list[ob:oe]), gt
+    two_part_lists.check(ref, cams, pairs, ranges, pairs_b, ranges_b, tiles=sel)
     # pixels of the sampled tiles
     img_g = img.cpu().numpy().astype(np.float64)
     nc_g = r.array(cg.WS_NCONTRIB, torch.int32).cpu().numpy().view(np.uint32)

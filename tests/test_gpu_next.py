@@ -359,7 +359,7 @@ def test_growth_matches_oracle_and_membership_update_matches_rebuild():
     assert np.array_equal(g2sh.cpu().numpy().view(np.uint16), ref["g2sh"])
     grown = tensors(n + m)
     r.codebook_append(grown, n)                           # incremental update of the kept lists
-    state = r.array(cg.WS_CSR_STATE, torch.int32, 10).cpu().numpy().reshape(2, 10)
+    state = r.array(cg.WS_CSR_STATE, torch.int32, 12).cpu().numpy().reshape(2, 12)
     assert list(state[:, 7]) == [1, 1]                    # both lists were extended, not rebuilt
     assert list(state[:, 5]) == [n + m, n + m]
     got = grads(r, grown)

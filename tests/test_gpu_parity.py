@@ -12,6 +12,7 @@ import pytest
 import torch
 
 import oracle
+import two_part_lists
 from paper_2509_03775_gb300 import cg, scenes
 
 pytestmark = pytest.mark.gpu
@@ -35,6 +36,10 @@ def _run_gpu(scene, cams, d_image, tile=16, batch=0, bg=(0.0, 0.0, 0.0), bf16=Fa
         "depth": r.array(cg.WS_DEPTH, torch.int32).cpu().numpy().view(np.uint32),
         "pairs": r.array(cg.WS_PAIRS, torch.int64).cpu().numpy().view(np.uint64),
         "ranges": r.array(cg.WS_RANGES, torch.int32, 2).cpu().numpy().view(np.uint32).reshape(-1, 2),
+        "pairs_b": r.array(cg.WS_PAIRS_B, torch.int64).cpu().numpy().view(np.uint64),
+        "ranges_b": r.array(cg.WS_RANGES_B, torch.int32, 2).cpu().numpy().view(np.uint32).reshape(-1, 2),
+        "cams": cams,
+        "tile": tile,
         "ncontrib": r.array(cg.WS_NCONTRIB, torch.int32).cpu().numpy().view(np.uint32),
         "tfinal": r.array(cg.WS_TFINAL, torch.float32).cpu().numpy(),
         "geo": r.array(cg.WS_GEO, torch.float32, 8).cpu().numpy().reshape(-1, 8),
@@ -82,21 +87,23 @@ def _compare(ref, gpu, check_grads=True):
     for j, f in enumerate(["mx", "my", "h0", "h1", "h2", "o"]):
         assert np.array_equal(geo[vis, j].view(np.uint32), q[f][vis].view(np.uint32)), f
     assert np.array_equal(gpu["rgbm"][vis, 3].astype(np.uint32), q["rgb_clamped"][vis])
-    # sorted pairs and ranges
-    pairs = gpu["pairs"]
-    assert pairs.size == ref.k_pairs
+    # the two parts of the tile lists against the oracle's whole lists
+    na, nb, nfull = two_part_lists.check(ref, gpu["cams"], gpu["pairs"], gpu["ranges"], gpu["pairs_b"],
+                                         gpu["ranges_b"], tile=gpu["tile"])
+    assert nfull == ref.k_pairs and na == gpu["pairs"].size and nb == gpu["pairs_b"].size
+    for part in ("pairs", "pairs_b"):
+        tiles = gpu[part] >> np.uint64(43)
+        assert np.all(tiles[1:] >= tiles[:-1])                        # sorted by tile
+    pairs = np.concatenate([gpu["pairs"], gpu["pairs_b"]])
     tiles = pairs >> np.uint64(43)
     recs = (pairs & np.uint64((1 << 26) - 1)).astype(np.int64)
     ranks = ((pairs >> np.uint64(26)) & np.uint64((1 << 17) - 1)).astype(np.int64)
-    assert np.array_equal(tiles, ref.keys >> np.uint64(32))
-    assert np.array_equal(recs, ref.list.astype(np.int64))
     # rank = position of the tile among the record's listed tiles (row-major)
     order = np.lexsort((tiles, recs))
     r_sorted, k_sorted = recs[order], ranks[order]
     first = np.concatenate([[0], np.nonzero(np.diff(r_sorted))[0] + 1])
     expect = np.arange(r_sorted.size) - np.repeat(first, np.diff(np.concatenate([first, [r_sorted.size]])))
     assert np.array_equal(k_sorted, expect)
-    assert np.array_equal(gpu["ranges"], ref.ranges)
     # per-pixel outputs
     assert np.array_equal(gpu["ncontrib"], ref.n_contrib.astype(np.uint32))
     assert np.abs(gpu["tfinal"] - ref.t_final).max() < 1e-5

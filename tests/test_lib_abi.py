@@ -69,8 +69,9 @@ def test_workspace_bytes_and_argument_checks(lib):
     o.pair_capacity = 20000
     n2 = lib.cg_workspace_bytes(ctypes.byref(sc), camarr, 1, ctypes.byref(o))
     assert n1 > 0 and n2 > n1
-    # per extra pair: two sort buffers (16 B) + pair gradient (36 B) + sort histograms
-    assert 52 * 10000 <= n2 - n1 <= 54 * 10000 + 4096
+    # per extra pair: two sort buffers for each of the two list parts (32 B), the
+    # pair gradient (36 B) and its live flag (1 B), plus the sort histograms
+    assert 69 * 10000 <= n2 - n1 <= 71 * 10000 + 4096
     o.tile = 12
     assert lib.cg_workspace_bytes(ctypes.byref(sc), camarr, 1, ctypes.byref(o)) == 0
     o.tile = 16

@@ -1,0 +1,72 @@
+"""Checks the two-part tile lists of the CUDA path against the oracle's
+whole, depth-ordered tile lists (test helper, no GPU code).
+
+The first part lists the pairs of the nearest ceil(visible / 10) records (by
+FP32 depth bits, then record index); the second lists the other records'
+pairs, only in tiles where some pixel was still compositing after the first
+part.  A tile's list is its first part followed by its second, so it must be
+the oracle's list, cut only where every pixel of the tile had stopped."""
+import numpy as np
+
+REC_MASK = np.uint64((1 << 26) - 1)
+
+
+def depth_ranks(rec32):
+    """Depth-order rank of every visible record (-1 for the others)."""
+    vis = np.nonzero(rec32["visible"])[0]
+    order = np.lexsort((vis, rec32["depth_bits"][vis]))
+    rank = np.full(rec32.size, -1, dtype=np.int64)
+    rank[vis[order]] = np.arange(vis.size)
+    return rank, vis.size
+
+
+def tile_pixels(cams, tile=16):
+    """Global pixel indices of every global tile (list of arrays)."""
+    out = []
+    pix_base = 0
+    for c in cams:
+        tx, ty = -(-c.width // tile), -(-c.height // tile)
+        ys, xs = np.mgrid[0:c.height, 0:c.width]
+        gt = (ys // tile) * tx + xs // tile
+        order = np.argsort(gt.ravel(), kind="stable")
+        counts = np.bincount(gt.ravel(), minlength=tx * ty)
+        starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
+        for t in range(tx * ty):
+            out.append(pix_base + order[starts[t]:starts[t] + counts[t]])
+        pix_base += c.width * c.height
+    return out
+
+
+def check(ref, cams, pairs_a, ranges_a, pairs_b, ranges_b, tiles=None, tile=16):
+    """Asserts the two parts against the oracle's lists for the given global
+    tiles (all when None).  Returns (pairs in the first part, pairs in the
+    second, pairs the oracle lists) over those tiles."""
+    rank, vis = depth_ranks(ref.rec32)
+    cut = (vis + 9) // 10
+    pix = tile_pixels(cams, tile)
+    stop = ref.term_pos
+    tiles = range(ref.n_tiles) if tiles is None else tiles
+    na = nb = nfull = 0
+    for gt in tiles:
+        ob, oe = (int(v) for v in ref.ranges[gt])
+        full = ref.list[ob:oe].astype(np.int64)
+        first = rank[full] < cut
+        len_a = int(first.sum())
+        assert np.all(first[:len_a]) and not np.any(first[len_a:]), gt   # the nearest records come first
+        a0, a1 = (int(v) for v in ranges_a[gt])
+        got_a = (pairs_a[a0:a1] & REC_MASK).astype(np.int64)
+        assert np.array_equal(got_a, full[:len_a]), gt
+        assert np.all((pairs_a[a0:a1] >> np.uint64(43)) == gt), gt
+        st = stop[pix[gt]]
+        finished = bool(np.all((st >= 0) & (st < len_a)))
+        b0, b1 = (int(v) for v in ranges_b[gt])
+        got_b = (pairs_b[b0:b1] & REC_MASK).astype(np.int64)
+        if finished:
+            assert got_b.size == 0, gt
+        else:
+            assert np.array_equal(got_b, full[len_a:]), gt
+            assert np.all((pairs_b[b0:b1] >> np.uint64(43)) == gt), gt
+        na += got_a.size
+        nb += got_b.size
+        nfull += full.size
+    return na, nb, nfull
