@@ -49,12 +49,13 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # formed once per pair, not per pixel).
 FLOPS_PER_EVAL = {"blend_fwd": 21, "blend_bwd": 55}
 
-# DRAM bytes (read + write) per launch from one ncu capture of the kernel on
-# the named workload (summaries under profiles/), valid while the kernel's
-# source file hashes (SHA-256, first 16 hex digits) to `src`; null otherwise.
+# DRAM bytes (read + write) of the stage's launches in one step (the forward
+# blend runs twice, once per list part), from one ncu capture on the named
+# workload (summaries under profiles/), valid while the kernel's source file
+# hashes (SHA-256, first 16 hex digits) to `src`; null otherwise.
 NCU_TRAFFIC = {
-    "blend_bwd": {"bytes": 366160384 + 907180288, "src": "0cb74b4455c2c0ae", "workload": "truck"},
-    "blend_fwd": {"bytes": 26038784 + 976640, "src": "0cb74b4455c2c0ae", "workload": "truck"},
+    "blend_bwd": {"bytes": 70413568 + 15240960, "src": "b1f07903b48e8821", "workload": "truck"},
+    "blend_fwd": {"bytes": 18494976 + 496640 + 27984640 + 10752, "src": "b1f07903b48e8821", "workload": "truck"},
 }
 
 
