@@ -365,11 +365,16 @@ cg_status cg_grow(const cg_params *params, uint16_t *g2sr, uint16_t *g2sh, int m
  *   CG_WS_CSR_STATE   [2]  48 B       kept-membership record of the SR and SH codebooks:
  *                                     uint64 tag, uint64 index-array address, uint32 rows,
  *                                     uint32 Gaussians, uint32 pending flags, uint32 count of
- *                                     incremental updates, uint64 chunk count, uint64 epoch */
+ *                                     incremental updates, uint64 chunk count, uint64 epoch
+ *   CG_WS_TILE_ORDER  [T]   uint32    the global tiles in the order the backward launch takes
+ *                                     them: a permutation of [0, T), by decreasing work class
+ *                                     of the tile (quarter octaves of the tile's largest
+ *                                     position after the last contributor); written by the
+ *                                     forward */
 typedef enum {
   CG_WS_RECT = 0, CG_WS_DEPTH, CG_WS_PAIRS, CG_WS_RANGES, CG_WS_NCONTRIB, CG_WS_TFINAL,
   CG_WS_DSIGMA, CG_WS_DRGB, CG_WS_GEO, CG_WS_RGB, CG_WS_SIGMA3, CG_WS_CSR_STATE,
-  CG_WS_PAIRS_B, CG_WS_RANGES_B
+  CG_WS_PAIRS_B, CG_WS_RANGES_B, CG_WS_TILE_ORDER
 } cg_ws_array;
 cg_status cg_workspace_array(void *workspace, size_t ws_bytes, cg_ws_array which, void **ptr_out,
                              uint64_t *count_out);

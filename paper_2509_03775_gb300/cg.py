@@ -26,7 +26,7 @@ WS_HEADER_ZERO_BYTES = 4096   # a new workspace's leading bytes cleared before f
 MAX_VIEWS = 64
 
 WS_RECT, WS_DEPTH, WS_PAIRS, WS_RANGES, WS_NCONTRIB, WS_TFINAL, WS_DSIGMA, WS_DRGB, WS_GEO, WS_RGB, WS_SIGMA3, \
-    WS_CSR_STATE, WS_PAIRS_B, WS_RANGES_B = range(14)
+    WS_CSR_STATE, WS_PAIRS_B, WS_RANGES_B, WS_TILE_ORDER = range(15)
 
 # every symbol include/cg.h declares
 EXPORTS = ["cg_workspace_bytes", "cg_render_fwd", "cg_render_bwd", "cg_codebook_reduce", "cg_last_device_status",

@@ -161,6 +161,9 @@ cg_status plan(const cg_scene* s, const cg_camera* cams, int n_views, const cg_o
   L->ranges_b = take(sizeof(uint32_t) * 2 * T);
   L->unsat = take(sizeof(uint8_t) * T);
   L->sat = take(sizeof(uint32_t) * S);           // prefix sums of unfinished tiles per view
+  L->tile_bucket = take(sizeof(uint8_t) * T);    // backward work class of each tile
+  L->tile_order = take(sizeof(uint32_t) * T);     // a blend launch's tiles by decreasing work
+  L->tile_hist = take(sizeof(uint32_t) * 6 * kWorkBuckets);  // per order: tiles per class, cursors
   L->tfinal = take(sizeof(float) * P);
   L->ncontrib = take(sizeof(uint32_t) * P);
   L->pairgrad = take(sizeof(float4) * 2 * Kc);   // 8 sums per pair, one 32-byte sector
@@ -368,6 +371,7 @@ cg_status cg_workspace_array(void* workspace, size_t ws_bytes, cg_ws_array which
     case CG_WS_RGB: off = L.rgbm; cnt = L.R; break;
     case CG_WS_SIGMA3: off = L.sigma3; cnt = L.k_sr; break;
     case CG_WS_CSR_STATE: off = L.csr_state; cnt = 2; break;
+    case CG_WS_TILE_ORDER: off = L.tile_order; cnt = L.T; break;
     default: return CG_ERR_ARG;
   }
   *ptr_out = b + off;

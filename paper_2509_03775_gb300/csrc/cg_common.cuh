@@ -279,7 +279,7 @@ struct ViewTable {
 struct Layout {
   uint64_t total;
   uint64_t hdr, views, sigma3, geo, rgbm, rect, ntiles, depth, offrec, scan, dkeys0, dkeys1, pairs0, pairs1,
-      ranges, tfinal, ncontrib, pairgrad, pairgrad1, pairlive, recgrad, pairs_b0, pairs_b1, ranges_b, unsat, sat, nemit, kmask, dsigma, drgb, csr_keys0, csr_keys1, csr_off_sr, csr_off_sh, csr_ids_sr, csr_ids_sh, chunks, chunks_sh,
+      ranges, tfinal, ncontrib, pairgrad, pairgrad1, pairlive, recgrad, pairs_b0, pairs_b1, ranges_b, unsat, sat, tile_bucket, tile_order, tile_hist, nemit, kmask, dsigma, drgb, csr_keys0, csr_keys1, csr_off_sr, csr_off_sh, csr_ids_sr, csr_ids_sh, chunks, chunks_sh,
       csr_idx_sr, csr_idx_sh, csr_state, csr_tmp, gsum,
       partials, hist, blocksums, l1;
   // sizes
@@ -451,6 +451,16 @@ cudaError_t launch_recon_loss(const float* x, const float* y, const cg_camera* c
 inline uint64_t* depth_sorted(void* ws, const Layout& L) { return ws_ptr<uint64_t>(ws, L.dkeys0); }
 // Members per chunk of the codebook reduction (one warp sums a chunk).
 constexpr int kCodebookChunk = 512;
+
+// Backward work classes of a tile (quarter octaves of its largest contributor
+// position m: 4 floor(log2 m) plus the next two bits of m, at most 63).
+constexpr int kWorkBuckets = 64;
+__device__ __forceinline__ uint32_t work_bucket(uint32_t m) {
+  if (m < 2u) return 0u;
+  const int e = 31 - __clz(m);
+  const uint32_t frac = e >= 2 ? (m >> (e - 2)) & 3u : (m & 1u) << 1;
+  return min((uint32_t)(kWorkBuckets - 1), 4u * (uint32_t)e + frac);
+}
 
 // Passes of a radix sort on nbits bits (digits of at most 8 bits).
 inline int sort_passes(int nbits) { return (nbits + 7) / 8; }

@@ -56,6 +56,10 @@ struct BlendArgs {
   float4* pairgrad;   // [K][2]
   float* pairgrad1;   // [K]
   uint8_t* pairlive;  // [K]
+  uint8_t* tile_bucket;      // per tile: work class of the backward (written by the forward)
+  uint32_t* tile_hist;       // the backward's tiles per work class, placement cursors
+  const uint32_t* tile_order;  // the launch's tiles by decreasing work class
+  int64_t n_tiles;
 };
 
 // power = h0 dx^2 + h1 dx dy + h2 dy^2 with d = mean - pixel centre
@@ -71,10 +75,14 @@ template <int TILE, int PPT>
 struct TileShape {
   static constexpr int NT = TILE * TILE / PPT;
   static constexpr int NW = NT / 32;
-  static_assert(NT % 32 == 0 && NT <= 256, "unsupported tile / pixels-per-thread");
-  // pixel k of thread t: column t % TILE, row (t / TILE) * PPT + k
-  __device__ static int px(int t) { return t % TILE; }
-  __device__ static int py(int t, int k) { return (t / TILE) * PPT + k; }
+  // each warp covers a block 8 pixels wide and WH = 4 PPT rows high (8x8 for
+  // two pixels per thread: a compact footprint, so that fewer of the tile's
+  // Gaussians reach a warp and its pixels stop at similar list positions);
+  // pixel k of lane l is column l % 8, row (l / 8) PPT + k of the block
+  static constexpr int WH = 4 * PPT;
+  static_assert(NT % 32 == 0 && NT <= 256 && TILE % 8 == 0 && TILE % WH == 0, "unsupported tile / pixels-per-thread");
+  __device__ static int px(int t) { return ((t >> 5) % (TILE / 8)) * 8 + (t & 7); }
+  __device__ static int py(int t, int k) { return ((t >> 5) / (TILE / 8)) * WH + ((t & 31) >> 3) * PPT + k; }
 };
 
 template <int TILE, int BATCH, int PPT>
@@ -82,7 +90,10 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_fwd(const Bl
   using S = TileShape<TILE, PPT>;
   constexpr int NT = S::NT;
   __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
-  const int64_t gt = blockIdx.x;
+  // tiles in decreasing order of their list length in this part, so the
+  // longest start first
+  const int64_t gt = args.tile_order[blockIdx.x];
+  if (gt >= args.n_tiles) return;
   const int v = find_view(args.views, args.n_views, gt);
   const ViewInfo& cam = args.views[v];
   const int64_t lt = gt - cam.tile_base;
@@ -167,6 +178,24 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_fwd(const Bl
   for (int k = 0; k < PPT; ++k) mine = mine && done[k];
   const bool final_out = args.phase == 1 || __syncthreads_and(mine);
   if (args.phase == 0 && threadIdx.x == 0) args.unsat[gt] = final_out ? 0 : 1;
+  if (final_out) {
+    // the backward walks the tile down from its largest contributor
+    // position: record the tile's work class for the backward's tile order
+    __shared__ uint32_t s_wmax[S::NW];
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) m = max(m, last[k]);
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0) s_wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int w = 1; w < S::NW; ++w) m = max(m, s_wmax[w]);
+      const uint32_t b = work_bucket(m);
+      args.tile_bucket[gt] = (uint8_t)b;
+      atomicAdd(&args.tile_hist[b], 1u);
+    }
+  }
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     const int y = ty * TILE + S::py(threadIdx.x, k);
@@ -280,7 +309,9 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const Bl
   __shared__ uint32_t s_maxc;
   __shared__ uint32_t s_list[3];  // first part's start and length, second part's start
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t gt = blockIdx.x;
+  // tiles in decreasing order of work, so the longest start first
+  const int64_t gt = args.tile_order[blockIdx.x];
+  if (gt >= args.n_tiles) return;
   const int v = find_view(args.views, args.n_views, gt);
   const ViewInfo& cam = args.views[v];
   const int64_t lt = gt - cam.tile_base;
@@ -398,6 +429,80 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const Bl
   }
 }
 
+// Tile orders: each blend launch takes the tiles by decreasing work class,
+// so that the longest start first and the short ones fill the tail.  The
+// class of a tile is work_bucket() of its list length in the first list part
+// (forward, first pass), of its length in the second part (second pass; 0
+// for tiles the first pass finished), or of its largest position after the
+// last contributor (backward; recorded by the forward).  Positions within a
+// class come from atomics: the order in which tiles run changes no output
+// bit, since every tile writes only its own pixels and its own pairs' slots.
+// hist holds per order kWorkBuckets counts, then kWorkBuckets cursors.
+__device__ __forceinline__ uint32_t tile_class(int mode, int64_t t, const uint2* ranges, const uint2* ranges_b,
+                                               const uint8_t* unsat, const uint8_t* bucket) {
+  if (mode == 0) return work_bucket(ranges[t].y - ranges[t].x);
+  if (mode == 1) return unsat[t] ? work_bucket(ranges_b[t].y - ranges_b[t].x) : 0u;
+  return min((uint32_t)bucket[t], (uint32_t)(kWorkBuckets - 1));
+}
+
+__global__ void __launch_bounds__(256) k_tile_hist(int mode, const uint2* __restrict__ ranges,
+                                                   const uint2* __restrict__ ranges_b,
+                                                   const uint8_t* __restrict__ unsat, uint32_t* hist,
+                                                   int64_t n_tiles) {
+  __shared__ uint32_t s_cnt[kWorkBuckets];
+  if (threadIdx.x < kWorkBuckets) s_cnt[threadIdx.x] = 0u;
+  __syncthreads();
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n_tiles) atomicAdd(&s_cnt[tile_class(mode, t, ranges, ranges_b, unsat, nullptr)], 1u);
+  __syncthreads();
+  if (threadIdx.x < kWorkBuckets && s_cnt[threadIdx.x] != 0u) atomicAdd(&hist[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(256) k_tile_order(int mode, const uint2* __restrict__ ranges,
+                                                    const uint2* __restrict__ ranges_b,
+                                                    const uint8_t* __restrict__ unsat,
+                                                    const uint8_t* __restrict__ bucket, uint32_t* hist,
+                                                    uint32_t* __restrict__ order, int64_t n_tiles) {
+  __shared__ uint32_t s_start[kWorkBuckets], s_cnt[kWorkBuckets], s_base[kWorkBuckets];
+  if (threadIdx.x < kWorkBuckets) s_cnt[threadIdx.x] = 0u;
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int b = kWorkBuckets - 1; b >= 0; --b) {
+      s_start[b] = acc;
+      acc += hist[b];
+    }
+  }
+  __syncthreads();
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t b = 0, r = 0;
+  if (t < n_tiles) {
+    b = tile_class(mode, t, ranges, ranges_b, unsat, bucket);
+    r = atomicAdd(&s_cnt[b], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < kWorkBuckets && s_cnt[threadIdx.x] != 0u)
+    s_base[threadIdx.x] = atomicAdd(&hist[kWorkBuckets + threadIdx.x], s_cnt[threadIdx.x]);
+  __syncthreads();
+  if (t < n_tiles) {
+    const uint64_t pos = (uint64_t)s_start[b] + s_base[b] + r;
+    if (pos < (uint64_t)n_tiles) order[pos] = (uint32_t)t;
+  }
+}
+
+// The tile order of one blend launch: mode 0 / 1 the forward's passes, 2 the
+// backward (whose class counts the forward kernels accumulated).
+static cudaError_t launch_tile_order(const Layout& L, void* ws, int mode, cudaStream_t s) {
+  const unsigned g = (unsigned)((L.T + 255) / 256);
+  const uint2* ranges = ws_ptr<uint2>(ws, L.ranges);
+  const uint2* ranges_b = ws_ptr<uint2>(ws, L.ranges_b);
+  const uint8_t* unsat = ws_ptr<uint8_t>(ws, L.unsat);
+  uint32_t* hist = ws_ptr<uint32_t>(ws, L.tile_hist) + 2 * kWorkBuckets * mode;
+  if (mode < 2) count_launch(), k_tile_hist<<<g, 256, 0, s>>>(mode, ranges, ranges_b, unsat, hist, L.T);
+  count_launch(), k_tile_order<<<g, 256, 0, s>>>(mode, ranges, ranges_b, unsat, ws_ptr<uint8_t>(ws, L.tile_bucket),
+                                                 hist, ws_ptr<uint32_t>(ws, L.tile_order), L.T);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // dispatch
 // ---------------------------------------------------------------------------
@@ -449,6 +554,10 @@ static BlendArgs blend_args(const Layout& L, void* ws, const float bg[3]) {
   a.pairgrad = ws_ptr<float4>(ws, L.pairgrad);
   a.pairgrad1 = ws_ptr<float>(ws, L.pairgrad1);
   a.pairlive = ws_ptr<uint8_t>(ws, L.pairlive);
+  a.tile_bucket = ws_ptr<uint8_t>(ws, L.tile_bucket);
+  a.tile_hist = ws_ptr<uint32_t>(ws, L.tile_hist) + 4 * kWorkBuckets;  // the backward's counts
+  a.tile_order = ws_ptr<uint32_t>(ws, L.tile_order);
+  a.n_tiles = L.T;
   return a;
 }
 
@@ -466,13 +575,18 @@ cudaError_t launch_blend_fwd(const Layout& L, void* ws, int tile, int batch, int
   BlendArgs a = blend_args(L, ws, bg);
   a.images = images;
   a.phase = phase;
-  if (tile == 8 && ppt == 1) return fwd_batch<8, 1>(batch, grid, s, a);
-  if (tile == 8 && ppt == 2) return fwd_batch<8, 2>(batch, grid, s, a);
-  if (tile == 16 && ppt == 1) return fwd_batch<16, 1>(batch, grid, s, a);
-  if (tile == 16 && ppt == 2) return fwd_batch<16, 2>(batch, grid, s, a);
-  if (tile == 16 && ppt == 4) return fwd_batch<16, 4>(batch, grid, s, a);
-  if (tile == 32 && ppt == 4) return fwd_batch<32, 4>(batch, grid, s, a);
-  return cudaErrorInvalidValue;
+  cudaError_t e = launch_tile_order(L, ws, phase, s);
+  if (e != cudaSuccess) return e;
+  e = cudaErrorInvalidValue;
+  if (tile == 8 && ppt == 1) e = fwd_batch<8, 1>(batch, grid, s, a);
+  if (tile == 8 && ppt == 2) e = fwd_batch<8, 2>(batch, grid, s, a);
+  if (tile == 16 && ppt == 1) e = fwd_batch<16, 1>(batch, grid, s, a);
+  if (tile == 16 && ppt == 2) e = fwd_batch<16, 2>(batch, grid, s, a);
+  if (tile == 16 && ppt == 4) e = fwd_batch<16, 4>(batch, grid, s, a);
+  if (tile == 32 && ppt == 4) e = fwd_batch<32, 4>(batch, grid, s, a);
+  if (e != cudaSuccess || phase != 1) return e;
+  // every tile has its backward work class once the second pass is done
+  return launch_tile_order(L, ws, 2, s);
 }
 
 cudaError_t launch_blend_bwd(const Layout& L, void* ws, int tile, int batch, int ppt, const float bg[3],

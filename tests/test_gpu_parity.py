@@ -41,6 +41,7 @@ def _run_gpu(scene, cams, d_image, tile=16, batch=0, bg=(0.0, 0.0, 0.0), bf16=Fa
         "cams": cams,
         "tile": tile,
         "ncontrib": r.array(cg.WS_NCONTRIB, torch.int32).cpu().numpy().view(np.uint32),
+        "tile_order": r.array(cg.WS_TILE_ORDER, torch.int32).cpu().numpy().view(np.uint32),
         "tfinal": r.array(cg.WS_TFINAL, torch.float32).cpu().numpy(),
         "geo": r.array(cg.WS_GEO, torch.float32, 8).cpu().numpy().reshape(-1, 8),
         "rgbm": r.array(cg.WS_RGB, torch.float32, 4).cpu().numpy().reshape(-1, 4),
@@ -106,6 +107,7 @@ def _compare(ref, gpu, check_grads=True):
     assert np.array_equal(k_sorted, expect)
     # per-pixel outputs
     assert np.array_equal(gpu["ncontrib"], ref.n_contrib.astype(np.uint32))
+    two_part_lists.check_tile_order(gpu["tile_order"], gpu["ncontrib"], gpu["cams"], tile=gpu["tile"])
     assert np.abs(gpu["tfinal"] - ref.t_final).max() < 1e-5
     assert np.abs(gpu["image"] - ref.image).max() < IMG_ATOL
     if check_grads:

@@ -70,3 +70,26 @@ def check(ref, cams, pairs_a, ranges_a, pairs_b, ranges_b, tiles=None, tile=16):
         nb += got_b.size
         nfull += full.size
     return na, nb, nfull
+
+
+def work_class(m):
+    """Quarter-octave class of a tile's largest contributor position m (the
+    backward's tile order): 4 floor(log2 m) plus the next two bits of m, 0 for
+    m < 2, at most 63."""
+    m = int(m)
+    if m < 2:
+        return 0
+    e = m.bit_length() - 1
+    frac = (m >> (e - 2)) & 3 if e >= 2 else (m & 1) << 1
+    return min(63, 4 * e + frac)
+
+
+def check_tile_order(order, ncontrib, cams, tile=16):
+    """The backward's tile order: a permutation of the global tiles whose
+    work classes (from the per-pixel contributor positions) never increase."""
+    pix = tile_pixels(cams, tile)
+    assert order.size == len(pix)
+    assert np.array_equal(np.sort(order.astype(np.int64)), np.arange(len(pix)))
+    cls = np.array([work_class(ncontrib[p].max() if p.size else 0) for p in pix])
+    seq = cls[order.astype(np.int64)]
+    assert np.all(seq[1:] <= seq[:-1])
