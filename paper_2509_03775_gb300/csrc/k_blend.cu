@@ -239,9 +239,12 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
   return v[0];
 }
 
+// Per-pixel state of the backward walk: T the transmittance in front of the
+// current Gaussian, accd = dL/dC . (colour composited behind it), bgdot the
+// background's share of that dot product (final transmittance x bg . dL/dC).
 template <int PPT>
 struct PixelBwd {
-  float pyc[PPT], T[PPT], dC[PPT][3], acc[PPT][3], bgdot[PPT];
+  float pyc[PPT], T[PPT], dC[PPT][3], accd[PPT], bgdot[PPT];
   uint32_t nc[PPT];
 };
 
@@ -276,8 +279,9 @@ __device__ __forceinline__ bool bwd_gaussian(const float4& a, const float4& b, c
     g[9 * S + 6] = fmaf(w, px.dC[k][0], g[9 * S + 6]);
     g[9 * S + 7] = fmaf(w, px.dC[k][1], g[9 * S + 7]);
     g[9 * S + 8] = fmaf(w, px.dC[k][2], g[9 * S + 8]);
-    const float dot = fmaf(c.x - px.acc[k][0], px.dC[k][0],
-                           fmaf(c.y - px.acc[k][1], px.dC[k][1], (c.z - px.acc[k][2]) * px.dC[k][2]));
+    // (c - behind) . dL/dC; the colour behind is only ever used in this dot
+    // product, so the walk carries the dot product instead of the colour
+    const float dot = fmaf(c.x, px.dC[k][0], fmaf(c.y, px.dC[k][1], c.z * px.dC[k][2])) - px.accd[k];
     const float dalpha = fmaf(Tk, dot, -px.bgdot[k] * rom);
     if (!clamped) {
       // moments of dL/dpower: sum dpow (dx, dy, dx^2, dx dy, dy^2); the
@@ -291,9 +295,7 @@ __device__ __forceinline__ bool bwd_gaussian(const float4& a, const float4& b, c
       g[9 * S + 4] = fmaf(py_, dy, g[9 * S + 4]);
       g[9 * S + 5] = fmaf(ex, dalpha, g[9 * S + 5]);
     }
-    px.acc[k][0] = fmaf(alpha, c.x - px.acc[k][0], px.acc[k][0]);
-    px.acc[k][1] = fmaf(alpha, c.y - px.acc[k][1], px.acc[k][1]);
-    px.acc[k][2] = fmaf(alpha, c.z - px.acc[k][2], px.acc[k][2]);
+    px.accd[k] = fmaf(alpha, dot, px.accd[k]);
     px.T[k] = Tk;
   }
   return any;
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const Bl
   for (int k = 0; k < PPT; ++k) {
     const int y = ty * TILE + S::py(threadIdx.x, k);
     px.pyc[k] = (float)y + 0.5f;
-    px.acc[k][0] = px.acc[k][1] = px.acc[k][2] = 0.0f;
+    px.accd[k] = 0.0f;
     float tf = 1.0f;
     if (x < cam.width && y < cam.height) {
       const int64_t pix = cam.pix_base + (int64_t)y * cam.width + x;
