@@ -270,12 +270,13 @@ __device__ __forceinline__ bool bwd_gaussian(const float4& a, const float4& b, c
     }
     const bool clamped = vv > kAlphaMax;
     const float alpha = clamped ? kAlphaMax : vv;
-    if (alpha < kAlphaMin) continue;
-    any = true;
+    // the rest without branches: a skipped pixel adds zeros and keeps its state
+    const bool ok = !(alpha < kAlphaMin);
+    any |= ok;
     const float om = 1.0f - alpha;
     const float rom = __fdividef(1.0f, om);
     const float Tk = px.T[k] * rom;
-    const float w = alpha * Tk;
+    const float w = ok ? alpha * Tk : 0.0f;
     g[9 * S + 6] = fmaf(w, px.dC[k][0], g[9 * S + 6]);
     g[9 * S + 7] = fmaf(w, px.dC[k][1], g[9 * S + 7]);
     g[9 * S + 8] = fmaf(w, px.dC[k][2], g[9 * S + 8]);
@@ -283,20 +284,20 @@ __device__ __forceinline__ bool bwd_gaussian(const float4& a, const float4& b, c
     // product, so the walk carries the dot product instead of the colour
     const float dot = fmaf(c.x, px.dC[k][0], fmaf(c.y, px.dC[k][1], c.z * px.dC[k][2])) - px.accd[k];
     const float dalpha = fmaf(Tk, dot, -px.bgdot[k] * rom);
-    if (!clamped) {
-      // moments of dL/dpower: sum dpow (dx, dy, dx^2, dx dy, dy^2); the
-      // mean and conic gradients are linear in them (see k_blend_bwd)
-      const float dpow = alpha * dalpha;
-      const float px_ = dpow * dx, py_ = dpow * dy;
-      g[9 * S + 0] += px_;
-      g[9 * S + 1] += py_;
-      g[9 * S + 2] = fmaf(px_, dx, g[9 * S + 2]);
-      g[9 * S + 3] = fmaf(px_, dy, g[9 * S + 3]);
-      g[9 * S + 4] = fmaf(py_, dy, g[9 * S + 4]);
-      g[9 * S + 5] = fmaf(ex, dalpha, g[9 * S + 5]);
-    }
-    px.accd[k] = fmaf(alpha, dot, px.accd[k]);
-    px.T[k] = Tk;
+    // moments of dL/dpower: sum dpow (dx, dy, dx^2, dx dy, dy^2); the mean
+    // and conic gradients are linear in them (see k_blend_bwd); a clamped
+    // alpha has no gradient with respect to power or opacity
+    const float dop = (ok && !clamped) ? dalpha : 0.0f;
+    const float dpow = alpha * dop;
+    const float px_ = dpow * dx, py_ = dpow * dy;
+    g[9 * S + 0] += px_;
+    g[9 * S + 1] += py_;
+    g[9 * S + 2] = fmaf(px_, dx, g[9 * S + 2]);
+    g[9 * S + 3] = fmaf(px_, dy, g[9 * S + 3]);
+    g[9 * S + 4] = fmaf(py_, dy, g[9 * S + 4]);
+    g[9 * S + 5] = fmaf(ex, dop, g[9 * S + 5]);
+    px.accd[k] = ok ? fmaf(alpha, dot, px.accd[k]) : px.accd[k];
+    px.T[k] = ok ? Tk : px.T[k];
   }
   return any;
 }
