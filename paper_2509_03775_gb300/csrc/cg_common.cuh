@@ -51,9 +51,8 @@ CG_HD uint32_t float_to_bits(float f) {
 // remainder), the degree-6 Taylor polynomial of e^r on |r| <= ln2/2 by
 // Horner's rule (truncation < 1.3e-7 relative), then the factor 2^n from its
 // exponent bits.  x <= -87 gives 0, x >= 88 gives +inf, NaN gives 0.
-CG_HD float exp32(float x) {
-  if (!(x > -87.0f)) return 0.0f;
-  if (!(x < 88.0f)) return bits_to_float(0x7f800000u);
+// exp32 for -87 < x < 88 (no range handling; the same bits as exp32 there).
+CG_HD float exp32_core(float x) {
   const float log2e = 1.44269502162933349609375f;
   const float ln2_hi = 0.693145751953125f;
   const float ln2_lo = 1.42860682030941723212e-6f;
@@ -69,6 +68,12 @@ CG_HD float exp32(float x) {
   p = fmaf(p, r, 1.0f);
   const int ni = (int)n;
   return p * bits_to_float((uint32_t)(ni + 127) << 23);
+}
+
+CG_HD float exp32(float x) {
+  if (!(x > -87.0f)) return 0.0f;
+  if (!(x < 88.0f)) return bits_to_float(0x7f800000u);
+  return exp32_core(x);
 }
 
 CG_HD float sigmoid32(float l) { return 1.0f / (1.0f + exp32(-l)); }

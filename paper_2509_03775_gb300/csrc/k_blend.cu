@@ -145,6 +145,8 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_fwd(const Bl
       sC[j] = args.rgbm[rec];
     }
     __syncthreads();
+    // a warp whose pixels have all stopped skips the batch
+    if (__all_sync(0xffffffffu, mine)) continue;
     for (int j = 0; j < n_in; ++j) {
       const float4 a = sA[j], b = sB[j];
 #pragma unroll
@@ -153,7 +155,9 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_fwd(const Bl
         float dx, dy;
         const float power = gauss_power(a, b, pxc, pyc[k], dx, dy);
         if (power > 0.0f || power < b.z) continue;
-        const float vv = b.y * exp32(power);
+        // here -5.55 < power <= 0 (the skip bound is -ln(255 o) - 0.001 with
+        // o <= 1), inside exp32's unguarded range
+        const float vv = b.y * exp32_core(power);
         const float alpha = vv > kAlphaMax ? kAlphaMax : vv;
         if (alpha < kAlphaMin) continue;
         const float test_T = T[k] * (1.0f - alpha);
