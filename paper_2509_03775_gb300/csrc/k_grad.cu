@@ -64,11 +64,14 @@ template <int NB>
 __device__ __forceinline__ void record_chain(const SceneArgs& sc, const ViewInfo* __restrict__ views,
                                            const float* __restrict__ sig3, const float4* __restrict__ geo,
                                            const float4* __restrict__ rgbm, uint32_t rec, const float (&gs)[9],
-                                           float (&out)[10], float* __restrict__ drgb) {
+                                           float (&out)[10], float (&dc)[3]) {
   const int v = (int)(rec / (uint32_t)sc.n);
   const int64_t g = (int64_t)rec - (int64_t)v * sc.n;
   const float p[3] = {sc.pos[3 * g], sc.pos[3 * g + 1], sc.pos[3 * g + 2]};
-  const uint32_t isr = sc.g2sr[g], ish = sc.g2sh[g];
+  // (indices of culled Gaussians are not checked: clamped to a valid row,
+  // their results are discarded by the caller)
+  const uint32_t isr = min((uint32_t)sc.g2sr[g], (uint32_t)sc.k_sr - 1u);
+  const uint32_t ish = min((uint32_t)sc.g2sh[g], (uint32_t)sc.k_sh - 1u);
   const ViewInfo& cam = views[v];
   const float* W = cam.w2c;
   float dp[3] = {0.0f, 0.0f, 0.0f}, dsg[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
@@ -76,12 +79,8 @@ __device__ __forceinline__ void record_chain(const SceneArgs& sc, const ViewInfo
   const float dl = gs[5] * (o * (1.0f - o));
   // colour -> clamp mask -> SH direction
   const uint32_t mask = (uint32_t)rgbm[rec].w;
-  float dc[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) dc[c] = (mask >> c & 1u) ? 0.0f : gs[6 + c];
-  drgb[3 * (size_t)rec] = dc[0];
-  drgb[3 * (size_t)rec + 1] = dc[1];
-  drgb[3 * (size_t)rec + 2] = dc[2];
   const float dv[3] = {p[0] - cam.campos[0], p[1] - cam.campos[1], p[2] - cam.campos[2]};
   const float dist = sqrtf(fmaf(dv[0], dv[0], fmaf(dv[1], dv[1], dv[2] * dv[2])));
   const float inv = 1.0f / dist;
@@ -250,7 +249,7 @@ __global__ void __launch_bounds__(256) k_slot_sum(const uint32_t* __restrict__ n
 // the position, logit and Sigma gradients; culled records contribute zero
 // (and get a zero colour gradient).
 template <int NB>
-__global__ void __launch_bounds__(256, 4) k_chain_sum(const SceneArgs sc, int n_views, const ViewInfo* __restrict__ views,
+__global__ void __launch_bounds__(256, 2) k_chain_sum(const SceneArgs sc, int n_views, const ViewInfo* __restrict__ views,
                                                    const float* __restrict__ sig3, const float4* __restrict__ geo,
                                                    const float4* __restrict__ rgbm,
                                                    const uint32_t* __restrict__ ntiles, const float* __restrict__ rg,
@@ -266,23 +265,25 @@ __global__ void __launch_bounds__(256, 4) k_chain_sum(const SceneArgs sc, int n_
     float acc[10] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     for (int v = 0; v < n_views; ++v) {
       const int64_t rec = (int64_t)v * n + g;
-      if (ok && ntiles[rec] > 0) {
-        float gs[9], out[10];
-        // the record's nine sums (40-byte records: 8-byte loads)
-        const float2* r2 = reinterpret_cast<const float2*>(rg + 10 * (size_t)rec);
+      // every record runs the chain rule without a branch, so that all its
+      // loads are in flight together; a culled record's results (from
+      // stale sums) are replaced by zeros
+      const bool live = ok && ntiles[rec] > 0;
+      float gs[9], out[10], dc[3];
+      // the record's nine sums (40-byte records: 8-byte loads)
+      const float2* r2 = reinterpret_cast<const float2*>(rg + 10 * (size_t)rec);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float2 u = r2[e];
-          gs[2 * e] = u.x;
-          gs[2 * e + 1] = u.y;
-        }
-        gs[8] = rg[10 * (size_t)rec + 8];
-        record_chain<NB>(sc, sviews, sig3, geo, rgbm, (uint32_t)rec, gs, out, drgb);
-#pragma unroll
-        for (int e = 0; e < 10; ++e) acc[e] += out[e];
-      } else {
-        drgb[3 * rec] = drgb[3 * rec + 1] = drgb[3 * rec + 2] = 0.0f;
+      for (int e = 0; e < 4; ++e) {
+        const float2 u = r2[e];
+        gs[2 * e] = u.x;
+        gs[2 * e + 1] = u.y;
       }
+      gs[8] = rg[10 * (size_t)rec + 8];
+      record_chain<NB>(sc, sviews, sig3, geo, rgbm, (uint32_t)rec, gs, out, dc);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) drgb[3 * rec + c] = live ? dc[c] : 0.0f;
+#pragma unroll
+      for (int e = 0; e < 10; ++e) acc[e] += live ? out[e] : 0.0f;
     }
     d_pos[3 * g] = acc[0];
     d_pos[3 * g + 1] = acc[1];

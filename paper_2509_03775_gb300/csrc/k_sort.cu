@@ -443,28 +443,45 @@ __device__ __forceinline__ int64_t list_cut(int64_t vis) { return (vis + 9) / 10
 
 // Per view, the 2D inclusive prefix sums of the unfinished-tile flags:
 // sat[(y + 1) (tiles_x + 1) + x + 1] = unfinished tiles in [0, x] x [0, y]
-// (row and column 0 are 0).  One block per view.
-__global__ void k_unsat_sat(const ViewInfo* __restrict__ views, const uint8_t* __restrict__ unsat,
-                            uint32_t* __restrict__ sat) {
+// (row and column 0 are 0).  One block per view: each warp scans whole tile
+// rows 32 columns at a time (coalesced), then each thread accumulates one
+// column down the rows, loading eight rows ahead of the running sum.
+__global__ void __launch_bounds__(256) k_unsat_sat(const ViewInfo* __restrict__ views,
+                                                   const uint8_t* __restrict__ unsat, uint32_t* __restrict__ sat) {
   const ViewInfo& cam = views[blockIdx.x];
   const int tx = cam.tiles_x, ty = cam.tiles_y, W = tx + 1;
   uint32_t* S = sat + cam.sat_base;
   const uint8_t* u = unsat + cam.tile_base;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int x = threadIdx.x; x < W; x += blockDim.x) S[x] = 0u;
-  for (int r = threadIdx.x; r < ty; r += blockDim.x) {
-    uint32_t acc = 0;
-    S[(int64_t)(r + 1) * W] = 0u;
-    for (int x = 0; x < tx; ++x) {
-      acc += u[(int64_t)r * tx + x];
-      S[(int64_t)(r + 1) * W + x + 1] = acc;
+  for (int r = wid; r < ty; r += nw) {
+    uint32_t* row = S + (int64_t)(r + 1) * W;
+    if (lane == 0) row[0] = 0u;
+    uint32_t carry = 0;
+    for (int x0 = 0; x0 < tx; x0 += 32) {
+      const int x = x0 + lane;
+      uint32_t v = x < tx ? (uint32_t)u[(int64_t)r * tx + x] : 0u;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += t;
+      }
+      if (x < tx) row[x + 1] = carry + v;
+      carry += __shfl_sync(0xffffffffu, v, 31);
     }
   }
   __syncthreads();
   for (int c = threadIdx.x; c < W; c += blockDim.x) {
     uint32_t acc = 0;
-    for (int r = 1; r <= ty; ++r) {
-      acc += S[(int64_t)r * W + c];
-      S[(int64_t)r * W + c] = acc;
+    for (int r0 = 1; r0 <= ty; r0 += 8) {
+      uint32_t v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = r0 + k <= ty ? S[(int64_t)(r0 + k) * W + c] : 0u;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        acc += v[k];
+        if (r0 + k <= ty) S[(int64_t)(r0 + k) * W + c] = acc;
+      }
     }
   }
 }
