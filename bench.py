@@ -293,7 +293,8 @@ def run_cg(args):
     cbt = torch.bfloat16 if bf16 else torch.float32
     st = cg.SceneTensors.from_scene(scene, device=dev, codebook_dtype=cbt)
     tst = cg.SceneTensors.from_scene(target_scene, device=dev, codebook_dtype=cbt)
-    shape = {"tile": args.tile, "batch": args.batch}
+    shape = {"tile": args.tile, "batch": args.batch, "batch_bwd": args.batch_bwd, "ppt_fwd": args.ppt_fwd,
+             "ppt_bwd": args.ppt_bwd}
     tuned = None
     if args.autotune or args.autotune_tiles:
         from paper_2509_03775_gb300 import autotune
@@ -753,7 +754,10 @@ def main():
     ap.add_argument("--autotune-tiles", action="store_true",
                     help="also tune the tile size (8/16/32; it changes which tiles list a Gaussian)")
     ap.add_argument("--tile", type=int, default=16)
-    ap.add_argument("--batch", type=int, default=0)
+    ap.add_argument("--batch", type=int, default=0, help="forward blend batch (0: library default)")
+    ap.add_argument("--batch-bwd", type=int, default=0, help="backward blend batch (0: library default)")
+    ap.add_argument("--ppt-fwd", type=int, default=0, help="forward pixels per thread (0: library default)")
+    ap.add_argument("--ppt-bwd", type=int, default=0, help="backward pixels per thread (0: library default)")
     ap.add_argument("--cpu-tiles", type=int, default=96, help="tiles in the CPU-baseline sample")
     ap.add_argument("--ref-tiles", type=int, default=24, help="tiles per step of the reference arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")

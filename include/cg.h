@@ -99,7 +99,7 @@ typedef struct {
  * batch, batch_bwd: Gaussians staged in shared memory per step of the
  * forward / backward blend kernel (0 = default; forward 64, 128 or 256,
  * backward 32, 64 or 128).  ppt_fwd, ppt_bwd: pixels per thread of the
- * blend kernels (0 = default; 1 or 2 for 8x8 tiles, 1, 2 or 4 for 16x16,
+ * blend kernels (0 = default; 1 or 2 for 8x8 tiles, 1, 2, 4 or 8 for 16x16,
  * 4 for 32x32; the defaults are 1 forward and 4 backward, 4 forward on
  * 32x32 tiles, 2 backward on 8x8 tiles).  These four change speed only,
  * never results.

@@ -23,7 +23,7 @@ from . import cg
 
 FWD_BATCH = (64, 128, 256)
 BWD_BATCH = (32, 64, 128)
-PPT = {8: (1, 2), 16: (1, 2, 4), 32: (4,)}
+PPT = {8: (1, 2), 16: (1, 2, 4, 8), 32: (4,)}
 
 
 def default_cache() -> str:

@@ -75,14 +75,18 @@ template <int TILE, int PPT>
 struct TileShape {
   static constexpr int NT = TILE * TILE / PPT;
   static constexpr int NW = NT / 32;
-  // each warp covers a block 8 pixels wide and WH = 4 PPT rows high (8x8 for
-  // two pixels per thread: a compact footprint, so that fewer of the tile's
-  // Gaussians reach a warp and its pixels stop at similar list positions);
-  // pixel k of lane l is column l % 8, row (l / 8) PPT + k of the block
-  static constexpr int WH = 4 * PPT;
-  static_assert(NT % 32 == 0 && NT <= 256 && TILE % 8 == 0 && TILE % WH == 0, "unsupported tile / pixels-per-thread");
-  __device__ static int px(int t) { return ((t >> 5) % (TILE / 8)) * 8 + (t & 7); }
-  __device__ static int py(int t, int k) { return ((t >> 5) / (TILE / 8)) * WH + ((t & 31) >> 3) * PPT + k; }
+  // each warp covers a block BW pixels wide and WH = 32 PPT / BW rows high:
+  // 8 wide (8x8 for two pixels per thread, 8x16 for four: a compact
+  // footprint, so that fewer of the tile's Gaussians reach a warp and its
+  // pixels stop at similar list positions), or the whole tile when one warp
+  // holds it; pixel k of lane l is column l % BW, row (l / BW) PPT + k of
+  // the block
+  static constexpr int BW = 32 * PPT >= TILE * TILE ? TILE : 8;
+  static constexpr int WH = 32 * PPT / BW;
+  static_assert(NT % 32 == 0 && NT <= 256 && TILE % BW == 0 && TILE % WH == 0 && 32 % BW == 0,
+                "unsupported tile / pixels-per-thread");
+  __device__ static int px(int t) { return ((t >> 5) % (TILE / BW)) * BW + (t & 31) % BW; }
+  __device__ static int py(int t, int k) { return ((t >> 5) / (TILE / BW)) * WH + ((t & 31) / BW) * PPT + k; }
 };
 
 template <int TILE, int BATCH, int PPT>
@@ -570,7 +574,7 @@ static BlendArgs blend_args(const Layout& L, void* ws, const float bg[3]) {
 
 bool blend_ppt_ok(int tile, int ppt) {
   if (tile == 8) return ppt == 1 || ppt == 2;
-  if (tile == 16) return ppt == 1 || ppt == 2 || ppt == 4;
+  if (tile == 16) return ppt == 1 || ppt == 2 || ppt == 4 || ppt == 8;
   if (tile == 32) return ppt == 4;
   return false;
 }
@@ -590,6 +594,7 @@ cudaError_t launch_blend_fwd(const Layout& L, void* ws, int tile, int batch, int
   if (tile == 16 && ppt == 1) e = fwd_batch<16, 1>(batch, grid, s, a);
   if (tile == 16 && ppt == 2) e = fwd_batch<16, 2>(batch, grid, s, a);
   if (tile == 16 && ppt == 4) e = fwd_batch<16, 4>(batch, grid, s, a);
+  if (tile == 16 && ppt == 8) e = fwd_batch<16, 8>(batch, grid, s, a);
   if (tile == 32 && ppt == 4) e = fwd_batch<32, 4>(batch, grid, s, a);
   if (e != cudaSuccess || phase != 1) return e;
   // every tile has its backward work class once the second pass is done
@@ -607,6 +612,7 @@ cudaError_t launch_blend_bwd(const Layout& L, void* ws, int tile, int batch, int
   if (tile == 16 && ppt == 1) return bwd_batch<16, 1>(batch, grid, s, a);
   if (tile == 16 && ppt == 2) return bwd_batch<16, 2>(batch, grid, s, a);
   if (tile == 16 && ppt == 4) return bwd_batch<16, 4>(batch, grid, s, a);
+  if (tile == 16 && ppt == 8) return bwd_batch<16, 8>(batch, grid, s, a);
   if (tile == 32 && ppt == 4) return bwd_batch<32, 4>(batch, grid, s, a);
   return cudaErrorInvalidValue;
 }

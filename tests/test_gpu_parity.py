@@ -148,7 +148,7 @@ def test_tile_sizes_and_background(tile):
 
 @pytest.mark.parametrize("tile,batch,batch_bwd,ppt_fwd,ppt_bwd", [
     (16, 64, 32, 1, 1), (16, 128, 64, 2, 2), (16, 256, 128, 4, 4), (16, 256, 64, 1, 2),
-    (8, 64, 32, 2, 2), (8, 128, 128, 1, 1), (32, 64, 32, 4, 4)])
+    (16, 64, 64, 8, 8), (16, 128, 32, 1, 8), (8, 64, 32, 2, 2), (8, 128, 128, 1, 1), (32, 64, 32, 4, 4)])
 def test_launch_shapes(tile, batch, batch_bwd, ppt_fwd, ppt_bwd):
     """Batch sizes and pixels per thread change speed only: same bits for the
     discrete outputs, same tolerances for the rest."""
