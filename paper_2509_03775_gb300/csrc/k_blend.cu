@@ -27,9 +27,12 @@
 //
 // The backward takes the forward's decisions exactly, but it only needs
 // alpha as a value: it uses the hardware exp and recomputes the library's
-// exact exp32 only when the value lies within 1e-5 (relative) of the skip
-// or clamp threshold, where the two could decide differently (both are
-// within 1e-6 of exp).
+// exact exp32 only near a decision threshold, where the two could decide
+// differently (both are within 1.5e-6, relative, of exp for the powers
+// here).  Near the skip threshold means a power within 1e-5 of
+// ln(kAlphaMin / opacity), computed per staged Gaussian (an error of a few
+// 1e-7); a Gaussian whose opacity reaches 0.99 (1 - 1e-5) can be clamped
+// and always takes the exact exp.
 #include <algorithm>
 
 #include "cg_common.cuh"
@@ -271,11 +274,8 @@ __device__ __forceinline__ bool bwd_gaussian(const float4& a, const float4& b, c
     const float power = gauss_power(a, b, pxc, px.pyc[k], dx, dy);
     if (power > 0.0f || power < b.z) continue;
     float ex = __expf(power);
-    float vv = b.y * ex;
-    if (fabsf(vv - kAlphaMin) < 1e-5f * kAlphaMin || fabsf(vv - kAlphaMax) < 1e-5f * kAlphaMax) {
-      ex = exp32(power);
-      vv = b.y * ex;
-    }
+    if (fabsf(power - b.w) < c.w) ex = exp32_core(power);
+    const float vv = b.y * ex;
     const bool clamped = vv > kAlphaMax;
     const float alpha = clamped ? kAlphaMax : vv;
     // the rest without branches: a skipped pixel adds zeros and keeps its state
@@ -382,8 +382,15 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const Bl
       const uint64_t key = p < len_a ? args.pairs[s_list[0] + p] : args.pairs_b[s_list[2] + (p - len_a)];
       const uint32_t rec = key_rec(key);
       sA[j] = args.geo[2 * (size_t)rec];
-      sB[j] = args.geo[2 * (size_t)rec + 1];
-      sC[j] = args.rgbm[rec];
+      float4 b = args.geo[2 * (size_t)rec + 1];
+      float4 c = args.rgbm[rec];
+      // b.w: the power at which opacity x exp reaches the skip threshold;
+      // c.w (the clamp bits, unused here): the half-width of the power
+      // window that takes the exact exp
+      b.w = logf(kAlphaMin / b.y);
+      c.w = b.y >= kAlphaMax * (1.0f - 1e-5f) ? __int_as_float(0x7f800000) : 1e-5f;
+      sB[j] = b;
+      sC[j] = c;
       sSlot[j] = args.offrec[rec] + key_rank(key);
     }
     __syncthreads();
