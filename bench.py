@@ -54,8 +54,8 @@ FLOPS_PER_EVAL = {"blend_fwd": 21, "blend_bwd": 55}
 # workload (summaries under profiles/), valid while the kernel's source file
 # hashes (SHA-256, first 16 hex digits) to `src`; null otherwise.
 NCU_TRAFFIC = {
-    "blend_bwd": {"bytes": 77711872 + 15775744, "src": "8eed182494e903ce", "workload": "truck"},
-    "blend_fwd": {"bytes": 18645248 + 676608 + 28017152 + 16128, "src": "8eed182494e903ce", "workload": "truck"},
+    "blend_bwd": {"bytes": 77190400 + 16061696, "src": "7b55c7546e7341be", "workload": "truck"},
+    "blend_fwd": {"bytes": 18647040 + 581376 + 28041984 + 256, "src": "7b55c7546e7341be", "workload": "truck"},
 }
 
 
