@@ -259,54 +259,88 @@ struct PixelBwd {
   uint32_t nc[PPT];
 };
 
-// Per-pixel backward of one Gaussian at list position `pos`; adds its nine
-// terms (summed over the thread's pixels) into g[9 * S ...]: the moments
+// Per-pixel backward of one Gaussian at list position `pos`: writes its nine
+// terms, summed over the thread's pixels, to g[9 S ...]: the moments
 // sum dpow dx, dpow dy, dpow dx^2, dpow dx dy, dpow dy^2 of dpow = dL/dpower,
-// dL/dopacity, dL/drgb.
+// dL/dopacity, dL/drgb.  The range test (list position before the pixel's
+// last contributor, power in [skip bound, 0]) is taken for all of the
+// thread's pixels first; a thread none of whose pixels is in range writes
+// zeros, the others run every pixel without branches, gating an
+// out-of-range or skipped pixel to zero terms and an unchanged state.  The
+// thread's pixels share a column, so dx is common to them and the moments
+// in dx are formed once from sums over the pixels.
 template <int PPT, int S>
 __device__ __forceinline__ bool bwd_gaussian(const float4& a, const float4& b, const float4& c, uint32_t pos,
                                              float pxc, PixelBwd<PPT>& px, float (&g)[32]) {
-  bool any = false;
+  float pw[PPT], dy[PPT], dx = 0.0f;
+  bool in[PPT];
+  bool anyin = false;
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
-    if (pos >= px.nc[k]) continue;
-    float dx, dy;
-    const float power = gauss_power(a, b, pxc, px.pyc[k], dx, dy);
-    if (power > 0.0f || power < b.z) continue;
-    float ex = __expf(power);
-    if (fabsf(power - b.w) < c.w) ex = exp32_core(power);
-    const float vv = b.y * ex;
+    pw[k] = gauss_power(a, b, pxc, px.pyc[k], dx, dy[k]);
+    in[k] = pos < px.nc[k] && !(pw[k] > 0.0f) && !(pw[k] < b.z);
+    anyin |= in[k];
+  }
+  if (!anyin) {
+#pragma unroll
+    for (int e = 0; e < 9; ++e) g[9 * S + e] = 0.0f;
+    return false;
+  }
+  float ex[PPT];
+  bool near = false;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    ex[k] = __expf(pw[k]);
+    near |= in[k] && fabsf(pw[k] - b.w) < c.w;
+  }
+  if (near) {
+#pragma unroll
+    for (int k = 0; k < PPT; ++k)
+      if (in[k] && fabsf(pw[k] - b.w) < c.w) ex[k] = exp32_core(pw[k]);
+  }
+  bool any = false;
+  float sdp = 0.0f, sdpy = 0.0f, sdpy2 = 0.0f, se = 0.0f, sw0 = 0.0f, sw1 = 0.0f, sw2 = 0.0f;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    const float vv = b.y * ex[k];
     const bool clamped = vv > kAlphaMax;
     const float alpha = clamped ? kAlphaMax : vv;
-    // the rest without branches: a skipped pixel adds zeros and keeps its state
-    const bool ok = !(alpha < kAlphaMin);
+    const bool ok = in[k] && !(alpha < kAlphaMin);
     any |= ok;
-    const float om = 1.0f - alpha;
-    const float rom = __fdividef(1.0f, om);
+    // a gated pixel takes alpha = 0: zero weight, zero dpow, accd kept
+    const float al = ok ? alpha : 0.0f;
+    const float rom = __fdividef(1.0f, 1.0f - al);
     const float Tk = px.T[k] * rom;
-    const float w = ok ? alpha * Tk : 0.0f;
-    g[9 * S + 6] = fmaf(w, px.dC[k][0], g[9 * S + 6]);
-    g[9 * S + 7] = fmaf(w, px.dC[k][1], g[9 * S + 7]);
-    g[9 * S + 8] = fmaf(w, px.dC[k][2], g[9 * S + 8]);
+    const float w = al * Tk;
+    sw0 = fmaf(w, px.dC[k][0], sw0);
+    sw1 = fmaf(w, px.dC[k][1], sw1);
+    sw2 = fmaf(w, px.dC[k][2], sw2);
     // (c - behind) . dL/dC; the colour behind is only ever used in this dot
     // product, so the walk carries the dot product instead of the colour
     const float dot = fmaf(c.x, px.dC[k][0], fmaf(c.y, px.dC[k][1], c.z * px.dC[k][2])) - px.accd[k];
     const float dalpha = fmaf(Tk, dot, -px.bgdot[k] * rom);
-    // moments of dL/dpower: sum dpow (dx, dy, dx^2, dx dy, dy^2); the mean
-    // and conic gradients are linear in them (see k_blend_bwd); a clamped
-    // alpha has no gradient with respect to power or opacity
+    // a clamped alpha has no gradient with respect to power or opacity
     const float dop = (ok && !clamped) ? dalpha : 0.0f;
-    const float dpow = alpha * dop;
-    const float px_ = dpow * dx, py_ = dpow * dy;
-    g[9 * S + 0] += px_;
-    g[9 * S + 1] += py_;
-    g[9 * S + 2] = fmaf(px_, dx, g[9 * S + 2]);
-    g[9 * S + 3] = fmaf(px_, dy, g[9 * S + 3]);
-    g[9 * S + 4] = fmaf(py_, dy, g[9 * S + 4]);
-    g[9 * S + 5] = fmaf(ex, dop, g[9 * S + 5]);
-    px.accd[k] = ok ? fmaf(alpha, dot, px.accd[k]) : px.accd[k];
+    const float dpow = al * dop;
+    const float pyv = dpow * dy[k];
+    sdp += dpow;
+    sdpy += pyv;
+    sdpy2 = fmaf(pyv, dy[k], sdpy2);
+    se = fmaf(ex[k], dop, se);
+    px.accd[k] = fmaf(al, dot, px.accd[k]);
     px.T[k] = ok ? Tk : px.T[k];
   }
+  // the mean and conic gradients are linear in these moments (see k_blend_bwd)
+  const float sdpx = dx * sdp;
+  g[9 * S + 0] = sdpx;
+  g[9 * S + 1] = sdpy;
+  g[9 * S + 2] = dx * sdpx;
+  g[9 * S + 3] = dx * sdpy;
+  g[9 * S + 4] = sdpy2;
+  g[9 * S + 5] = se;
+  g[9 * S + 6] = sw0;
+  g[9 * S + 7] = sw1;
+  g[9 * S + 8] = sw2;
   return any;
 }
 
@@ -401,10 +435,20 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const Bl
     for (int j = j_top; j >= 0; j -= 3) {
       float g[32];
 #pragma unroll
-      for (int e = 0; e < 32; ++e) g[e] = 0.0f;
+      for (int e = 27; e < 32; ++e) g[e] = 0.0f;
       bool any = bwd_gaussian<PPT, 0>(sA[j], sB[j], sC[j], pos0 + j, pxc, px, g);
-      if (j >= 1) any |= bwd_gaussian<PPT, 1>(sA[j - 1], sB[j - 1], sC[j - 1], pos0 + j - 1, pxc, px, g);
-      if (j >= 2) any |= bwd_gaussian<PPT, 2>(sA[j - 2], sB[j - 2], sC[j - 2], pos0 + j - 2, pxc, px, g);
+      if (j >= 1) {
+        any |= bwd_gaussian<PPT, 1>(sA[j - 1], sB[j - 1], sC[j - 1], pos0 + j - 1, pxc, px, g);
+      } else {
+#pragma unroll
+        for (int e = 9; e < 18; ++e) g[e] = 0.0f;
+      }
+      if (j >= 2) {
+        any |= bwd_gaussian<PPT, 2>(sA[j - 2], sB[j - 2], sC[j - 2], pos0 + j - 2, pxc, px, g);
+      } else {
+#pragma unroll
+        for (int e = 18; e < 27; ++e) g[e] = 0.0f;
+      }
       float mine = 0.0f;
       if (__any_sync(0xffffffffu, any)) mine = warp_reduce_scatter32(g);
       if (lane < 27) {
