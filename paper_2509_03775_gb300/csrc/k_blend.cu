@@ -92,8 +92,12 @@ struct TileShape {
   __device__ static int py(int t, int k) { return ((t >> 5) / (TILE / BW)) * WH + ((t & 31) / BW) * PPT + k; }
 };
 
+// 256-thread launches are held to six blocks per SM (40 registers), which
+// keeps 48 warps resident; the forward is instruction-bound and gains more
+// from the warps than from the three registers it gives up.
 template <int TILE, int BATCH, int PPT>
-__global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_fwd(const BlendArgs args) {
+__global__ void __launch_bounds__(TileShape<TILE, PPT>::NT, (TileShape<TILE, PPT>::NT == 256 ? 6 : 1))
+    k_blend_fwd(const BlendArgs args) {
   using S = TileShape<TILE, PPT>;
   constexpr int NT = S::NT;
   __shared__ float4 sA[BATCH], sB[BATCH], sC[BATCH];
@@ -158,27 +162,29 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_fwd(const Bl
       const float4 a = sA[j], b = sB[j];
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
-        if (done[k]) continue;
+        // one branch: a stopped pixel, or a power outside [skip bound, 0]
         float dx, dy;
         const float power = gauss_power(a, b, pxc, pyc[k], dx, dy);
-        if (power > 0.0f || power < b.z) continue;
+        if (done[k] || power > 0.0f || power < b.z) continue;
         // here -5.55 < power <= 0 (the skip bound is -ln(255 o) - 0.001 with
         // o <= 1), inside exp32's unguarded range
         const float vv = b.y * exp32_core(power);
         const float alpha = vv > kAlphaMax ? kAlphaMax : vv;
-        if (alpha < kAlphaMin) continue;
         const float test_T = T[k] * (1.0f - alpha);
-        if (test_T < kTMin) {
-          done[k] = true;
-          continue;
-        }
+        // the skip (alpha < 1/255) and the stop (transmittance would fall
+        // below 1e-4; this Gaussian is not added) without branches: a pixel
+        // that does not take the Gaussian adds zero weight and keeps its state
+        const bool ok = !(alpha < kAlphaMin);
+        const bool stop = ok && test_T < kTMin;
+        const bool take = ok && !stop;
+        done[k] = stop;
         const float4 c = sC[j];
-        const float w = alpha * T[k];
+        const float w = take ? alpha * T[k] : 0.0f;
         C[k][0] = fmaf(w, c.x, C[k][0]);
         C[k][1] = fmaf(w, c.y, C[k][1]);
         C[k][2] = fmaf(w, c.z, C[k][2]);
-        T[k] = test_T;
-        last[k] = pos0 + (b0 - rg.x) + j + 1;
+        T[k] = take ? test_T : T[k];
+        last[k] = take ? pos0 + (b0 - rg.x) + j + 1 : last[k];
       }
     }
   }
