@@ -38,6 +38,8 @@ HBM_PEAK_FALLBACK = 6800.0
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
+# (view, Gaussian) records one workspace can hold: n * views < 2^26
+RECORD_LIMIT = 1 << 26
 
 # Algorithmic FP32 operations per (pixel, listed Gaussian) evaluation of the
 # blend kernels (an FMA counts 2, an exponential or reciprocal 1): the
@@ -669,11 +671,14 @@ def run_next_rows(args, r, st, scene, cams, images, target, grads, dev, bf16, hb
     cg.grow(gpos, glogit, gsr, gsh, n, m, 7, 1, src_out=src, workspace=gws)
     ms_grow = _time_calls(lambda: cg.grow(gpos, glogit, gsr, gsh, n, m, 7, 1, src_out=src, workspace=gws), reps,
                           stream)
-    rg = cg.Renderer(cams, pair_capacity=r.pair_capacity, device=dev, n_capacity=n + m)
+    # the renderer holds at most 2^26 (view, Gaussian) records: the grown
+    # scene is rendered from as many of the workload's views as fit
+    gcams = cams[:max(1, min(len(cams), (RECORD_LIMIT - 1) // (n + m)))]
+    rg = cg.Renderer(gcams, pair_capacity=r.pair_capacity, device=dev, n_capacity=n + m)
     small = cg.SceneTensors(gpos[:n], glogit[:n], gsr[:n], gsh[:n], st.sr_rows, st.sh_rows, st.sh_degree)
     grown = cg.SceneTensors(gpos, glogit, gsr, gsh, st.sr_rows, st.sh_rows, st.sh_degree)
     rg.forward(small)
-    rg.backward(torch.zeros_like(images))
+    rg.backward(torch.zeros(sum(3 * c.width * c.height for c in gcams), device=dev))
     rg.codebook_reduce()                     # memberships of the first n Gaussians
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -684,7 +689,8 @@ def run_next_rows(args, r, st, scene, cams, images, target, grads, dev, bf16, hb
     ms_app = a.elapsed_time(b)
     state = rg.array(cg.WS_CSR_STATE, torch.int32, 10).cpu().numpy().reshape(2, 10)
     out["grow"] = {"ms": round(ms_grow, 4), "gaussians": n, "added": m, "bytes_model": "copies of 24 B per new Gaussian"}
-    out["membership_append"] = {"ms": round(ms_app, 4), "appended": m, "incremental": bool((state[:, 7] == 1).all()),
+    out["membership_append"] = {"ms": round(ms_app, 4), "appended": m, "views": len(gcams),
+                                "incremental": bool((state[:, 7] == 1).all()),
                                 "timing": "one eager call between CUDA events (includes launch gaps)"}
     del rg
     # split and merge of each codebook with the paper's hyperparameters

@@ -268,7 +268,7 @@ struct PixelBwd {
 // Per-pixel backward of one Gaussian at list position `pos`: writes its nine
 // terms, summed over the thread's pixels, to g[9 S ...]: the moments
 // sum dpow dx, dpow dy, dpow dx^2, dpow dx dy, dpow dy^2 of dpow = dL/dpower,
-// dL/dopacity, dL/drgb.  The range test (list position before the pixel's
+// sum dpow (dL/dopacity times the opacity), dL/drgb.  The range test (list position before the pixel's
 // last contributor, power in [skip bound, 0]) is taken for all of the
 // thread's pixels first; a thread none of whose pixels is in range writes
 // zeros, the others run every pixel without branches, gating an
@@ -305,7 +305,7 @@ __device__ __forceinline__ bool bwd_gaussian(const float4& a, const float4& b, c
       if (in[k] && fabsf(pw[k] - b.w) < c.w) ex[k] = exp32_core(pw[k]);
   }
   bool any = false;
-  float sdp = 0.0f, sdpy = 0.0f, sdpy2 = 0.0f, se = 0.0f, sw0 = 0.0f, sw1 = 0.0f, sw2 = 0.0f;
+  float sdp = 0.0f, sdpy = 0.0f, sdpy2 = 0.0f, sw0 = 0.0f, sw1 = 0.0f, sw2 = 0.0f;
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     const float vv = b.y * ex[k];
@@ -332,7 +332,6 @@ __device__ __forceinline__ bool bwd_gaussian(const float4& a, const float4& b, c
     sdp += dpow;
     sdpy += pyv;
     sdpy2 = fmaf(pyv, dy[k], sdpy2);
-    se = fmaf(ex[k], dop, se);
     px.accd[k] = fmaf(al, dot, px.accd[k]);
     px.T[k] = ok ? Tk : px.T[k];
   }
@@ -343,7 +342,9 @@ __device__ __forceinline__ bool bwd_gaussian(const float4& a, const float4& b, c
   g[9 * S + 2] = dx * sdpx;
   g[9 * S + 3] = dx * sdpy;
   g[9 * S + 4] = sdpy2;
-  g[9 * S + 5] = se;
+  // dL/dopacity = sum ex dop = (sum dpow) / opacity: the division is
+  // applied once per pair, after the sums
+  g[9 * S + 5] = sdp;
   g[9 * S + 6] = sw0;
   g[9 * S + 7] = sw1;
   g[9 * S + 8] = sw2;
@@ -490,7 +491,9 @@ __global__ void __launch_bounds__(TileShape<TILE, PPT>::NT) k_blend_bwd(const Bl
         float t = part[0][j][5];
 #pragma unroll
         for (int w = 1; w < NW; ++w) t += part[w][j][5];
-        args.pairgrad1[sSlot[j]] = t;
+        // sum over pixels of dL/dpower -> dL/dopacity (a Gaussian that
+        // never passes the skip test has a zero sum, whatever its opacity)
+        args.pairgrad1[sSlot[j]] = t == 0.0f ? 0.0f : t / sB[j].y;
         args.pairlive[sSlot[j]] = 1;
       }
     }
