@@ -56,8 +56,8 @@ FLOPS_PER_EVAL = {"blend_fwd": 21, "blend_bwd": 55}
 # workload (summaries under profiles/), valid while the kernel's source file
 # hashes (SHA-256, first 16 hex digits) to `src`; null otherwise.
 NCU_TRAFFIC = {
-    "blend_bwd": {"bytes": 77190400 + 16061696, "src": "7b55c7546e7341be", "workload": "truck"},
-    "blend_fwd": {"bytes": 18647040 + 581376 + 28041984 + 256, "src": "7b55c7546e7341be", "workload": "truck"},
+    "blend_bwd": {"bytes": 78473472 + 16445952, "src": "5db0e61261d7c743", "workload": "truck"},
+    "blend_fwd": {"bytes": 18648320 + 820480 + 28021760 + 23296, "src": "5db0e61261d7c743", "workload": "truck"},
 }
 
 
@@ -687,7 +687,7 @@ def run_next_rows(args, r, st, scene, cams, images, target, grads, dev, bf16, hb
     b.record(stream)
     torch.cuda.synchronize()
     ms_app = a.elapsed_time(b)
-    state = rg.array(cg.WS_CSR_STATE, torch.int32, 10).cpu().numpy().reshape(2, 10)
+    state = rg.array(cg.WS_CSR_STATE, torch.int32, 12).cpu().numpy().reshape(2, 12)  # two 48-byte states
     out["grow"] = {"ms": round(ms_grow, 4), "gaussians": n, "added": m, "bytes_model": "copies of 24 B per new Gaussian"}
     out["membership_append"] = {"ms": round(ms_app, 4), "appended": m, "views": len(gcams),
                                 "incremental": bool((state[:, 7] == 1).all()),

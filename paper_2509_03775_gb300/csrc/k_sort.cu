@@ -341,8 +341,84 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* in, 
   }
 }
 
+// Exclusive scan of at most kScanOneMax values in one CTA (the codebooks'
+// chunk and membership counts): one launch instead of three.  Longer inputs
+// (the group sums of the tile lists) keep the three-kernel path, which
+// spreads them over the SMs: on one SM a 47K-value scan took longer than
+// the three launches.
+// Warp w owns the contiguous range [w * 32 * kScanOneRows, ...), read as rows
+// of 32 consecutive values (coalesced), kScanOneBatch rows per batch of
+// loads; pass one sums each warp's range, the warp totals are scanned in 64
+// bits, pass two scans each row across the warp and carries the running
+// 64-bit base.  Every caller's values are small enough that 32 of them sum
+// below 2^32 (group sums of 32 records' tile counts, chunk and membership
+// counts, flags).  Each thread reads its own positions before writing them,
+// so `in` may equal `out`.
+constexpr int kScanOneRows = 16;
+constexpr int kScanOneBatch = 16;
+constexpr int64_t kScanOneMax = 1024 * kScanOneRows;
+
+__global__ void __launch_bounds__(1024) k_scan_one(const uint32_t* in, uint32_t* out, const uint64_t* count_dev,
+                                                   int64_t count_cap, uint64_t* total_dev) {
+  __shared__ uint64_t wsum[32];
+  const int64_t count = min((int64_t)*count_dev, count_cap);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t row0 = (int64_t)wid * 32 * kScanOneRows;  // first value of the warp's range
+  uint32_t v[kScanOneBatch];
+  uint64_t local = 0;
+  for (int r0 = 0; r0 < kScanOneRows && row0 + 32 * r0 < count; r0 += kScanOneBatch) {
+#pragma unroll
+    for (int q = 0; q < kScanOneBatch; ++q) {
+      const int64_t i = row0 + 32 * (r0 + q) + lane;
+      v[q] = i < count ? in[i] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < kScanOneBatch; ++q) local += v[q];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+  if (lane == 0) wsum[wid] = local;
+  __syncthreads();
+  if (wid == 0) {
+    uint64_t x = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    wsum[lane] = x;
+  }
+  __syncthreads();
+  uint64_t run = wid > 0 ? wsum[wid - 1] : 0ull;
+  // the loop bounds are warp-uniform, so every shuffle has all 32 lanes
+  for (int r0 = 0; r0 < kScanOneRows && row0 + 32 * r0 < count; r0 += kScanOneBatch) {
+#pragma unroll
+    for (int q = 0; q < kScanOneBatch; ++q) {
+      const int64_t i = row0 + 32 * (r0 + q) + lane;
+      v[q] = i < count ? in[i] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < kScanOneBatch; ++q) {
+      const int64_t i = row0 + 32 * (r0 + q) + lane;
+      uint32_t x = v[q];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (i < count) out[i] = (uint32_t)(run + (x - v[q]));
+      run += __shfl_sync(0xffffffffu, x, 31);
+    }
+  }
+  if (threadIdx.x == 0) *total_dev = wsum[31];
+}
+
 cudaError_t scan_u32(void* ws, const Layout& L, const uint32_t* in, uint32_t* out, const uint64_t* count_dev,
                      int64_t count_cap, uint64_t* total_dev, cudaStream_t s) {
+  if (count_cap <= kScanOneMax) {
+    count_launch(), k_scan_one<<<1, 1024, 0, s>>>(in, out, count_dev, count_cap, total_dev);
+    return cudaGetLastError();
+  }
   uint64_t* bsum = ws_ptr<uint64_t>(ws, L.blocksums);
   const int64_t nb_cap = (count_cap + kScanTile - 1) / kScanTile;
   if (nb_cap > L.scan_blocks_cap) return cudaErrorInvalidValue;
