@@ -61,6 +61,12 @@ cudaError_t launch_sigma3(const SceneArgs& sc, const Layout& L, void* ws, cudaSt
   return cudaGetLastError();
 }
 
+__device__ __forceinline__ void cull_record(ushort4* rect, uint32_t* ntiles, uint32_t* depth, int64_t rec) {
+  ntiles[rec] = 0u;
+  rect[rec] = make_ushort4(0, 0, 0, 0);
+  depth[rec] = 0xffffffffu;
+}
+
 // One thread per (view, Gaussian) record, record = v * n + g.
 template <int NB>
 __global__ void __launch_bounds__(256, 3) k_preprocess(const SceneArgs sc, const ViewInfo* __restrict__ views,
@@ -76,12 +82,12 @@ __global__ void __launch_bounds__(256, 3) k_preprocess(const SceneArgs sc, const
     const int v = (int)(rec / sc.n);
     const int64_t g = rec - (int64_t)v * sc.n;
     const ViewInfo& cam = sviews[v];
-    ntiles[rec] = 0u;
-    rect[rec] = make_ushort4(0, 0, 0, 0);
-    depth[rec] = 0xffffffffu;
+    // a culled record gets an empty rectangle, no tiles and the largest
+    // depth key; a visible one writes its own values once, at the end
     const uint32_t isr = sc.g2sr[g], ish = sc.g2sh[g];
     if (isr >= (uint32_t)sc.k_sr || ish >= (uint32_t)sc.k_sh) {
       set_status(st, CG_ERR_INDEX, (uint32_t)g);
+      cull_record(rect, ntiles, depth, rec);
       continue;
     }
     const float p0 = sc.pos[3 * g], p1 = sc.pos[3 * g + 1], p2 = sc.pos[3 * g + 2];
@@ -89,7 +95,10 @@ __global__ void __launch_bounds__(256, 3) k_preprocess(const SceneArgs sc, const
     float t[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) t[a] = fmaf(W[4 * a], p0, fmaf(W[4 * a + 1], p1, fmaf(W[4 * a + 2], p2, W[4 * a + 3])));
-    if (!(t[2] > cam.near_z)) continue;
+    if (!(t[2] > cam.near_z)) {
+      cull_record(rect, ntiles, depth, rec);
+      continue;
+    }
     const float tz = t[2];
     const float u = t[0] / tz, w = t[1] / tz;
     const float fx = cam.fx, fy = cam.fy;
@@ -113,7 +122,10 @@ __global__ void __launch_bounds__(256, 3) k_preprocess(const SceneArgs sc, const
     const float B = fmaf(U[0], T[3], fmaf(U[1], T[4], U[2] * T[5]));
     const float C = fmaf(U[3], T[3], fmaf(U[4], T[4], U[5] * T[5])) + kDilation;
     const float det = fmaf(A, C, -(B * B));
-    if (!(det > 0.0f)) continue;
+    if (!(det > 0.0f)) {
+      cull_record(rect, ntiles, depth, rec);
+      continue;
+    }
     const float mid = 0.5f * (A + C);
     const float disc = fmaf(mid, mid, -det);
     const float lam = mid + sqrtf(disc > kLambdaFloor ? disc : kLambdaFloor);
@@ -128,7 +140,10 @@ __global__ void __launch_bounds__(256, 3) k_preprocess(const SceneArgs sc, const
     fy0 = fy0 < 0.0f ? 0.0f : (fy0 > TY ? TY : fy0);
     fy1 = fy1 < 0.0f ? 0.0f : (fy1 > TY ? TY : fy1);
     const int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1;
-    if (x1 <= x0 || y1 <= y0) continue;
+    if (x1 <= x0 || y1 <= y0) {
+      cull_record(rect, ntiles, depth, rec);
+      continue;
+    }
     const float c0 = C / det, c1 = -B / det, c2 = A / det;
     const float o = sigmoid32(sc.logit[g]);
     // conservative skip bound: power below it means o * exp32(power) < 1/255

@@ -357,6 +357,24 @@ def test_largest_codebooks():
     _compare(ref, gpu)
 
 
+@pytest.mark.parametrize("k_sr,k_sh", [(16384, 16385), (16385, 16384)])
+def test_codebooks_at_the_short_scan_limit(k_sr, k_sh):
+    """Codebooks of 16,384 rows (the longest chunk-count scan done by one CTA)
+    and 16,385 rows (the first done by the three-kernel scan), each in both
+    codebooks, so that both scan paths feed the chunked row sums."""
+    scene, cams = scenes.config_single(n=30_000, k=1024, width=160, height=128)
+    rng = np.random.default_rng(43)
+    s = scene.copy()
+    s.sr_rows = scenes._sr_rows(rng, k_sr, -3.0, 0.5)
+    s.sh_rows = scenes._sh_rows(rng, k_sh, 3)
+    s.g2sr = rng.integers(0, k_sr, size=s.n).astype(np.uint16)
+    s.g2sh = rng.integers(0, k_sh, size=s.n).astype(np.uint16)
+    s.g2sr[:3] = k_sr - 1
+    s.g2sh[3:6] = k_sh - 1
+    ref, gpu = _case(s, cams)
+    _compare(ref, gpu)
+
+
 def test_most_views_in_one_launch():
     """64 views (the most one call takes) of small, uneven resolutions."""
     scene, _ = scenes.config_single(n=5_000, k=256, width=8, height=8)
