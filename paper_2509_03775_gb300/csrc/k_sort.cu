@@ -519,10 +519,11 @@ __device__ __forceinline__ int64_t list_cut(int64_t vis) { return (vis + 9) / 10
 
 // Per view, the 2D inclusive prefix sums of the unfinished-tile flags:
 // sat[(y + 1) (tiles_x + 1) + x + 1] = unfinished tiles in [0, x] x [0, y]
-// (row and column 0 are 0).  One block per view: each warp scans whole tile
-// rows 32 columns at a time (coalesced), then each thread accumulates one
-// column down the rows, loading eight rows ahead of the running sum.
-__global__ void __launch_bounds__(256) k_unsat_sat(const ViewInfo* __restrict__ views,
+// (row and column 0 are 0).  One block of 1024 threads per view: each warp
+// scans whole tile rows 32 columns at a time (coalesced, four columns'
+// loads issued together), then each thread accumulates one column down the
+// rows, loading eight rows ahead of the running sum.
+__global__ void __launch_bounds__(1024) k_unsat_sat(const ViewInfo* __restrict__ views,
                                                    const uint8_t* __restrict__ unsat, uint32_t* __restrict__ sat) {
   const ViewInfo& cam = views[blockIdx.x];
   const int tx = cam.tiles_x, ty = cam.tiles_y, W = tx + 1;
@@ -534,16 +535,25 @@ __global__ void __launch_bounds__(256) k_unsat_sat(const ViewInfo* __restrict__ 
     uint32_t* row = S + (int64_t)(r + 1) * W;
     if (lane == 0) row[0] = 0u;
     uint32_t carry = 0;
-    for (int x0 = 0; x0 < tx; x0 += 32) {
-      const int x = x0 + lane;
-      uint32_t v = x < tx ? (uint32_t)u[(int64_t)r * tx + x] : 0u;
+    // four 32-column chunks per round: their loads are issued together
+    for (int x0 = 0; x0 < tx; x0 += 128) {
+      uint32_t v[4];
 #pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, v, d);
-        if (lane >= d) v += t;
+      for (int q = 0; q < 4; ++q) {
+        const int x = x0 + 32 * q + lane;
+        v[q] = x < tx ? (uint32_t)u[(int64_t)r * tx + x] : 0u;
       }
-      if (x < tx) row[x + 1] = carry + v;
-      carry += __shfl_sync(0xffffffffu, v, 31);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int x = x0 + 32 * q + lane;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t t = __shfl_up_sync(0xffffffffu, v[q], d);
+          if (lane >= d) v[q] += t;
+        }
+        if (x < tx) row[x + 1] = carry + v[q];
+        carry += __shfl_sync(0xffffffffu, v[q], 31);
+      }
     }
   }
   __syncthreads();
@@ -911,7 +921,7 @@ cudaError_t launch_build_lists(const Layout& L, void* ws, int part, cudaStream_t
   //    only), pair offsets of the groups of 32 records in depth order, the
   //    part's pair count and the capacity check
   uint32_t* sat = ws_ptr<uint32_t>(ws, L.sat);
-  if (part == 1) count_launch(), k_unsat_sat<<<L.n_views, 256, 0, s>>>(ws_ptr<ViewInfo>(ws, L.views), unsat, sat);
+  if (part == 1) count_launch(), k_unsat_sat<<<L.n_views, 1024, 0, s>>>(ws_ptr<ViewInfo>(ws, L.views), unsat, sat);
   count_launch(), k_count_emit<<<g, 256, 0, s>>>(dsorted, ws_ptr<const float4>(ws, L.geo),
                                                  ws_ptr<const ushort4>(ws, L.rect), ws_ptr<ViewInfo>(ws, L.views),
                                                  L.n, R, L.tile, part, unsat, sat, ws_ptr<uint32_t>(ws, L.nemit), scan,
