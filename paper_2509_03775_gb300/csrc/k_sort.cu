@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(1024) k_unsat_sat(const ViewInfo* __restrict__
     uint32_t* row = S + (int64_t)(r + 1) * W;
     if (lane == 0) row[0] = 0u;
     uint32_t carry = 0;
-    // four 32-column chunks per round: their loads are issued together
+    // four 32-column chunks per iteration: their loads are issued together
     for (int x0 = 0; x0 < tx; x0 += 128) {
       uint32_t v[4];
 #pragma unroll
